@@ -1,0 +1,331 @@
+"""ctypes front end of the CPU oracle (``pbad_oracle.c``).
+
+TEST INFRASTRUCTURE ONLY: the test suite, the smoke check and the benchmark's
+CPU-baseline leg are the only callers. The product path never imports this
+module, and this module never imports the product package.
+
+Builds ``libpbad_oracle.so`` with gcc on first use if it is missing.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pbad_oracle.c")
+_LIB = os.path.join(_HERE, "libpbad_oracle.so")
+
+HINGE, BALL = 0, 1
+STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE"}
+
+
+def build(force: bool = False) -> str:
+    """Compiles the oracle (plain C99, FP64, no fast-math, no FMA contraction)."""
+    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+        subprocess.check_call(["gcc", "-O2", "-std=c99", "-D_DEFAULT_SOURCE",
+                               "-ffp-contract=off", "-fPIC", "-shared", "-o",
+                               _LIB, _SRC, "-lm"])
+    return _LIB
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = C.CDLL(_LIB)
+        dp = C.POINTER(C.c_double)
+        ip = C.POINTER(C.c_int)
+        vp = C.c_void_p
+        L.om_model_new.restype = vp
+        L.om_model_new.argtypes = [C.c_int, ip, ip, dp, dp, dp, dp]
+        L.om_model_free.argtypes = [vp]
+        L.om_n_dof.restype = C.c_int
+        L.om_n_dof.argtypes = [vp]
+        L.om_fk.argtypes = [vp, dp, dp]
+        L.om_link_dT.argtypes = [vp, dp, C.c_int, dp]
+        L.om_link_ddT.argtypes = [vp, dp, C.c_int, C.c_int, C.c_int, dp]
+        L.om_joint_rot.argtypes = [C.c_int, dp, dp, dp]
+        L.om_joint_drot.argtypes = [C.c_int, dp, dp, C.c_int, dp]
+        L.om_joint_ddrot.argtypes = [C.c_int, dp, dp, C.c_int, C.c_int, dp]
+        L.om_legendre_roots.restype = C.c_int
+        L.om_legendre_roots.argtypes = [C.c_int, dp]
+        L.om_colloc.restype = C.c_int
+        L.om_colloc.argtypes = [C.c_int, dp, dp]
+        L.om_mass_moment_rod.argtypes = [C.c_double, C.c_double, dp]
+        L.om_mass_moment_capsule.argtypes = [C.c_double, C.c_double, C.c_double, dp]
+        L.om_hmass.argtypes = [vp, dp, dp]
+        L.om_eval.restype = C.c_double
+        L.om_eval.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp]
+        L.om_resid_known_jac.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp]
+        L.om_step.restype = C.c_int
+        L.om_step.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, C.c_int, C.c_int,
+                              C.c_double, C.c_int, C.c_int, dp, ip, ip]
+        L.om_rollout.restype = C.c_int
+        L.om_rollout.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, C.c_int, C.c_int,
+                                 C.c_int, C.c_double, C.c_int, C.c_int, dp, dp, dp, dp, ip, ip]
+        L.om_step_adjoint.restype = C.c_int
+        L.om_step_adjoint.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp, dp]
+        L.om_rnea.restype = C.c_int
+        L.om_rnea.argtypes = [vp, dp, dp, dp, dp]
+        L.om_rk4.restype = C.c_int
+        L.om_rk4.argtypes = [vp, dp, dp, dp, C.c_double, C.c_int]
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    a = np.ascontiguousarray(a, dtype=np.float64)
+    return a, a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _i(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _null():
+    return C.POINTER(C.c_double)()
+
+
+# --------------------------------------------------------------------------
+# stand-alone functions
+# --------------------------------------------------------------------------
+
+def legendre_roots(n: int) -> np.ndarray:
+    x = np.zeros(max(n, 1))
+    _, xp = _d(x)
+    lib().om_legendre_roots(n, xp)
+    return x[:n].copy() if n else np.zeros(0)
+
+
+def colloc(S: int):
+    """(nodes (S+2,), W (S, S+2)) in units of dt and 1/dt^2."""
+    nodes = np.zeros(S + 2)
+    W = np.zeros((S, S + 2))
+    rc = lib().om_colloc(S, nodes.ctypes.data_as(C.POINTER(C.c_double)),
+                         W.ctypes.data_as(C.POINTER(C.c_double)))
+    if rc != 0:
+        raise ValueError("unsupported stage count")
+    return nodes, W
+
+
+def mass_moment_rod(m: float, L: float) -> np.ndarray:
+    out = np.zeros(10)
+    lib().om_mass_moment_rod(m, L, out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
+
+
+def mass_moment_capsule(m: float, L: float, r: float) -> np.ndarray:
+    out = np.zeros(10)
+    lib().om_mass_moment_capsule(m, L, r, out.ctypes.data_as(C.POINTER(C.c_double)))
+    return out
+
+
+def joint_rot(jtype: int, axis, q, k: int | None = None, m: int | None = None):
+    """R, dR/dq_k or d2R/dq_k dq_m of one joint (3x3)."""
+    axis, ap = _d(np.asarray(axis, dtype=np.float64).reshape(3))
+    q, qp = _d(np.atleast_1d(np.asarray(q, dtype=np.float64)))
+    out = np.zeros(9)
+    op = out.ctypes.data_as(C.POINTER(C.c_double))
+    if k is None:
+        lib().om_joint_rot(jtype, ap, qp, op)
+    elif m is None:
+        lib().om_joint_drot(jtype, ap, qp, k, op)
+    else:
+        lib().om_joint_ddrot(jtype, ap, qp, k, m, op)
+    return out.reshape(3, 3)
+
+
+# --------------------------------------------------------------------------
+# models
+# --------------------------------------------------------------------------
+
+def mass_moments_from_spec(spec, b: int) -> np.ndarray:
+    N = spec.n_links
+    mm = np.zeros((N, 10))
+    for l in range(N):
+        if spec.shape[l] == 0:
+            mm[l] = mass_moment_rod(spec.mass[b, l], spec.length[b, l])
+        else:
+            mm[l] = mass_moment_capsule(spec.mass[b, l], spec.length[b, l], spec.radius[b, l])
+    return mm
+
+
+def rest_from_spec(spec, b: int) -> np.ndarray:
+    N = spec.n_links
+    rest = np.zeros((N, 3, 4))
+    rest[:, :, :3] = spec.rest_rot
+    rest[:, :, 3] = spec.attach[b]
+    return rest.reshape(N, 12)
+
+
+class OracleModel:
+    """One articulated body (one instance) in the oracle."""
+
+    def __init__(self, parent, jtype, axis, mm, rest, gravity):
+        self.parent, pp = _i(parent)
+        self.jtype, jp = _i(jtype)
+        self.axis, ap = _d(np.asarray(axis).reshape(-1, 3))
+        self.mm, mp = _d(np.asarray(mm).reshape(-1, 10))
+        self.rest, rp = _d(np.asarray(rest).reshape(-1, 12))
+        self.gravity, gp = _d(gravity)
+        self.n_links = int(self.parent.shape[0])
+        h = lib().om_model_new(self.n_links, pp, jp, ap, mp, rp, gp)
+        if not h:
+            raise ValueError("malformed model")
+        self._h = C.c_void_p(h)
+        self.n_dof = lib().om_n_dof(self._h)
+
+    @classmethod
+    def from_spec(cls, spec, b: int = 0):
+        return cls(spec.parent, spec.jtype, spec.axis, mass_moments_from_spec(spec, b),
+                   rest_from_spec(spec, b), spec.gravity)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and _lib is not None:
+            _lib.om_model_free(h)
+            self._h = None
+
+    def fk(self, q):
+        q, qp = _d(q)
+        T = np.zeros((self.n_links, 4, 4))
+        lib().om_fk(self._h, qp, T.ctypes.data_as(C.POINTER(C.c_double)))
+        return T
+
+    def link_dT(self, q, l: int):
+        q, qp = _d(q)
+        out = np.zeros((self.n_dof, 4, 4))
+        lib().om_link_dT(self._h, qp, l, out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
+
+    def link_ddT(self, q, l: int, d: int, e: int):
+        q, qp = _d(q)
+        out = np.zeros((4, 4))
+        lib().om_link_ddT(self._h, qp, l, d, e, out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
+
+    def hmass(self, q):
+        q, qp = _d(q)
+        H = np.zeros((self.n_dof, self.n_dof))
+        lib().om_hmass(self._h, qp, H.ctypes.data_as(C.POINTER(C.c_double)))
+        return H
+
+    def eval(self, S: int, dt: float, qs, q_prev, q_cur, tau, want_grad=True, want_jac=False):
+        """Returns (E, r, grad, Jr); grad / Jr are None unless requested."""
+        n = self.n_dof
+        qs, qsp = _d(np.asarray(qs).reshape(S * n))
+        q_prev, pp = _d(q_prev)
+        q_cur, cp = _d(q_cur)
+        tau, tp = _d(tau)
+        r = np.zeros(S * n)
+        g = np.zeros(S * n) if want_grad else None
+        J = np.zeros((S * n, S * n)) if want_jac else None
+        E = lib().om_eval(self._h, S, dt, qsp, pp, cp, tp,
+                          r.ctypes.data_as(C.POINTER(C.c_double)),
+                          g.ctypes.data_as(C.POINTER(C.c_double)) if g is not None else _null(),
+                          J.ctypes.data_as(C.POINTER(C.c_double)) if J is not None else _null())
+        return E, r, g, J
+
+    def resid_known_jac(self, S: int, dt: float, qs, q_prev, q_cur):
+        n = self.n_dof
+        qs, qsp = _d(np.asarray(qs).reshape(S * n))
+        q_prev, pp = _d(q_prev)
+        q_cur, cp = _d(q_cur)
+        Jp = np.zeros((S * n, n))
+        Jc = np.zeros((S * n, n))
+        lib().om_resid_known_jac(self._h, S, dt, qsp, pp, cp,
+                                 Jp.ctypes.data_as(C.POINTER(C.c_double)),
+                                 Jc.ctypes.data_as(C.POINTER(C.c_double)))
+        return Jp, Jc
+
+    def step(self, S, dt, q_prev, q_cur, tau, solver="lbfgs", history=8, tol=1e-10,
+             max_iter=None, precond=True):
+        n = self.n_dof
+        sv = 0 if solver == "lbfgs" else 1
+        if max_iter is None:
+            max_iter = 1000 if sv == 0 else 100
+        q_prev, pp = _d(q_prev)
+        q_cur, cp = _d(q_cur)
+        tau, tp = _d(tau)
+        qs = np.zeros(S * n)
+        it = C.c_int(0)
+        ev = C.c_int(0)
+        st = lib().om_step(self._h, S, dt, pp, cp, tp, sv, history, tol, max_iter,
+                           int(precond), qs.ctypes.data_as(C.POINTER(C.c_double)),
+                           C.byref(it), C.byref(ev))
+        return qs.reshape(S, n), st, it.value, ev.value
+
+    def rollout(self, S, dt, q_prev0, q_cur0, tau_seq, solver="lbfgs", history=8,
+                tol=1e-10, max_iter=None, precond=True):
+        """Returns dict(traj_prev, traj_cur (n_steps, n), q_prev, q_cur, status,
+        iters, evals)."""
+        n = self.n_dof
+        sv = 0 if solver == "lbfgs" else 1
+        if max_iter is None:
+            max_iter = 1000 if sv == 0 else 100
+        tau_seq, tsp = _d(np.asarray(tau_seq).reshape(-1, n))
+        n_steps = tau_seq.shape[0]
+        q_prev0, pp = _d(q_prev0)
+        q_cur0, cp = _d(q_cur0)
+        tp_ = np.zeros((n_steps, n))
+        tc_ = np.zeros((n_steps, n))
+        qpo = np.zeros(n)
+        qco = np.zeros(n)
+        it = C.c_int(0)
+        ev = C.c_int(0)
+        fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        st = lib().om_rollout(self._h, S, dt, pp, cp, tsp, n_steps, sv, history, tol,
+                              max_iter, int(precond), fp(tp_), fp(tc_), fp(qpo), fp(qco),
+                              C.byref(it), C.byref(ev))
+        return dict(traj_prev=tp_, traj_cur=tc_, q_prev=qpo, q_cur=qco, status=st,
+                    iters=it.value, evals=ev.value)
+
+    def step_adjoint(self, S, dt, q_prev, q_cur, tau, qs, gbar):
+        n = self.n_dof
+        q_prev, pp = _d(q_prev)
+        q_cur, cp = _d(q_cur)
+        tau, tp = _d(tau)
+        qs, qsp = _d(np.asarray(qs).reshape(S * n))
+        gbar, gp = _d(np.asarray(gbar).reshape(S * n))
+        gqp = np.zeros(n)
+        gqc = np.zeros(n)
+        gt = np.zeros(n)
+        fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
+        rc = lib().om_step_adjoint(self._h, S, dt, pp, cp, tp, qsp, gp, fp(gqp), fp(gqc), fp(gt))
+        if rc != 0:
+            raise RuntimeError("singular residual Jacobian")
+        return gqp, gqc, gt
+
+    def rnea(self, q, qd, qdd):
+        q, qp = _d(q)
+        qd, vp = _d(qd)
+        qdd, ap = _d(qdd)
+        tau = np.zeros(self.n_dof)
+        rc = lib().om_rnea(self._h, qp, vp, ap, tau.ctypes.data_as(C.POINTER(C.c_double)))
+        if rc != 0:
+            raise ValueError("RNEA supports hinge joints only")
+        return tau
+
+    def rk4(self, q, qd, tau, h: float, n_steps: int):
+        q = np.array(q, dtype=np.float64)
+        qd = np.array(qd, dtype=np.float64)
+        tau, tp = _d(tau)
+        rc = lib().om_rk4(self._h, q.ctypes.data_as(C.POINTER(C.c_double)),
+                          qd.ctypes.data_as(C.POINTER(C.c_double)), tp, h, n_steps)
+        if rc != 0:
+            raise RuntimeError("RK4 failed")
+        return q, qd
+
+
+def initial_prev(q0, qd0, S: int, dt: float):
+    """q at the node k-1+alpha_{S-1} from q0 and an initial velocity:
+    q_prev = q0 + node_prev * dt * qd0 (node_prev < 0)."""
+    nodes, _ = colloc(S)
+    return q0 + nodes[0] * dt * qd0

@@ -1,0 +1,243 @@
+"""Seeded synthetic workloads for the position-based articulated dynamics path.
+
+This module only draws random numbers and assembles plain descriptions of
+articulated bodies (topology, link lengths, masses, radii, initial poses and
+torques). It holds none of the method's arithmetic: mass moments, kinematics,
+objectives and solvers live on each side (the CUDA library and the CPU oracle)
+separately, and both consume the same description.
+
+Every generator takes a seed; ``numpy.random.default_rng(seed)`` (PCG64) is
+the only source of randomness. The workloads mirror the paper's chain-swinging
+benchmark (Section 6.1, Fig. SWING/OPTProf/CPUGPU) and its articulated
+characters (Section 6.2): serial chains of rods or capsules, and branching
+trees with hinge and ball joints, always with a fixed root.
+
+Geometry conventions: a link's frame origin is its joint; the link body runs
+along its local -z axis from 0 to -L; a child's joint sits at its parent's tip
+unless an explicit attachment point is given; hinge axes are local +y.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+HINGE = 0
+BALL = 1
+ROD = 0
+CAPSULE = 1
+
+GRAVITY = np.array([0.0, 0.0, -9.81])
+
+
+@dataclass
+class BodySpec:
+    """Plain description of ``count`` instances sharing one topology.
+
+    Attributes (N links, B = count instances):
+        parent:   (N,) int32, parent[l] < l, -1 = world.
+        jtype:    (N,) int32, 0 hinge / 1 ball.
+        axis:     (N, 3) hinge axes in the joint frame (ignored for balls).
+        rest_rot: (N, 3, 3) rotation of the joint frame in the parent frame.
+        attach:   (B, N, 3) joint position in the parent link frame.
+        length:   (B, N) link lengths.
+        mass:     (B, N) link masses.
+        radius:   (B, N) capsule radii (0 for rods).
+        shape:    (N,) int32, 0 rod / 1 capsule.
+        gravity:  (3,).
+    """
+
+    parent: np.ndarray
+    jtype: np.ndarray
+    axis: np.ndarray
+    rest_rot: np.ndarray
+    attach: np.ndarray
+    length: np.ndarray
+    mass: np.ndarray
+    radius: np.ndarray
+    shape: np.ndarray
+    gravity: np.ndarray = field(default_factory=lambda: GRAVITY.copy())
+    name: str = ""
+
+    @property
+    def n_links(self) -> int:
+        return int(self.parent.shape[0])
+
+    @property
+    def count(self) -> int:
+        return int(self.length.shape[0])
+
+    @property
+    def n_dof(self) -> int:
+        return int(np.sum(np.where(self.jtype == BALL, 3, 1)))
+
+    def dof_slices(self):
+        off = 0
+        out = []
+        for t in self.jtype:
+            k = 3 if t == BALL else 1
+            out.append(slice(off, off + k))
+            off += k
+        return out
+
+    def select(self, idx) -> "BodySpec":
+        """Sub-batch with the given instance indices."""
+        idx = np.asarray(idx)
+        return BodySpec(self.parent, self.jtype, self.axis, self.rest_rot,
+                        self.attach[idx], self.length[idx], self.mass[idx],
+                        self.radius[idx], self.shape, self.gravity, self.name)
+
+
+def _chain_topology(n_links: int, joint: int):
+    parent = np.arange(-1, n_links - 1, dtype=np.int32)
+    jtype = np.full(n_links, joint, dtype=np.int32)
+    axis = np.tile(np.array([0.0, 1.0, 0.0]), (n_links, 1))
+    rest_rot = np.tile(np.eye(3), (n_links, 1, 1))
+    return parent, jtype, axis, rest_rot
+
+
+def _chain_attach(length: np.ndarray) -> np.ndarray:
+    B, N = length.shape
+    attach = np.zeros((B, N, 3))
+    attach[:, 1:, 2] = -length[:, :-1]
+    return attach
+
+
+def rod_chain(count: int, n_links: int, length: float = 1.0, mass: float = 1.0,
+              name: str = "") -> BodySpec:
+    """Planar serial chain of uniform rods with hinge joints (paper Fig. SWING
+    chains; the 3-link pendulum and the hinge chains of the scaling study)."""
+    parent, jtype, axis, rest_rot = _chain_topology(n_links, HINGE)
+    L = np.full((count, n_links), float(length))
+    M = np.full((count, n_links), float(mass))
+    return BodySpec(parent, jtype, axis, rest_rot, _chain_attach(L), L, M,
+                    np.zeros((count, n_links)), np.full(n_links, ROD, np.int32),
+                    name=name or f"rod_chain{n_links}")
+
+
+def ball_chain(count: int, n_links: int, seed: int, radius: float = 0.05,
+               name: str = "") -> BodySpec:
+    """3D serial chains of capsules with ball joints; per-instance lengths
+    U[0.5, 1.5] and masses lognormal(0, 0.3)."""
+    rng = np.random.default_rng(seed)
+    parent, jtype, axis, rest_rot = _chain_topology(n_links, BALL)
+    L = rng.uniform(0.5, 1.5, size=(count, n_links))
+    M = rng.lognormal(0.0, 0.3, size=(count, n_links))
+    return BodySpec(parent, jtype, axis, rest_rot, _chain_attach(L), L, M,
+                    np.full((count, n_links), radius),
+                    np.full(n_links, CAPSULE, np.int32),
+                    name=name or f"ball_chain{n_links}")
+
+
+def humanoid(count: int, seed: int, name: str = "humanoid20") -> BodySpec:
+    """Branching humanoid-like tree with 20 links and 34 DOFs: a torso on a
+    ball joint at the world origin; four limbs (ball, hinge, hinge, hinge);
+    a spine/head of (ball, ball, hinge) pointing up. Capsules (torso radius
+    0.1, others 0.05), lengths U[0.25, 0.45], masses lognormal(0, 0.3)."""
+    rng = np.random.default_rng(seed)
+    parent, jtype, attach_pts, flips = [], [], [], []
+    parent.append(-1); jtype.append(BALL); attach_pts.append(("fixed", (0, 0, 0))); flips.append(False)
+    limb_attach = [(0.15, 0.0, "top"), (-0.15, 0.0, "top"), (0.1, 0.0, "bottom"), (-0.1, 0.0, "bottom")]
+    for ax, ay, where in limb_attach:
+        for k, jt in enumerate([BALL, HINGE, HINGE, HINGE]):
+            if k == 0:
+                parent.append(0)
+                attach_pts.append((where, (ax, ay)))
+            else:
+                parent.append(len(parent) - 1)
+                attach_pts.append(("tip", None))
+            jtype.append(jt)
+            flips.append(False)
+    for k, jt in enumerate([BALL, BALL, HINGE]):
+        if k == 0:
+            parent.append(0)
+            attach_pts.append(("top", (0.0, 0.0)))
+            flips.append(True)
+        else:
+            parent.append(len(parent) - 1)
+            attach_pts.append(("tip", None))
+            flips.append(False)
+        jtype.append(jt)
+    N = len(parent)
+    parent = np.array(parent, np.int32)
+    jtype = np.array(jtype, np.int32)
+    axis = np.tile(np.array([0.0, 1.0, 0.0]), (N, 1))
+    rest_rot = np.tile(np.eye(3), (N, 1, 1))
+    for l in range(N):
+        if flips[l]:  # rotate by pi about x: the link points up
+            rest_rot[l] = np.diag([1.0, -1.0, -1.0])
+    L = rng.uniform(0.25, 0.45, size=(count, N))
+    M = rng.lognormal(0.0, 0.3, size=(count, N))
+    R = np.full((count, N), 0.05)
+    R[:, 0] = 0.1
+    attach = np.zeros((count, N, 3))
+    for l in range(N):
+        kind, val = attach_pts[l]
+        if kind == "top":
+            attach[:, l, 0], attach[:, l, 1] = val
+        elif kind == "bottom":
+            attach[:, l, 0], attach[:, l, 1] = val
+            attach[:, l, 2] = -L[:, parent[l]]
+        elif kind == "tip":
+            attach[:, l, 2] = -L[:, parent[l]]
+    return BodySpec(parent, jtype, axis, rest_rot, attach, L, M, R,
+                    np.full(N, CAPSULE, np.int32), name=name)
+
+
+def random_state(spec: BodySpec, seed: int, pose_scale: float = np.pi / 8,
+                 vel_sigma: float = 0.5, hinge_scale: float | None = None):
+    """Initial poses and velocities: exp-map / hinge coordinates uniform in
+    [-pose_scale, pose_scale] (hinges use hinge_scale if given) and velocities
+    N(0, vel_sigma^2). Returns (q0, qdot0), each (B, n)."""
+    rng = np.random.default_rng(seed)
+    B, n = spec.count, spec.n_dof
+    q0 = rng.uniform(-pose_scale, pose_scale, size=(B, n))
+    if hinge_scale is not None:
+        for l, sl in enumerate(spec.dof_slices()):
+            if spec.jtype[l] == HINGE:
+                q0[:, sl] = rng.uniform(-hinge_scale, hinge_scale, size=(B, 1))
+    qd0 = rng.normal(0.0, vel_sigma, size=(B, n)) if vel_sigma > 0 else np.zeros((B, n))
+    return q0, qd0
+
+
+def torques(spec: BodySpec, n_steps: int, seed: int, sigma: float = 0.1):
+    """Per-step generalised joint torques, Gaussian N(0, sigma^2):
+    (n_steps, B, n). sigma = 0 gives zeros."""
+    if sigma == 0:
+        return np.zeros((n_steps, spec.count, spec.n_dof))
+    rng = np.random.default_rng(seed)
+    return rng.normal(0.0, sigma, size=(n_steps, spec.count, spec.n_dof))
+
+
+def target_points(count: int, center: np.ndarray, seed: int, radius: float = 1.0):
+    """Targets uniform in a ball of the given radius around center: (B, 3)."""
+    rng = np.random.default_rng(seed)
+    v = rng.normal(size=(count, 3))
+    v /= np.linalg.norm(v, axis=1, keepdims=True)
+    rad = radius * rng.uniform(0, 1, size=(count, 1)) ** (1.0 / 3.0)
+    return center + v * rad
+
+
+# --------------------------------------------------------------------------
+# The workloads (seed = 1000 * workload + stream)
+# --------------------------------------------------------------------------
+
+def pendulum3(seed_base: int = 1000):
+    """3-link planar rod pendulum (L = 1, m = 1), q0 ~ U[-pi/4, pi/4], zero
+    velocity, dt = 0.01, one stage (K = 2), L-BFGS history 5, tol 1e-10,
+    200 steps."""
+    spec = rod_chain(1, 3, name="pendulum3")
+    rng = np.random.default_rng(seed_base + 1)
+    q0 = rng.uniform(-np.pi / 4, np.pi / 4, size=(1, 3))
+    return dict(spec=spec, q0=q0, qd0=np.zeros((1, 3)), dt=0.01, stages=1,
+                history=5, tol=1e-10, n_steps=200, solver="lbfgs")
+
+
+def ball_chains(count: int = 4096, n_links: int = 10, seed_base: int = 2000,
+                n_steps: int = 100):
+    """Batched 3D ball-joint capsule chains: dt = 0.033, three stages (K = 4),
+    L-BFGS history 8, 100 steps."""
+    spec = ball_chain(count, n_links, seed_base + 1)
+    q0, qd0 = random_state(spec, seed_base + 2)
+    return dict(spec=spec, q0=q0, qd0=qd0, dt=0.033, stages=3, history=8,
+                tol=1e-8, n_steps=n_steps, solver="lbfgs")
