@@ -1,0 +1,384 @@
+#!/usr/bin/env python
+"""Throughput of the batched position-based collocation rollout on B300.
+
+Workload (default): 4096 independent 3D serial chains of 10 capsule links
+with ball joints (exponential-map coordinates), link lengths U[0.5, 1.5],
+masses lognormal(0, 0.3), dt = 0.033, three collocation stages, L-BFGS
+history 8, 100 time steps in one persistent launch captured in a CUDA graph.
+One bench step = one full 100-step rollout of the whole batch from the same
+seeded initial state. Metric: link-steps/s = instances * links * time steps /
+time.
+
+Prints one JSON line (rank 0). See --help for the knobs.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "link-steps/s on 1 B300, batched vs plain; fwd+adjoint rollout ms; % FP64 peak"
+UNIT = "link-steps/s"
+
+# Algorithmic FP64 flops of one objective evaluation, per link and per stage
+# (FMA = 2 flops), counted from the formulas of the residual pass (forward
+# kinematics, seeds of Eq. HOC, wrench, joint contraction) and of the tangent
+# pass (S >= 2); the stage coupling adds 24 S per pass. sincos calls are not
+# counted as flops.
+PRIMAL_FLOPS = {0: 347, 1: 540}    # hinge, ball
+TANGENT_FLOPS = {0: 327, 1: 680}
+ENERGY_FLOPS = 54                   # Eq. EQ energy terms (one stage only)
+COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
+
+
+def flops_per_eval(jtypes, S):
+    per_stage = 0
+    for jt in jtypes:
+        per_stage += PRIMAL_FLOPS[jt] + COUPLING_FLOPS * S
+        if S == 1:
+            per_stage += ENERGY_FLOPS
+        else:
+            per_stage += TANGENT_FLOPS[jt] + COUPLING_FLOPS * S
+    return per_stage * S
+
+
+def lbfgs_flops_per_iter(n, S, m):
+    """Two-loop recursion, preconditioner, dots and updates per iteration."""
+    return S * n * (8 * m + 20 + 2 * 3 + 2 * S)
+
+
+def parse():
+    p = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=3, help="timed bench steps (rollouts)")
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    p.add_argument("--instances", type=int, default=4096)
+    p.add_argument("--links", type=int, default=10)
+    p.add_argument("--timesteps", type=int, default=100)
+    p.add_argument("--max-iter", type=int, default=50, help="L-BFGS iteration cap per time step")
+    p.add_argument("--tol", type=float, default=1e-8)
+    p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-clocks", action="store_true")
+    p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    return p.parse_args()
+
+
+def workload(args, rank=0):
+    from paper_1709_04145_b300 import inputs as I
+    w = I.ball_chains(count=args.instances, n_links=args.links, seed_base=2000 + 17 * rank,
+                      n_steps=args.timesteps)
+    w["max_iter"] = args.max_iter
+    w["tol"] = args.tol
+    return w
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [x.strip() for x in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------------- oracle
+def _oracle_instance(job):
+    """Runs the CPU oracle on one instance (spawned worker)."""
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    spec, b, qp, qc, S, dt, m, tol, max_iter, n_steps = job
+    om = O.OracleModel.from_spec(spec, b)
+    t0 = time.perf_counter()
+    res = om.rollout(S, dt, qp, qc, np.zeros((n_steps, om.n_dof)), "lbfgs", m, tol, max_iter)
+    return time.perf_counter() - t0, res["iters"], res["evals"]
+
+
+def cpu_oracle_rate(w, n_inst, n_steps, budget_s):
+    """Oracle link-steps/s on the host cores over a bounded sample: the first
+    instances of the workload, n_steps time steps each, one process per core
+    (spawn). Returns (rate, cores, sample description)."""
+    import multiprocessing as mp
+    import numpy as np
+    from oracle import oracle as O
+    spec = w["spec"]
+    S, dt = w["stages"], w["dt"]
+    nodes, _ = O.colloc(S)
+    qp = w["q0"] + nodes[0] * dt * w["qd0"]
+    cores = os.cpu_count() or 1
+    jobs = [(spec.select([b]), 0, qp[b], w["q0"][b], S, dt, w["history"], w["tol"], w["max_iter"],
+             n_steps) for b in range(n_inst)]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(min(cores, n_inst)) as pool:
+        res = pool.map(_oracle_instance, jobs)
+    wall = time.perf_counter() - t0
+    link_steps = n_inst * spec.n_links * n_steps
+    sample = (f"{n_inst} of {spec.count} instances x {n_steps} of {w['n_steps']} time steps, "
+              f"same solver settings; {wall:.1f} s wall on {min(cores, n_inst)} processes")
+    return link_steps / wall, min(cores, n_inst), sample
+
+
+# --------------------------------------------------------------------- ours
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1709_04145_b300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    w = workload(args, rank)
+    spec = w["spec"]
+    S, dt, m = w["stages"], w["dt"], w["history"]
+    nodes, _ = P.colloc(S)
+    q_prev0_h = (w["q0"] + nodes[0] * dt * w["qd0"]).reshape(-1)
+    q_cur0_h = w["q0"].reshape(-1)
+    model = P.Model.from_spec(spec, device=local)
+    batch = P.Batch([model], max_stages=S, max_history=m)
+    q_prev0 = torch.tensor(q_prev0_h, device=dev)
+    q_cur0 = torch.tensor(q_cur0_h, device=dev)
+    T = w["n_steps"]
+    out = dict(q_prev=torch.empty(batch.D, dtype=torch.float64, device=dev),
+               q_cur=torch.empty(batch.D, dtype=torch.float64, device=dev),
+               status=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+               iters=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+               evals=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+               traj_prev=None, traj_cur=None)
+
+    def launch():
+        P.rollout(batch, q_prev0, q_cur0, None, T, dt, S, P.LBFGS, m, w["tol"], w["max_iter"],
+                  out=out)
+
+    # one rollout = one persistent kernel, captured in a CUDA graph
+    launch()
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        with torch.cuda.graph(g, stream=s):
+            launch()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)  # > L2
+
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    peak_gflops = P.fp64_peak(local)
+
+    clocks = ClockSampler(local)
+    if not args.no_clocks:
+        clocks.start()
+        time.sleep(0.5)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    cur = torch.cuda.current_stream()
+    for k in range(args.steps):
+        flush.fill_(float(k))  # L2 flush between timed steps (outside the events)
+        ev[k][0].record(cur)
+        g.replay()
+        ev[k][1].record(cur)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    clk = clocks.stop() if not args.no_clocks else None
+    ms = sum(ms_steps) / len(ms_steps)
+    if world > 1:
+        t = torch.tensor([ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = t.item()
+
+    status = out["status"].cpu().numpy()
+    iters = out["iters"].cpu().numpy()
+    evals = out["evals"].cpu().numpy()
+    link_steps = spec.count * spec.n_links * T
+    value = link_steps * world / (ms / 1e3)
+
+    # roofline of the rollout kernel (the only kernel of the timed region)
+    fe = flops_per_eval(spec.jtype.tolist(), S)
+    flops = float(evals.sum()) * fe + float(iters.sum()) * lbfgs_flops_per_iter(spec.n_dof, S, m)
+    achieved = flops / (ms / 1e3) / 1e12
+    peak = peak_gflops / 1e3
+
+    # end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        qp_h = torch.tensor(q_prev0_h).pin_memory()
+        qc_h = torch.tensor(q_cur0_h).pin_memory()
+        res_h = torch.empty(batch.D, dtype=torch.float64).pin_memory()
+        st_h = torch.empty(batch.n_instances, dtype=torch.int32).pin_memory()
+        qp_d = torch.empty_like(q_prev0)
+        qc_d = torch.empty_like(q_cur0)
+        out2 = dict(out)
+        torch.cuda.synchronize()
+        t_e2e = []
+        for k in range(max(args.steps, 1)):
+            flush.fill_(float(k))
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(cur)
+            qp_d.copy_(qp_h, non_blocking=True)
+            qc_d.copy_(qc_h, non_blocking=True)
+            P.rollout(batch, qp_d, qc_d, None, T, dt, S, P.LBFGS, m, w["tol"], w["max_iter"],
+                      out=out2)
+            res_h.copy_(out2["q_cur"], non_blocking=True)
+            st_h.copy_(out2["status"], non_blocking=True)
+            e1.record(cur)
+            torch.cuda.synchronize()
+            t_e2e.append(e0.elapsed_time(e1))
+        ms_e = sum(t_e2e) / len(t_e2e)
+        if world > 1:
+            t = torch.tensor([ms_e], device=dev, dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms_e = t.item()
+        e2e = {"value": link_steps * world / (ms_e / 1e3), "unit": UNIT,
+               "h2d_bytes_per_step": 2 * batch.D * 8,
+               "d2h_bytes_per_step": batch.D * 8 + batch.n_instances * 4,
+               "ms_per_step": ms_e}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded generators; no dataset)",
+        "config": {"workload": f"batched ball-joint capsule chains: {spec.count} x {spec.n_links} "
+                               f"links, dt={dt}, {S} stages, L-BFGS m={m}, {T} steps per rollout, "
+                               "one persistent launch in a CUDA graph",
+                   "instances_per_gpu": spec.count, "links": spec.n_links, "timesteps": T,
+                   "stages": S, "solver": "lbfgs", "history": m, "tol": w["tol"],
+                   "max_iter_per_step": w["max_iter"], "parallelism": f"instances sharded, {world} GPU",
+                   "l2": "flushed between timed steps (512 MB write outside the events)"},
+        "solver_stats": {"converged_fraction": float((status == 0).mean()),
+                         "status_counts": {P.STATUS[k]: int((status == k).sum()) for k in range(5)},
+                         "iters_per_step": float(iters.mean() / T),
+                         "evals_per_step": float(evals.mean() / T)},
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None,
+                     "peak_source": "measured FP64 FMA probe (pbad_fp64_peak) on this GPU",
+                     "flops_per_launch": flops},
+        "gpu_launches": args.steps,
+        "e2e": e2e,
+        "clocks": clk,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        rate, cores, sample = cpu_oracle_rate(w, n_inst=min(os.cpu_count() or 1, 16), n_steps=1,
+                                              budget_s=args.cpu_sample_seconds)
+        line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                "sample": sample}
+    if world > 1:
+        dist.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_reference(args):
+    """The CPU oracle as it stands, on the host cores, same workload."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    w = workload(args)
+    spec = w["spec"]
+    n_inst = min(os.cpu_count() or 1, 16)
+    for _ in range(args.warmup):
+        cpu_oracle_rate(w, n_inst=min(2, n_inst), n_steps=1, budget_s=1)
+    rates = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        r, cores, sample = cpu_oracle_rate(w, n_inst=n_inst, n_steps=1, budget_s=args.cpu_sample_seconds)
+        rates.append(r)
+    wall = time.perf_counter() - t0
+    value = statistics.median(rates)
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": wall * 1e3 / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded generators; no dataset)", "impl": "reference",
+            "config": {"workload": f"batched ball-joint capsule chains: {spec.count} x {spec.n_links} "
+                                   f"links, dt={w['dt']}, {w['stages']} stages, L-BFGS "
+                                   f"m={w['history']}, {w['n_steps']} steps per rollout",
+                       "max_iter_per_step": w["max_iter"], "tol": w["tol"]},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

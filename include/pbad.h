@@ -1,0 +1,165 @@
+/*
+ * pbad.h - C ABI of the B300 position-based articulated dynamics library.
+ *
+ * The method is Pan & Manocha, "Time Integrating Articulated Body Dynamics
+ * Using Position-Based Collocation Methods" (arXiv 1709.04145): every time
+ * step solves for the S = K-1 unknown stage configurations of a K-th order
+ * position-based collocation (Section 4.1) by minimising
+ *   S == 1: the energy of Eq. EQ
+ *             E(q) = sum_l tr(D_l M_l D_l^T)/(2 dt^2) - g.(T_l [mc; m]) - tau.q,
+ *             D_l = T_l(q) - 2 T_l(q_cur) + T_l(q_prev),
+ *   S >= 2: the squared stage residuals of Eq. EQHOC, E = sum_i |r_i|^2, with
+ *             r_i = int dP(q_i)/dq_i^T [rho Pddot(t_i) - f] dp - tau  (Eq. HOC)
+ * using L-BFGS or Newton (Levenberg-Marquardt), Section 5.
+ *
+ * Conventions shared by every entry point:
+ *   - Links l = 0..N-1 are topologically sorted: parent[l] < l, -1 = world.
+ *     The link frame origin is at its joint; T_l = T_parent * X_l * Rot(q_l)
+ *     with X_l the 3x4 rest transform (row-major) and Rot a hinge rotation
+ *     about a unit axis of the joint frame (1 DOF) or the exponential map of
+ *     a 3-vector (ball, 3 DOF). Generalised torques tau are conjugate to q.
+ *   - A model is one topology with `count` instances; each instance has its
+ *     own mass moments and rest transforms. A batch is an ordered list of
+ *     models (buckets of an uneven batch).
+ *   - DOF-packed arrays (q, tau, ...) hold, model after model, `count` rows
+ *     of that model's n DOFs: row-major [instance][dof] within each model
+ *     block. Their total length is D = sum_m count_m * n_m.
+ *   - Stage-packed arrays hold, model after model, [instance][stage][dof]:
+ *     total length S * D.
+ *   - Per-instance arrays (E, status, iters) hold one entry per instance in
+ *     batch order.
+ *   - Collocation nodes (units of dt, relative to t_k) are
+ *     [k-1+alpha_{S-1}, k, k+alpha_1, ..., k+alpha_S], alpha_S = 1 and
+ *     alpha_1..alpha_{S-1} the roots of L_{S-1}(2 alpha - 1). A step maps the
+ *     state (q_prev at node k-1+alpha_{S-1}, q_cur at node k) to
+ *     (stage S-1 (q_cur when S == 1), stage S).
+ *   - All array arguments of the compute entry points are DEVICE pointers on
+ *     the batch's device, owned by the caller, and must not alias outputs.
+ *     Model set-up arrays are HOST pointers (copied). `stream` is a
+ *     cudaStream_t (NULL = legacy default stream). The compute entry points
+ *     only enqueue work: they allocate nothing, never synchronise the host and
+ *     may be captured in a CUDA graph.
+ *   - Every function returns PBAD_OK (0) or a negative PBAD_ERR_* code and
+ *     then pbad_last_error() describes the failure (thread-local). Nothing
+ *     aborts or throws across the ABI. Per-instance solver outcomes are
+ *     reported through `status` (PBAD_CONVERGED ...), never as return codes.
+ */
+#ifndef PBAD_H
+#define PBAD_H
+
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define PBAD_API __attribute__((visibility("default")))
+#else
+#define PBAD_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PBAD_OK 0
+#define PBAD_ERR_ARG (-1)         /* invalid argument (null, size, range) */
+#define PBAD_ERR_CUDA (-2)        /* a CUDA runtime call failed */
+#define PBAD_ERR_ALLOC (-3)       /* device or host allocation failed */
+#define PBAD_ERR_UNSUPPORTED (-4) /* valid request outside what is built */
+
+#define PBAD_HINGE 0
+#define PBAD_BALL 1
+
+#define PBAD_LBFGS 0
+#define PBAD_NEWTON 1
+
+/* per-instance solver status (the worst over the steps of a rollout) */
+#define PBAD_CONVERGED 0  /* |r|_2 < tol */
+#define PBAD_MAX_ITER 1   /* iteration cap reached */
+#define PBAD_LS_FAIL 2    /* line search / damping could not decrease E */
+#define PBAD_CHOL_FAIL 3  /* Newton system not factorable for any damping */
+#define PBAD_NONFINITE 4  /* NaN or Inf in E, r or the gradient */
+
+#define PBAD_MAX_STAGES 5
+#define PBAD_MAX_HISTORY 16
+#define PBAD_MAX_MODELS 8
+
+typedef struct pbad_model pbad_model;
+typedef struct pbad_batch pbad_batch;
+
+/* Library version (major*10000 + minor*100 + patch). */
+PBAD_API int pbad_version(void);
+
+/* Message of the last failed call on this thread ("" if none). */
+PBAD_API const char* pbad_last_error(void);
+
+/* Collocation table of Section 4.1 for S stages (1..PBAD_MAX_STAGES):
+ * nodes[S+2] as documented above; W[S][S+2] row-major, W[i][j] = l_j''(node
+ * of stage i) of the Lagrange basis over all S+2 nodes, in units of 1/dt^2.
+ * Host pointers. */
+PBAD_API int pbad_colloc(int32_t stages, double* nodes, double* W);
+
+/* Creates a model (one topology, `count` instances) on CUDA device `device`.
+ *   parent[n_links], joint_type[n_links] (PBAD_HINGE/PBAD_BALL),
+ *   axis[n_links][3] (hinge axes in the joint frame, unit length; ignored for
+ *   balls), mass_moment[count][n_links][10] = Sxx Sxy Sxz Syy Syz Szz mcx mcy
+ *   mcz m of int rho [p;1][p;1]^T dp in the link frame (Eq. ATOM),
+ *   rest[count][n_links][12] (3x4 row-major), gravity[3].
+ * All host pointers, copied. Errors: PBAD_ERR_ARG for a malformed tree,
+ * unknown joint type, non-positive sizes or n_links > 4096. */
+PBAD_API int pbad_model_create(int32_t n_links, const int32_t* parent, const int32_t* joint_type,
+                      const double* axis, int64_t count, const double* mass_moment,
+                      const double* rest, const double* gravity, int32_t device,
+                      pbad_model** out);
+PBAD_API int pbad_model_destroy(pbad_model* model);
+PBAD_API int pbad_model_info(const pbad_model* model, int32_t* n_links, int32_t* n_dof, int64_t* count);
+
+/* Creates a batch over 1..PBAD_MAX_MODELS models (same device) and allocates
+ * the solver workspace for up to max_stages stages and L-BFGS history
+ * max_history. The models must outlive the batch. */
+PBAD_API int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_stages,
+                      int32_t max_history, pbad_batch** out);
+PBAD_API int pbad_batch_destroy(pbad_batch* batch);
+/* n_instances = sum count_m; n_dof_total = D; workspace_bytes = device bytes
+ * the batch owns. Any output pointer may be NULL. */
+PBAD_API int pbad_batch_info(const pbad_batch* batch, int64_t* n_instances, int64_t* n_dof_total,
+                    int64_t* workspace_bytes);
+
+/* Objective and gradient of one step at given stage configurations
+ * (Eq. EQ / Eq. EQHOC; gradient by Algorithm DERIV in world coordinates and,
+ * for S >= 2, its tangent sweep: grad = 2 Jr^T r in O(N)).
+ *   q_star[S*D] stage-packed, q_prev[D], q_cur[D], tau[D] (NULL = zero),
+ *   E[instances], grad[S*D], resid[S*D] (stage residuals r_i; NULL = skip).
+ */
+PBAD_API int pbad_eval_objective_grad(pbad_batch* batch, const double* q_star, const double* q_prev,
+                             const double* q_cur, const double* tau, double dt, int32_t stages,
+                             double* E, double* grad, double* resid, void* stream);
+
+/* One time step for every instance: q_prev'/q_cur' [D] (either may be NULL),
+ * q_stages_out[S*D] (NULL = skip), status/iters [instances] (NULL = skip).
+ * solvers[n_models] (host, NULL = all PBAD_LBFGS); history <= max_history;
+ * tol is the bound on |r|_2 (r = dE/dq for S == 1); max_iter >= 0. */
+PBAD_API int pbad_step(pbad_batch* batch, const double* q_prev, const double* q_cur, const double* tau,
+              double dt, int32_t stages, const int32_t* solvers, int32_t history, double tol,
+              int32_t max_iter, double* q_prev_out, double* q_cur_out, double* q_stages_out,
+              int32_t* status, int32_t* iters, void* stream);
+
+/* n_steps steps in one persistent launch. tau_seq[n_steps][D] (NULL = zero),
+ * traj_prev/traj_cur [n_steps][D] the state after each step (NULL = skip),
+ * q_prev_out/q_cur_out [D] the final state (NULL = skip), status = worst
+ * status over the steps, iters = total accepted iterations, evals = total
+ * objective/gradient evaluations (line-search trials included); each of
+ * status/iters/evals [instances] may be NULL. */
+PBAD_API int pbad_rollout(pbad_batch* batch, const double* q_prev0, const double* q_cur0,
+                 const double* tau_seq, int32_t n_steps, double dt, int32_t stages,
+                 const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
+                 double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
+                 int32_t* status, int32_t* iters, int32_t* evals, void* stream);
+
+/* Measures the device's FP64 FMA throughput (GFLOP/s, FMA = 2 flops) with
+ * the library's own probe kernel; synchronises the device. */
+PBAD_API int pbad_fp64_peak(int32_t device, double* gflops);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PBAD_H */

@@ -1,0 +1,226 @@
+"""B300-native position-based articulated dynamics (Pan & Manocha, arXiv
+1709.04145): Python front end of the CUDA library ``libpbad.so``.
+
+Every step of the hot path runs in the library's kernels; this module only
+marshals arguments (PyTorch tensors for device memory and streams). Importing
+the package does not load the library; the first call does, and fails loudly
+if it has not been built.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import inputs
+from ._native import PBADError, check, lib
+
+__all__ = ["Model", "Batch", "colloc", "eval_objective_grad", "step", "rollout", "fp64_peak",
+           "PBADError", "LBFGS", "NEWTON", "STATUS", "inputs"]
+
+LBFGS = 0
+NEWTON = 1
+STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE"}
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int32))
+
+
+def _tptr(t):
+    """Device pointer of a CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("arrays must be contiguous CUDA tensors")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream(stream):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return C.c_void_p(s.cuda_stream)
+
+
+def colloc(stages: int):
+    """(nodes (S+2,), W (S, S+2)) from the library's own table."""
+    nodes = np.zeros(stages + 2)
+    W = np.zeros((stages, stages + 2))
+    check(lib().pbad_colloc(stages, _dptr(nodes), _dptr(W)), "pbad_colloc")
+    return nodes, W
+
+
+def fp64_peak(device: int = 0) -> float:
+    """Measured FP64 FMA throughput of the device, GFLOP/s."""
+    out = C.c_double(0)
+    check(lib().pbad_fp64_peak(device, C.byref(out)), "pbad_fp64_peak")
+    return out.value
+
+
+class Model:
+    """One topology with ``count`` instances (pbad_model)."""
+
+    def __init__(self, parent, jtype, axis, mass_moment, rest, gravity, device: int = 0):
+        parent = np.ascontiguousarray(parent, dtype=np.int32)
+        jtype = np.ascontiguousarray(jtype, dtype=np.int32)
+        axis = np.ascontiguousarray(axis, dtype=np.float64).reshape(-1, 3)
+        N = parent.shape[0]
+        mass_moment = np.ascontiguousarray(mass_moment, dtype=np.float64).reshape(-1, N, 10)
+        rest = np.ascontiguousarray(rest, dtype=np.float64).reshape(-1, N, 12)
+        gravity = np.ascontiguousarray(gravity, dtype=np.float64).reshape(3)
+        count = mass_moment.shape[0]
+        if rest.shape[0] != count:
+            raise ValueError("mass_moment and rest disagree on the instance count")
+        h = C.c_void_p()
+        check(lib().pbad_model_create(N, _iptr(parent), _iptr(jtype), _dptr(axis), count,
+                                      _dptr(mass_moment), _dptr(rest), _dptr(gravity), device,
+                                      C.byref(h)), "pbad_model_create")
+        self._h = h
+        self.n_links = N
+        self.count = count
+        self.device = device
+        nl, nd, cnt = C.c_int32(), C.c_int32(), C.c_int64()
+        check(lib().pbad_model_info(h, C.byref(nl), C.byref(nd), C.byref(cnt)), "pbad_model_info")
+        self.n_dof = nd.value
+
+    @classmethod
+    def from_spec(cls, spec: "inputs.BodySpec", device: int = 0) -> "Model":
+        from .models import mass_moments, rest_transforms
+        return cls(spec.parent, spec.jtype, spec.axis, mass_moments(spec), rest_transforms(spec),
+                   spec.gravity, device)
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().pbad_model_destroy(h)
+            self._h = None
+
+
+class Batch:
+    """An ordered list of models with solver workspace (pbad_batch).
+
+    DOF-packed tensors have length D (models concatenated, each [count][n]);
+    use ``pack``/``unpack`` to convert from/to per-model (count, n) arrays.
+    """
+
+    def __init__(self, models, max_stages: int = 5, max_history: int = 16):
+        self.models = list(models)
+        arr = (C.c_void_p * len(self.models))(*[m._h for m in self.models])
+        h = C.c_void_p()
+        check(lib().pbad_batch_create(len(self.models), arr, max_stages, max_history, C.byref(h)),
+              "pbad_batch_create")
+        self._h = h
+        self.max_stages = max_stages
+        self.max_history = max_history
+        ni, nd, wb = C.c_int64(), C.c_int64(), C.c_int64()
+        check(lib().pbad_batch_info(h, C.byref(ni), C.byref(nd), C.byref(wb)), "pbad_batch_info")
+        self.n_instances = ni.value
+        self.D = nd.value
+        self.workspace_bytes = wb.value
+        self.device = self.models[0].device
+        self.dof_off = np.cumsum([0] + [m.count * m.n_dof for m in self.models])
+        self.inst_off = np.cumsum([0] + [m.count for m in self.models])
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().pbad_batch_destroy(h)
+            self._h = None
+
+    def pack(self, per_model, stages: int = 0):
+        """Concatenates per-model arrays (count, n) (or (count, S, n)) into one
+        flat array (numpy or torch, whatever was given)."""
+        flats = [a.reshape(-1) for a in per_model]
+        if hasattr(flats[0], "detach"):
+            import torch
+            return torch.cat(flats).contiguous()
+        return np.concatenate(flats)
+
+    def unpack(self, flat, stages: int = 0):
+        """Splits a DOF- or stage-packed flat array into per-model views."""
+        out = []
+        mult = max(stages, 1)
+        for k, m in enumerate(self.models):
+            a, b = self.dof_off[k] * mult, self.dof_off[k + 1] * mult
+            shape = (m.count, stages, m.n_dof) if stages else (m.count, m.n_dof)
+            out.append(flat[a:b].reshape(shape))
+        return out
+
+
+def _solvers(batch: Batch, solvers):
+    if solvers is None:
+        return None
+    if isinstance(solvers, int):
+        solvers = [solvers] * len(batch.models)
+    arr = np.ascontiguousarray(solvers, dtype=np.int32)
+    if arr.shape[0] != len(batch.models):
+        raise ValueError("one solver per model")
+    return arr
+
+
+def eval_objective_grad(batch: Batch, q_star, q_prev, q_cur, tau, dt: float, stages: int,
+                        want_resid: bool = True, stream=None):
+    """Objective E (per instance), dE/dq_* (stage-packed) and the stage
+    residuals r (stage-packed) at the given stage configurations."""
+    import torch
+    dev = q_star.device
+    E = torch.empty(batch.n_instances, dtype=torch.float64, device=dev)
+    grad = torch.empty(stages * batch.D, dtype=torch.float64, device=dev)
+    resid = torch.empty_like(grad) if want_resid else None
+    check(lib().pbad_eval_objective_grad(batch._h, _tptr(q_star), _tptr(q_prev), _tptr(q_cur),
+                                         _tptr(tau), float(dt), int(stages), _tptr(E),
+                                         _tptr(grad), _tptr(resid), _stream(stream)),
+          "pbad_eval_objective_grad")
+    return E, grad, resid
+
+
+def step(batch: Batch, q_prev, q_cur, tau, dt: float, stages: int, solver=LBFGS,
+         history: int = 8, tol: float = 1e-10, max_iter: int = 1000, stream=None):
+    """One time step. Returns dict(q_prev, q_cur, q_stages, status, iters)."""
+    import torch
+    dev = q_prev.device
+    qp = torch.empty(batch.D, dtype=torch.float64, device=dev)
+    qc = torch.empty_like(qp)
+    qs = torch.empty(stages * batch.D, dtype=torch.float64, device=dev)
+    st = torch.empty(batch.n_instances, dtype=torch.int32, device=dev)
+    it = torch.empty_like(st)
+    sv = _solvers(batch, solver)
+    check(lib().pbad_step(batch._h, _tptr(q_prev), _tptr(q_cur), _tptr(tau), float(dt),
+                          int(stages), _iptr(sv) if sv is not None else None, int(history),
+                          float(tol), int(max_iter), _tptr(qp), _tptr(qc), _tptr(qs), _tptr(st),
+                          _tptr(it), _stream(stream)), "pbad_step")
+    return dict(q_prev=qp, q_cur=qc, q_stages=qs, status=st, iters=it)
+
+
+def rollout(batch: Batch, q_prev0, q_cur0, tau_seq, n_steps: int, dt: float, stages: int,
+            solver=LBFGS, history: int = 8, tol: float = 1e-10, max_iter: int = 1000,
+            want_traj: bool = True, out=None, stream=None):
+    """n_steps steps in one persistent launch. tau_seq: (n_steps*D) or None.
+    Returns dict(traj_prev, traj_cur (n_steps, D) or None, q_prev, q_cur,
+    status, iters, evals). ``out`` may supply preallocated output tensors (same keys)
+    so that the call allocates nothing (e.g. inside a CUDA graph)."""
+    import torch
+    dev = q_cur0.device
+    if out is None:
+        out = dict(q_prev=torch.empty(batch.D, dtype=torch.float64, device=dev),
+                   q_cur=torch.empty(batch.D, dtype=torch.float64, device=dev),
+                   status=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+                   iters=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+                   evals=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+                   traj_prev=None, traj_cur=None)
+        if want_traj:
+            out["traj_prev"] = torch.empty((n_steps, batch.D), dtype=torch.float64, device=dev)
+            out["traj_cur"] = torch.empty((n_steps, batch.D), dtype=torch.float64, device=dev)
+    sv = _solvers(batch, solver)
+    check(lib().pbad_rollout(batch._h, _tptr(q_prev0), _tptr(q_cur0), _tptr(tau_seq),
+                             int(n_steps), float(dt), int(stages),
+                             _iptr(sv) if sv is not None else None, int(history), float(tol),
+                             int(max_iter), _tptr(out.get("traj_prev")),
+                             _tptr(out.get("traj_cur")), _tptr(out["q_prev"]),
+                             _tptr(out["q_cur"]), _tptr(out["status"]), _tptr(out["iters"]),
+                             _tptr(out.get("evals")), _stream(stream)), "pbad_rollout")
+    return out

@@ -1,0 +1,563 @@
+// C ABI of the PBAD library (declarations and contracts: include/pbad.h).
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/pbad.h"
+#include "pbad_kernels.cuh"
+
+namespace pbad {
+#define PBAD_DECL(S)                                                                \
+  cudaError_t launch_eval_s##S(const LaunchArgs& A, int grid, cudaStream_t s);     \
+  cudaError_t launch_rollout_s##S(const LaunchArgs& A, int grid, cudaStream_t s);
+PBAD_DECL(1)
+PBAD_DECL(2)
+PBAD_DECL(3)
+PBAD_DECL(4)
+PBAD_DECL(5)
+cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters);
+
+cudaError_t launch_eval(int S, const LaunchArgs& A, int grid, cudaStream_t s) {
+  switch (S) {
+    case 1: return launch_eval_s1(A, grid, s);
+    case 2: return launch_eval_s2(A, grid, s);
+    case 3: return launch_eval_s3(A, grid, s);
+    case 4: return launch_eval_s4(A, grid, s);
+    case 5: return launch_eval_s5(A, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_rollout(int S, const LaunchArgs& A, int grid, cudaStream_t s) {
+  switch (S) {
+    case 1: return launch_rollout_s1(A, grid, s);
+    case 2: return launch_rollout_s2(A, grid, s);
+    case 3: return launch_rollout_s3(A, grid, s);
+    case 4: return launch_rollout_s4(A, grid, s);
+    case 5: return launch_rollout_s5(A, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+}  // namespace pbad
+
+using namespace pbad;
+
+struct pbad_model {
+  int N = 0, n = 0, device = 0;
+  int64_t count = 0;
+  std::vector<int> parent, jtype, dof;
+  double g[3] = {0, 0, 0};
+  int* d_topo = nullptr;     // parent[N] | jtype[N] | dof[N]
+  double* d_axis = nullptr;  // [N][3]
+  double* d_mm = nullptr;    // [N][10][count]
+  double* d_rest = nullptr;  // [N][12][count]
+};
+
+struct pbad_batch {
+  int device = 0, max_stages = 0, max_history = 0;
+  std::vector<pbad_model*> models;
+  std::vector<int64_t> inst_off, dof_off, lanes;
+  std::vector<size_t> ws_off;  // in doubles
+  int64_t n_inst = 0, D = 0;
+  double* d_ws = nullptr;
+  size_t ws_doubles = 0;
+};
+
+namespace {
+
+thread_local std::string g_err;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(PBAD_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) ok = cudaSetDevice(dev) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// Legendre roots on [-1, 1] in closed form (degrees 0..4).
+void legendre(int deg, double* x) {
+  switch (deg) {
+    case 1: x[0] = 0.0; break;
+    case 2: x[0] = -1.0 / std::sqrt(3.0); x[1] = -x[0]; break;
+    case 3: x[0] = -std::sqrt(0.6); x[1] = 0.0; x[2] = -x[0]; break;
+    case 4: {
+      const double a = std::sqrt(3.0 / 7.0 - 2.0 / 7.0 * std::sqrt(1.2));
+      const double b = std::sqrt(3.0 / 7.0 + 2.0 / 7.0 * std::sqrt(1.2));
+      x[0] = -b; x[1] = -a; x[2] = a; x[3] = b;
+      break;
+    }
+    default: break;
+  }
+}
+
+// nodes[S+2] and W[S][S+2] (1/dt^2 units): second derivative of the Lagrange
+// basis polynomial l_j at stage node t_i, by the product rule:
+//   l_j''(t) = sum_{a != j} sum_{b != j, a} prod_{p != j, a, b} (t - x_p)
+//              / prod_{p != j} (x_j - x_p).
+int colloc_table(int S, double* nodes, double* W) {
+  if (S < 1 || S > kMaxStages) return -1;
+  double alpha[kMaxStages + 1];
+  double r[kMaxStages];
+  legendre(S - 1, r);
+  alpha[0] = 0.0;
+  for (int k = 1; k < S; ++k) alpha[k] = 0.5 * (r[k - 1] + 1.0);
+  alpha[S] = 1.0;
+  const int P = S + 2;
+  nodes[0] = alpha[S - 1] - 1.0;
+  nodes[1] = 0.0;
+  for (int k = 1; k <= S; ++k) nodes[1 + k] = alpha[k];
+  for (int i = 0; i < S; ++i) {
+    const double t = nodes[2 + i];
+    for (int j = 0; j < P; ++j) {
+      double den = 1.0;
+      for (int p = 0; p < P; ++p)
+        if (p != j) den *= nodes[j] - nodes[p];
+      double num = 0.0;
+      for (int a = 0; a < P; ++a) {
+        if (a == j) continue;
+        for (int b = 0; b < P; ++b) {
+          if (b == j || b == a) continue;
+          double pr = 1.0;
+          for (int p = 0; p < P; ++p)
+            if (p != j && p != a && p != b) pr *= t - nodes[p];
+          num += pr;
+        }
+      }
+      W[i * P + j] = num / den;
+    }
+  }
+  return 0;
+}
+
+// Gauss-Jordan inverse of a small dense matrix (n <= kMaxStages).
+bool small_inverse(int n, const double* A_, double* X) {
+  double A[kMaxStages * kMaxStages];
+  std::memcpy(A, A_, sizeof(double) * n * n);
+  for (int r = 0; r < n; ++r)
+    for (int c = 0; c < n; ++c) X[r * n + c] = (r == c) ? 1.0 : 0.0;
+  for (int c = 0; c < n; ++c) {
+    int piv = c;
+    for (int r = c + 1; r < n; ++r)
+      if (std::fabs(A[r * n + c]) > std::fabs(A[piv * n + c])) piv = r;
+    if (A[piv * n + c] == 0.0) return false;
+    for (int k = 0; k < n; ++k) {
+      std::swap(A[c * n + k], A[piv * n + k]);
+      std::swap(X[c * n + k], X[piv * n + k]);
+    }
+    const double d = A[c * n + c];
+    for (int k = 0; k < n; ++k) {
+      A[c * n + k] /= d;
+      X[c * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == c) continue;
+      const double f = A[r * n + c];
+      for (int k = 0; k < n; ++k) {
+        A[r * n + k] -= f * A[c * n + k];
+        X[r * n + k] -= f * X[c * n + k];
+      }
+    }
+  }
+  return true;
+}
+
+int make_colloc(int S, double dt, Colloc* K) {
+  double nodes[kMaxStages + 2], W[kMaxStages * (kMaxStages + 2)];
+  if (colloc_table(S, nodes, W) != 0) return fail(PBAD_ERR_ARG, "stages out of range");
+  std::memset(K, 0, sizeof(Colloc));
+  K->S = S;
+  K->dt = dt;
+  const int P = S + 2;
+  const double idt2 = 1.0 / (dt * dt);
+  for (int k = 0; k < P; ++k) K->nodes[k] = nodes[k];
+  for (int i = 0; i < S; ++i) {
+    K->Wk[i][0] = W[i * P + 0] * idt2;
+    K->Wk[i][1] = W[i * P + 1] * idt2;
+    for (int j = 0; j < S; ++j) K->Wu[i][j] = W[i * P + 2 + j] * idt2;
+  }
+  // stage block of the L-BFGS initial inverse Hessian:
+  //   S == 1: dt^2; S >= 2: (Wu^T Wu)^-1 / 2
+  if (S == 1) {
+    K->Ps[0][0] = dt * dt;
+  } else {
+    double G[kMaxStages * kMaxStages], X[kMaxStages * kMaxStages];
+    for (int a = 0; a < S; ++a)
+      for (int b = 0; b < S; ++b) {
+        double s = 0;
+        for (int i = 0; i < S; ++i) s += K->Wu[i][a] * K->Wu[i][b];
+        G[a * S + b] = s;
+      }
+    if (!small_inverse(S, G, X)) return fail(PBAD_ERR_ARG, "singular collocation block");
+    for (int a = 0; a < S; ++a)
+      for (int b = 0; b < S; ++b) K->Ps[a][b] = 0.5 * X[a * S + b];
+  }
+  return PBAD_OK;
+}
+
+int groups_per_warp(int S) { return 32 / S; }
+
+int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int history,
+                LaunchArgs* A, int* grid) {
+  std::memset(A, 0, sizeof(LaunchArgs));
+  int rc = make_colloc(S, dt, &A->K);
+  if (rc != PBAD_OK) return rc;
+  A->nb = (int)bt->models.size();
+  A->D = bt->D;
+  A->history = history;
+  int blocks = 0;
+  for (int k = 0; k < A->nb; ++k) {
+    const pbad_model* m = bt->models[k];
+    Bucket& B = A->bk[k];
+    B.N = m->N;
+    B.n = m->n;
+    B.count = (int)m->count;
+    B.parent = m->d_topo;
+    B.jtype = m->d_topo + m->N;
+    B.dof = m->d_topo + 2 * m->N;
+    B.axis = m->d_axis;
+    B.mm = m->d_mm;
+    B.rest = m->d_rest;
+    for (int c = 0; c < 3; ++c) B.g[c] = m->g[c];
+    B.inst_off = bt->inst_off[k];
+    B.dof_off = bt->dof_off[k];
+    B.ws = bt->d_ws + bt->ws_off[k];
+    B.ws_stride = bt->lanes[k];
+    B.block_begin = blocks;
+    B.solver = solvers ? solvers[k] : PBAD_LBFGS;
+    const int64_t warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
+    blocks += (int)((warps + 3) / 4);
+  }
+  *grid = blocks;
+  return PBAD_OK;
+}
+
+
+int check_common(pbad_batch* bt, int32_t stages, double dt) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (stages < 1 || stages > bt->max_stages)
+    return fail(PBAD_ERR_ARG, "stages must be in 1..max_stages of the batch");
+  if (!(dt > 0.0) || !std::isfinite(dt)) return fail(PBAD_ERR_ARG, "dt must be positive and finite");
+  return PBAD_OK;
+}
+
+int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
+                 const double* tau_seq, int32_t n_steps, double dt, int32_t stages,
+                 const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
+                 double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
+                 double* q_stages_out, int32_t* status, int32_t* iters, int32_t* evals,
+                 void* stream) {
+  int rc = check_common(bt, stages, dt);
+  if (rc != PBAD_OK) return rc;
+  if (!q_prev0 || !q_cur0) return fail(PBAD_ERR_ARG, "null state");
+  if (n_steps < 1) return fail(PBAD_ERR_ARG, "n_steps must be positive");
+  if (history < 0 || history > bt->max_history)
+    return fail(PBAD_ERR_ARG, "history must be in 0..max_history of the batch");
+  if (max_iter < 0) return fail(PBAD_ERR_ARG, "max_iter must be >= 0");
+  if (!(tol >= 0.0)) return fail(PBAD_ERR_ARG, "tol must be >= 0");
+  for (size_t k = 0; k < bt->models.size(); ++k) {
+    const int sv = solvers ? solvers[k] : PBAD_LBFGS;
+    if (sv == PBAD_NEWTON) return fail(PBAD_ERR_UNSUPPORTED, "Newton solver not built");
+    if (sv != PBAD_LBFGS) return fail(PBAD_ERR_ARG, "unknown solver");
+  }
+  DeviceGuard dg(bt->device);
+  LaunchArgs A;
+  int grid = 0;
+  rc = fill_launch(bt, stages, dt, solvers, history, &A, &grid);
+  if (rc != PBAD_OK) return rc;
+  A.q_prev0 = q_prev0;
+  A.q_cur0 = q_cur0;
+  A.tau = tau_seq;
+  A.n_steps = n_steps;
+  A.tol = tol;
+  A.max_iter = max_iter;
+  A.traj_prev = traj_prev;
+  A.traj_cur = traj_cur;
+  A.q_prev_out = q_prev_out;
+  A.q_cur_out = q_cur_out;
+  A.q_stages_out = q_stages_out;
+  A.status = status;
+  A.iters = iters;
+  A.evals = evals;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaError_t e = launch_rollout(stages, A, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
+  return PBAD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int pbad_version(void) { return 100; }
+
+const char* pbad_last_error(void) { return g_err.c_str(); }
+
+int pbad_colloc(int32_t stages, double* nodes, double* W) {
+  if (!nodes || !W) return fail(PBAD_ERR_ARG, "null output");
+  if (colloc_table(stages, nodes, W) != 0) return fail(PBAD_ERR_ARG, "stages out of range");
+  return PBAD_OK;
+}
+
+int pbad_model_create(int32_t n_links, const int32_t* parent, const int32_t* joint_type,
+                      const double* axis, int64_t count, const double* mass_moment,
+                      const double* rest, const double* gravity, int32_t device,
+                      pbad_model** out) {
+  if (!out) return fail(PBAD_ERR_ARG, "null out");
+  *out = nullptr;
+  if (n_links <= 0 || n_links > 4096) return fail(PBAD_ERR_ARG, "n_links must be in 1..4096");
+  if (count <= 0 || count > (int64_t)1 << 30) return fail(PBAD_ERR_ARG, "count must be in 1..2^30");
+  if (!parent || !joint_type || !axis || !mass_moment || !rest || !gravity)
+    return fail(PBAD_ERR_ARG, "null model array");
+  auto* m = new (std::nothrow) pbad_model();
+  if (!m) return fail(PBAD_ERR_ALLOC, "host allocation");
+  m->N = n_links;
+  m->count = count;
+  m->device = device;
+  int off = 0;
+  for (int l = 0; l < n_links; ++l) {
+    if (parent[l] < -1 || parent[l] >= l) {
+      delete m;
+      return fail(PBAD_ERR_ARG, "parent[l] must be in -1..l-1");
+    }
+    if (joint_type[l] != PBAD_HINGE && joint_type[l] != PBAD_BALL) {
+      delete m;
+      return fail(PBAD_ERR_ARG, "unknown joint type");
+    }
+    m->parent.push_back(parent[l]);
+    m->jtype.push_back(joint_type[l]);
+    m->dof.push_back(off);
+    off += joint_type[l] == PBAD_HINGE ? 1 : 3;
+  }
+  m->n = off;
+  for (int c = 0; c < 3; ++c) m->g[c] = gravity[c];
+  DeviceGuard dg(device);
+  if (!dg.ok) {
+    delete m;
+    return fail(PBAD_ERR_CUDA, "cudaSetDevice failed");
+  }
+  std::vector<int> topo(3 * n_links);
+  for (int l = 0; l < n_links; ++l) {
+    topo[l] = m->parent[l];
+    topo[n_links + l] = m->jtype[l];
+    topo[2 * n_links + l] = m->dof[l];
+  }
+  // SoA over instances: [l][k][instance]
+  std::vector<double> mm((size_t)n_links * 10 * count), rs((size_t)n_links * 12 * count);
+  for (int64_t b = 0; b < count; ++b)
+    for (int l = 0; l < n_links; ++l) {
+      for (int k = 0; k < 10; ++k)
+        mm[((size_t)l * 10 + k) * count + b] = mass_moment[((size_t)b * n_links + l) * 10 + k];
+      for (int k = 0; k < 12; ++k)
+        rs[((size_t)l * 12 + k) * count + b] = rest[((size_t)b * n_links + l) * 12 + k];
+    }
+  cudaError_t e;
+  if ((e = cudaMalloc(&m->d_topo, sizeof(int) * topo.size())) != cudaSuccess ||
+      (e = cudaMalloc(&m->d_axis, sizeof(double) * 3 * n_links)) != cudaSuccess ||
+      (e = cudaMalloc(&m->d_mm, sizeof(double) * mm.size())) != cudaSuccess ||
+      (e = cudaMalloc(&m->d_rest, sizeof(double) * rs.size())) != cudaSuccess) {
+    pbad_model_destroy(m);
+    return fail(PBAD_ERR_ALLOC, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  if ((e = cudaMemcpy(m->d_topo, topo.data(), sizeof(int) * topo.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(m->d_axis, axis, sizeof(double) * 3 * n_links, cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(m->d_mm, mm.data(), sizeof(double) * mm.size(), cudaMemcpyHostToDevice)) != cudaSuccess ||
+      (e = cudaMemcpy(m->d_rest, rs.data(), sizeof(double) * rs.size(), cudaMemcpyHostToDevice)) != cudaSuccess) {
+    pbad_model_destroy(m);
+    return cuda_fail(e, "cudaMemcpy");
+  }
+  *out = m;
+  return PBAD_OK;
+}
+
+int pbad_model_destroy(pbad_model* m) {
+  if (!m) return PBAD_OK;
+  DeviceGuard dg(m->device);
+  cudaFree(m->d_topo);
+  cudaFree(m->d_axis);
+  cudaFree(m->d_mm);
+  cudaFree(m->d_rest);
+  delete m;
+  return PBAD_OK;
+}
+
+int pbad_model_info(const pbad_model* m, int32_t* n_links, int32_t* n_dof, int64_t* count) {
+  if (!m) return fail(PBAD_ERR_ARG, "null model");
+  if (n_links) *n_links = m->N;
+  if (n_dof) *n_dof = m->n;
+  if (count) *count = m->count;
+  return PBAD_OK;
+}
+
+int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_stages,
+                      int32_t max_history, pbad_batch** out) {
+  if (!out) return fail(PBAD_ERR_ARG, "null out");
+  *out = nullptr;
+  if (n_models < 1 || n_models > PBAD_MAX_MODELS || !models)
+    return fail(PBAD_ERR_ARG, "n_models must be in 1..PBAD_MAX_MODELS");
+  if (max_stages < 1 || max_stages > PBAD_MAX_STAGES)
+    return fail(PBAD_ERR_ARG, "max_stages must be in 1..PBAD_MAX_STAGES");
+  if (max_history < 0 || max_history > PBAD_MAX_HISTORY)
+    return fail(PBAD_ERR_ARG, "max_history must be in 0..PBAD_MAX_HISTORY");
+  auto* bt = new (std::nothrow) pbad_batch();
+  if (!bt) return fail(PBAD_ERR_ALLOC, "host allocation");
+  bt->max_stages = max_stages;
+  bt->max_history = max_history;
+  size_t ws = 0;
+  for (int k = 0; k < n_models; ++k) {
+    pbad_model* m = models[k];
+    if (!m) {
+      delete bt;
+      return fail(PBAD_ERR_ARG, "null model in batch");
+    }
+    if (k > 0 && m->device != bt->device) {
+      delete bt;
+      return fail(PBAD_ERR_ARG, "models of a batch must share one device");
+    }
+    bt->device = m->device;
+    bt->models.push_back(m);
+    bt->inst_off.push_back(bt->n_inst);
+    bt->dof_off.push_back(bt->D);
+    bt->n_inst += m->count;
+    bt->D += m->count * m->n;
+    // the widest lane layout over the admissible stage counts
+    int64_t lanes = 0;
+    for (int S = 1; S <= max_stages; ++S) {
+      const int64_t warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
+      const int64_t l = ((warps + 3) / 4) * 4 * 32;
+      if (l > lanes) lanes = l;
+    }
+    WsLayout L;
+    L.make(m->N, m->n, max_history);
+    bt->lanes.push_back(lanes);
+    bt->ws_off.push_back(ws);
+    ws += (size_t)lanes * L.total;
+  }
+  DeviceGuard dg(bt->device);
+  bt->ws_doubles = ws;
+  cudaError_t e = cudaMalloc(&bt->d_ws, sizeof(double) * ws);
+  if (e != cudaSuccess) {
+    delete bt;
+    return fail(PBAD_ERR_ALLOC, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemset(bt->d_ws, 0, sizeof(double) * ws);
+  if (e != cudaSuccess) {
+    cudaFree(bt->d_ws);
+    delete bt;
+    return cuda_fail(e, "cudaMemset");
+  }
+  *out = bt;
+  return PBAD_OK;
+}
+
+int pbad_batch_destroy(pbad_batch* bt) {
+  if (!bt) return PBAD_OK;
+  DeviceGuard dg(bt->device);
+  cudaFree(bt->d_ws);
+  delete bt;
+  return PBAD_OK;
+}
+
+int pbad_batch_info(const pbad_batch* bt, int64_t* n_instances, int64_t* n_dof_total,
+                    int64_t* workspace_bytes) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (n_instances) *n_instances = bt->n_inst;
+  if (n_dof_total) *n_dof_total = bt->D;
+  if (workspace_bytes) *workspace_bytes = (int64_t)(bt->ws_doubles * sizeof(double));
+  return PBAD_OK;
+}
+
+int pbad_eval_objective_grad(pbad_batch* bt, const double* q_star, const double* q_prev,
+                             const double* q_cur, const double* tau, double dt, int32_t stages,
+                             double* E, double* grad, double* resid, void* stream) {
+  int rc = check_common(bt, stages, dt);
+  if (rc != PBAD_OK) return rc;
+  if (!q_star || !q_prev || !q_cur || !E || !grad) return fail(PBAD_ERR_ARG, "null array");
+  DeviceGuard dg(bt->device);
+  LaunchArgs A;
+  int grid = 0;
+  rc = fill_launch(bt, stages, dt, nullptr, 0, &A, &grid);
+  if (rc != PBAD_OK) return rc;
+  A.q_prev0 = q_prev;
+  A.q_cur0 = q_cur;
+  A.tau = tau;
+  A.q_star = q_star;
+  A.E_out = E;
+  A.grad_out = grad;
+  A.resid_out = resid;
+  A.n_steps = 1;
+  cudaStream_t s = (cudaStream_t)stream;
+  const cudaError_t e = launch_eval(stages, A, grid, s);
+  if (e != cudaSuccess) return cuda_fail(e, "eval launch");
+  return PBAD_OK;
+}
+
+int pbad_rollout(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
+                 const double* tau_seq, int32_t n_steps, double dt, int32_t stages,
+                 const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
+                 double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
+                 int32_t* status, int32_t* iters, int32_t* evals, void* stream) {
+  return rollout_impl(bt, q_prev0, q_cur0, tau_seq, n_steps, dt, stages, solvers, history, tol,
+                      max_iter, traj_prev, traj_cur, q_prev_out, q_cur_out, nullptr, status, iters,
+                      evals, stream);
+}
+
+int pbad_step(pbad_batch* bt, const double* q_prev, const double* q_cur, const double* tau,
+              double dt, int32_t stages, const int32_t* solvers, int32_t history, double tol,
+              int32_t max_iter, double* q_prev_out, double* q_cur_out, double* q_stages_out,
+              int32_t* status, int32_t* iters, void* stream) {
+  return rollout_impl(bt, q_prev, q_cur, tau, 1, dt, stages, solvers, history, tol, max_iter,
+                      nullptr, nullptr, q_prev_out, q_cur_out, q_stages_out, status, iters,
+                      nullptr, stream);
+}
+
+int pbad_fp64_peak(int32_t device, double* gflops) {
+  if (!gflops) return fail(PBAD_ERR_ARG, "null output");
+  DeviceGuard dg(device);
+  if (!dg.ok) return fail(PBAD_ERR_CUDA, "cudaSetDevice failed");
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return cuda_fail(e, "attribute");
+  const int threads = 256, blocks = sms * 4, iters = 20000;
+  double* d = nullptr;
+  if ((e = cudaMalloc(&d, sizeof(double) * threads * blocks)) != cudaSuccess)
+    return fail(PBAD_ERR_ALLOC, "probe buffer");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    launch_fp64_peak(d, blocks, threads, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "probe");
+  *gflops = 2.0 * 8.0 * iters * (double)threads * blocks / (best * 1e-3) / 1e9;
+  return PBAD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,284 @@
+// Device-side building blocks of the position-based articulated dynamics
+// (PBAD) hot path: joint rotations, forward kinematics, the per-link seeds of
+// Eq. EQ / Eq. HOC, world-frame wrench accumulation (Algorithm DERIV in world
+// coordinates) and the tangent-over-adjoint sweep that gives the gradient of
+// Eq. EQHOC in O(N).
+//
+// Execution model: a group of S lanes of one warp owns one instance; lane i
+// of the group owns collocation stage i. Every lane walks the link tree
+// sequentially; the stages meet only where Eq. HOC couples them (the second
+// derivative of the collocation polynomial), through warp shuffles.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace pbad {
+
+constexpr int kMaxStages = 5;
+constexpr int kMaxHistory = 16;
+
+// Per-lane array in a lane-interleaved workspace: element k of lane L lives at
+// base[k * stride + L], so that the lanes of a warp touch consecutive words.
+struct Lane {
+  double* p;
+  int64_t st;
+  __device__ __forceinline__ double& operator[](int64_t k) const { return p[k * st]; }
+};
+
+// One bucket of instances that share a topology (a "model").
+struct Bucket {
+  int N, n, count;       // links, DOFs, instances
+  const int* parent;     // [N]
+  const int* jtype;      // [N] 0 hinge, 1 ball
+  const int* dof;        // [N] first DOF of each joint
+  const double* axis;    // [N][3] hinge axes (joint frame)
+  const double* mm;      // [N][10][count] mass moments (SoA over instances)
+  const double* rest;    // [N][12][count] rest transforms (SoA over instances)
+  double g[3];           // gravity
+  int64_t inst_off;      // first instance of the bucket in the batch
+  int64_t dof_off;       // offset of the bucket's block in DOF-packed arrays
+  double* ws;            // lane workspace
+  int64_t ws_stride;     // lanes in the workspace (>= groups * S)
+  int block_begin;       // first block of the launch that serves this bucket
+  int solver;            // 0 L-BFGS, 1 Newton
+};
+
+// Collocation constants of one launch (all in units of 1/dt^2 already).
+struct Colloc {
+  int S;
+  double dt;
+  double nodes[kMaxStages + 2];
+  double Wk[kMaxStages][2];           // weights of the two known nodes
+  double Wu[kMaxStages][kMaxStages];  // Wu[i][j]: residual stage i, unknown j
+  double Ps[kMaxStages][kMaxStages];  // stage block of the L-BFGS H0
+};
+
+// ---------------------------------------------------------------- 3x4 math
+struct M34 {
+  double a[12];
+};
+
+__device__ __forceinline__ void compose(const double* A, const double* B, double* C) {
+  // C = A * B for affine 3x4 matrices (implicit bottom row 0 0 0 1)
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double a0 = A[4 * r], a1 = A[4 * r + 1], a2 = A[4 * r + 2], a3 = A[4 * r + 3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) C[4 * r + c] = fma(a0, B[c], fma(a1, B[4 + c], a2 * B[8 + c]));
+    C[4 * r + 3] = fma(a0, B[3], fma(a1, B[7], fma(a2, B[11], a3)));
+  }
+}
+
+__device__ __forceinline__ void cross(const double* a, const double* b, double* c) {
+  c[0] = fma(a[1], b[2], -a[2] * b[1]);
+  c[1] = fma(a[2], b[0], -a[0] * b[2]);
+  c[2] = fma(a[0], b[1], -a[1] * b[0]);
+}
+__device__ __forceinline__ double dot3(const double* a, const double* b) {
+  return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
+}
+
+// R = c0 I + c1 [v]x + c2 v v^T (Rodrigues form shared by hinges and the
+// exponential map).
+__device__ __forceinline__ void rodrigues(const double* v, double c0, double c1, double c2, double* R) {
+  R[0] = fma(c2, v[0] * v[0], c0);
+  R[1] = fma(c2, v[0] * v[1], -c1 * v[2]);
+  R[2] = fma(c2, v[0] * v[2], c1 * v[1]);
+  R[3] = fma(c2, v[1] * v[0], c1 * v[2]);
+  R[4] = fma(c2, v[1] * v[1], c0);
+  R[5] = fma(c2, v[1] * v[2], -c1 * v[0]);
+  R[6] = fma(c2, v[2] * v[0], -c1 * v[1]);
+  R[7] = fma(c2, v[2] * v[1], c1 * v[0]);
+  R[8] = fma(c2, v[2] * v[2], c0);
+}
+
+// Scalar functions of x = |theta|^2 for the exponential map:
+//   b(x) = (1 - cos phi)/x, h(x) = (phi - sin phi)/phi^3 and their x-derivatives,
+//   plus cos phi and a = sin(phi)/phi. Power series below x = 0.25.
+struct ExpCoef {
+  double c, a, b, h, db, dh;
+};
+__device__ __forceinline__ ExpCoef exp_coef(double x) {
+  ExpCoef e;
+  if (x < 0.25) {
+    // Horner in x; terms through x^9 (remainder < 1e-21 at x = 0.25)
+    // a = sum (-1)^k x^k/(2k+1)!, b = sum (-1)^k x^k/(2k+2)!, h = sum (-1)^k x^k/(2k+3)!
+    const double ia[10] = {1.0, -1.0 / 6, 1.0 / 120, -1.0 / 5040, 1.0 / 362880, -1.0 / 39916800,
+                           1.0 / 6227020800.0, -1.0 / 1307674368000.0, 1.0 / 355687428096000.0,
+                           -1.0 / 121645100408832000.0};
+    const double ib[10] = {1.0 / 2, -1.0 / 24, 1.0 / 720, -1.0 / 40320, 1.0 / 3628800,
+                           -1.0 / 479001600, 1.0 / 87178291200.0, -1.0 / 20922789888000.0,
+                           1.0 / 6402373705728000.0, -1.0 / 2432902008176640000.0};
+    const double ih[10] = {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800,
+                           -1.0 / 6227020800.0, 1.0 / 1307674368000.0, -1.0 / 355687428096000.0,
+                           1.0 / 121645100408832000.0, -1.0 / 51090942171709440000.0};
+    double A = ia[9], B = ib[9], H = ih[9], dB = 9 * ib[9], dH = 9 * ih[9];
+#pragma unroll
+    for (int k = 8; k >= 0; --k) {
+      A = fma(A, x, ia[k]);
+      B = fma(B, x, ib[k]);
+      H = fma(H, x, ih[k]);
+    }
+#pragma unroll
+    for (int k = 8; k >= 1; --k) {
+      dB = fma(dB, x, k * ib[k]);
+      dH = fma(dH, x, k * ih[k]);
+    }
+    e.a = A;
+    e.b = B;
+    e.h = H;
+    e.db = dB;
+    e.dh = dH;
+    e.c = fma(-B, x, 1.0);  // cos phi = 1 - x b
+  } else {
+    const double phi = sqrt(x);
+    double s, c;
+    sincos(phi, &s, &c);
+    const double ix = 1.0 / x;
+    e.c = c;
+    e.a = s / phi;
+    e.b = (1.0 - c) * ix;
+    e.h = (phi - s) * ix / phi;
+    e.db = (phi * s - 2.0 * (1.0 - c)) * 0.5 * ix * ix;
+    e.dh = (3.0 * s - phi * (2.0 + c)) * 0.5 * ix * ix / phi;
+  }
+  return e;
+}
+
+// Joint rotation (and, for balls, the right Jacobian Jr) of one joint.
+//   hinge: R = Rot(u, q), world axis w = R_link u
+//   ball:  R = exp([theta]x), world axes w_k = R_link Jr(theta) e_k
+__device__ __forceinline__ void joint_rotation(int jt, const double* u, const double* q, double* R,
+                                               double* Jr) {
+  if (jt == 0) {
+    double s, c;
+    sincos(q[0], &s, &c);
+    rodrigues(u, c, s, 1.0 - c, R);
+  } else {
+    const double x = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
+    const ExpCoef e = exp_coef(x);
+    rodrigues(q, e.c, e.a, e.b, R);
+    // Jr = (1 - h x) I - b [theta]x + h theta theta^T
+    rodrigues(q, fma(-e.h, x, 1.0), -e.b, e.h, Jr);
+  }
+}
+
+// Derivative of Jr along v: -2 (theta.v) b' K - b [v]x + 2 (theta.v) h' K^2 + h ([v]x K + K [v]x)
+// with K = [theta]x and K^2 = theta theta^T - x I.
+__device__ __forceinline__ void jr_tangent(const double* th, const double* v, double* dJ) {
+  const double x = fma(th[0], th[0], fma(th[1], th[1], th[2] * th[2]));
+  const ExpCoef e = exp_coef(x);
+  const double tv = dot3(th, v);
+  const double cb = -2.0 * tv * e.db, ch = 2.0 * tv * e.dh;
+  // [v]x K + K [v]x = v th^T + th v^T - 2 (v.th) I
+  double K[9], K2[9], VK[9], Vx[9];
+  K[0] = 0; K[1] = -th[2]; K[2] = th[1];
+  K[3] = th[2]; K[4] = 0; K[5] = -th[0];
+  K[6] = -th[1]; K[7] = th[0]; K[8] = 0;
+  Vx[0] = 0; Vx[1] = -v[2]; Vx[2] = v[1];
+  Vx[3] = v[2]; Vx[4] = 0; Vx[5] = -v[0];
+  Vx[6] = -v[1]; Vx[7] = v[0]; Vx[8] = 0;
+#pragma unroll
+  for (int r = 0; r < 3; ++r)
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      K2[3 * r + c] = th[r] * th[c] - (r == c ? x : 0.0);
+      VK[3 * r + c] = v[r] * th[c] + th[r] * v[c] - (r == c ? 2.0 * tv : 0.0);
+    }
+#pragma unroll
+  for (int k = 0; k < 9; ++k) dJ[k] = fma(cb, K[k], fma(-e.b, Vx[k], fma(ch, K2[k], e.h * VK[k])));
+}
+
+// Mass moment M (4x4 symmetric) of link l for instance b.
+struct MassMoment {
+  double s[10];  // Sxx Sxy Sxz Syy Syz Szz mcx mcy mcz m
+  __device__ __forceinline__ double at(int r, int c) const {
+    // index map of the symmetric 4x4
+    const int idx[16] = {0, 1, 2, 6, 1, 3, 4, 7, 2, 4, 5, 8, 6, 7, 8, 9};
+    return s[idx[4 * r + c]];
+  }
+};
+
+// Y = A * M for a 3x4 A (the fourth column of M's row 3 is m).
+__device__ __forceinline__ void mul_mass(const double* A, const MassMoment& M, double* Y) {
+  const double* s = M.s;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double a0 = A[4 * r], a1 = A[4 * r + 1], a2 = A[4 * r + 2], a3 = A[4 * r + 3];
+    Y[4 * r + 0] = fma(a0, s[0], fma(a1, s[1], fma(a2, s[2], a3 * s[6])));
+    Y[4 * r + 1] = fma(a0, s[1], fma(a1, s[3], fma(a2, s[4], a3 * s[7])));
+    Y[4 * r + 2] = fma(a0, s[2], fma(a1, s[4], fma(a2, s[5], a3 * s[8])));
+    Y[4 * r + 3] = fma(a0, s[6], fma(a1, s[7], fma(a2, s[8], a3 * s[9])));
+  }
+}
+
+// World wrench (moment about the world origin, force) of a 3x4 seed G at
+// transform T: m = ax(G_R R^T) + t x f, f = G_t, where ax(Y) = (Y21 - Y12,
+// Y02 - Y20, Y10 - Y01). Derivation: G : (S T) = w.(m - o x f) for a unit
+// twist S about an axis w through o.
+__device__ __forceinline__ void wrench(const double* G, const double* T, double* w6) {
+  // Y_rk = G_R[r] . R[k]
+  auto Y = [&](int r, int k) {
+    return fma(G[4 * r], T[4 * k], fma(G[4 * r + 1], T[4 * k + 1], G[4 * r + 2] * T[4 * k + 2]));
+  };
+  const double f[3] = {G[3], G[7], G[11]};
+  const double t[3] = {T[3], T[7], T[11]};
+  double tf[3];
+  cross(t, f, tf);
+  w6[0] = Y(2, 1) - Y(1, 2) + tf[0];
+  w6[1] = Y(0, 2) - Y(2, 0) + tf[1];
+  w6[2] = Y(1, 0) - Y(0, 1) + tf[2];
+  w6[3] = f[0];
+  w6[4] = f[1];
+  w6[5] = f[2];
+}
+
+// Tangent of the wrench: d/de of wrench(G + e Gd, T + e Td).
+__device__ __forceinline__ void wrench_tangent(const double* G, const double* Gd, const double* T,
+                                               const double* Td, double* w6) {
+  auto Y = [&](const double* A, const double* B, int r, int k) {
+    return fma(A[4 * r], B[4 * k], fma(A[4 * r + 1], B[4 * k + 1], A[4 * r + 2] * B[4 * k + 2]));
+  };
+  auto Yd = [&](int r, int k) { return Y(Gd, T, r, k) + Y(G, Td, r, k); };
+  const double f[3] = {G[3], G[7], G[11]}, fd[3] = {Gd[3], Gd[7], Gd[11]};
+  const double t[3] = {T[3], T[7], T[11]}, td[3] = {Td[3], Td[7], Td[11]};
+  double a1[3], a2[3];
+  cross(td, f, a1);
+  cross(t, fd, a2);
+  w6[0] = Yd(2, 1) - Yd(1, 2) + a1[0] + a2[0];
+  w6[1] = Yd(0, 2) - Yd(2, 0) + a1[1] + a2[1];
+  w6[2] = Yd(1, 0) - Yd(0, 1) + a1[2] + a2[2];
+  w6[3] = fd[0];
+  w6[4] = fd[1];
+  w6[5] = fd[2];
+}
+
+// ------------------------------------------------------- group primitives
+template <int S>
+struct Group {
+  int lane, base, stage;
+  unsigned mask;
+  __device__ __forceinline__ Group() {
+    lane = threadIdx.x & 31;
+    stage = lane % S;
+    base = lane - stage;
+    mask = (S == 32) ? 0xffffffffu : (((1u << S) - 1u) << base);
+  }
+  // value of lane base+j (all lanes of the warp must call with full mask)
+  __device__ __forceinline__ double from_full(double v, int j) const {
+    return __shfl_sync(0xffffffffu, v, base + j);
+  }
+  __device__ __forceinline__ double from(double v, int j) const {
+    return __shfl_sync(mask, v, base + j);
+  }
+  // group sum in a fixed order: identical bits on every lane of the group
+  __device__ __forceinline__ double sum(double v) const {
+    if (S == 1) return v;
+    double s = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) s += __shfl_sync(mask, v, base + j);
+    return s;
+  }
+};
+
+}  // namespace pbad

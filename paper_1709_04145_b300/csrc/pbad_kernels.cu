@@ -1,0 +1,290 @@
+// Kernels of the PBAD hot path: batched objective/gradient evaluation and the
+// persistent L-BFGS rollout. See pbad_kernels.cuh for the per-lane passes.
+#include "pbad_kernels.cuh"
+
+#ifndef PBAD_S
+#error "compile with -DPBAD_S=<stages>"
+#endif
+
+namespace pbad {
+
+__device__ __forceinline__ int find_bucket(const LaunchArgs& A) {
+  int bk = 0;
+  while (bk + 1 < A.nb && (int)blockIdx.x >= A.bk[bk + 1].block_begin) ++bk;
+  return bk;
+}
+
+// Lane identity inside a bucket: groups of S lanes, floor(32/S) groups per warp.
+template <int S>
+struct LaneId {
+  int64_t lane_id;  // lane index inside the bucket's workspace
+  int64_t inst;     // instance index inside the bucket (may be >= count)
+  bool real;        // lane belongs to a full group
+  __device__ LaneId(const Bucket& B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)(blockIdx.x - B.block_begin) * blockDim.x + threadIdx.x) >> 5;
+    constexpr int G = 32 / S;
+    lane_id = warp * 32 + lane;
+    real = lane < G * S;
+    inst = warp * G + lane / S;
+  }
+};
+
+// ------------------------------------------------------------------------
+// E, r and dE/dq at given stage configurations (one evaluation per instance)
+// ------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(128) k_eval(const __grid_constant__ LaunchArgs A) {
+  const Bucket& B = A.bk[find_bucket(A)];
+  const LaneId<S> id(B);
+  const bool active = id.real && id.inst < B.count;
+  const int b = active ? (int)id.inst : 0;
+  Ctx<S> c(B, A.K, b, id.lane_id, 0);
+  for (int d = 0; d < c.n; ++d) {
+    c.ws[c.L.qp + d] = A.q_prev0[c.gdof(d)];
+    c.ws[c.L.qc + d] = A.q_cur0[c.gdof(d)];
+  }
+  c.setup();
+  for (int d = 0; d < c.n; ++d) c.ws[c.L.xt + d] = A.q_star[c.gstage(d)];
+  const double E = c.evaluate(A.tau);
+  if (active) {
+    if (c.i == 0) A.E_out[B.inst_off + b] = E;
+    for (int d = 0; d < c.n; ++d) {
+      A.grad_out[c.gstage(d)] = c.ws[c.L.gt + d];
+      if (A.resid_out) A.resid_out[c.gstage(d)] = c.ws[c.L.rt + d];
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// Persistent L-BFGS rollout: every group of S lanes integrates one instance
+// for n_steps steps. Each loop trip evaluates E, r, dE/dq at every group's
+// current trial point (convergent), then each group advances its own state
+// machine (line search, history update, convergence, next step) - the
+// iteration-level scheduling of the paper's Fig. GPU, inside a warp.
+// ------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(128) k_rollout_lbfgs(const __grid_constant__ LaunchArgs A) {
+  const Bucket& B = A.bk[find_bucket(A)];
+  const LaneId<S> id(B);
+  const bool active = id.real && id.inst < B.count;
+  const int b = active ? (int)id.inst : 0;
+  const int m = A.history;
+  Ctx<S> c(B, A.K, b, id.lane_id, m);
+  const int n = c.n;
+  const auto& L = c.L;
+  const Lane& ws = c.ws;
+  const int64_t D = A.D;
+
+  for (int d = 0; d < n; ++d) {
+    ws[L.qp + d] = A.q_prev0[c.gdof(d)];
+    ws[L.qc + d] = A.q_cur0[c.gdof(d)];
+  }
+  int step = 0, phase = kFirst, k = 0, trials = 0, nh = 0, head = 0;
+  int worst = kConverged, iters_total = 0, evals_total = 0;
+  double E = 0.0, alpha = 1.0, gd = 0.0, gamma = 1.0;
+  c.setup();
+  if (!active) phase = kDone;
+
+  auto finish = [&](int st) {
+    worst = max(worst, st);
+    // new state: q_prev' = stage S-2 (or q_cur when S = 1), q_cur' = stage S-1
+    for (int d = 0; d < n; ++d) {
+      const double xs = c.grp.from(ws[L.x + d], S - 1);
+      const double xp = (S == 1) ? ws[L.qc + d] : c.grp.from(ws[L.x + d], S - 2);
+      ws[L.qp + d] = xp;
+      ws[L.qc + d] = xs;
+      if (c.i == 0) {
+        if (A.traj_cur) A.traj_cur[(int64_t)step * D + c.gdof(d)] = xs;
+        if (A.traj_prev) A.traj_prev[(int64_t)step * D + c.gdof(d)] = xp;
+      }
+    }
+    if (A.q_stages_out && step == A.n_steps - 1)
+      for (int d = 0; d < n; ++d) A.q_stages_out[c.gstage(d)] = ws[L.x + d];
+    ++step;
+    if (step >= A.n_steps) {
+      phase = kDone;
+    } else {
+      c.setup();
+      phase = kFirst;
+    }
+  };
+
+  auto start_iteration = [&]() {
+    // convergence / caps at the accepted point x
+    double rr = 0.0;
+    int bad = 0;
+    for (int d = 0; d < n; ++d) {
+      rr = fma(ws[L.r + d], ws[L.r + d], rr);
+      if (!isfinite(ws[L.g + d])) bad = 1;
+    }
+    rr = c.grp.sum(rr);
+    bad = (int)c.grp.sum((double)bad);
+    if (bad || !isfinite(E) || !isfinite(rr)) { finish(kNonFinite); return; }
+    if (sqrt(rr) < A.tol) { finish(kConverged); return; }
+    if (k >= A.max_iter) { finish(kMaxIter); return; }
+    // two-loop recursion with H0 = gamma * P
+    double al[kMaxHistory];
+    for (int d = 0; d < n; ++d) ws[L.d + d] = -ws[L.g + d];
+    for (int t = 0; t < nh; ++t) {
+      const int j = (head - 1 - t + 2 * m) % m;
+      const double a = ws[L.rho + j] * c.gdot(L.sh + j * n, L.d);
+      al[j] = a;
+      for (int d = 0; d < n; ++d) ws[L.d + d] = fma(-a, ws[L.yh + j * n + d], ws[L.d + d]);
+    }
+    c.precond(L.d);
+    for (int d = 0; d < n; ++d) ws[L.d + d] *= gamma;
+    for (int t = nh - 1; t >= 0; --t) {
+      const int j = (head - 1 - t + 2 * m) % m;
+      const double bta = ws[L.rho + j] * c.gdot(L.yh + j * n, L.d);
+      for (int d = 0; d < n; ++d) ws[L.d + d] = fma(al[j] - bta, ws[L.sh + j * n + d], ws[L.d + d]);
+    }
+    gd = c.gdot(L.g, L.d);
+    if (!(gd < 0.0)) {
+      nh = 0;
+      gamma = 1.0;
+      for (int d = 0; d < n; ++d) ws[L.d + d] = -ws[L.g + d];
+      c.precond(L.d);
+      gd = c.gdot(L.g, L.d);
+    }
+    alpha = 1.0;
+    trials = 0;
+    for (int d = 0; d < n; ++d) ws[L.xt + d] = ws[L.x + d] + ws[L.d + d];
+    phase = kTrial;
+  };
+
+  while (__any_sync(0xffffffffu, phase != kDone)) {
+    const double* tau = A.tau ? A.tau + (int64_t)min(step, A.n_steps - 1) * D : nullptr;
+    const double Et = c.evaluate(tau);
+    if (phase == kDone) continue;
+    ++evals_total;
+    if (phase == kFirst) {
+      for (int d = 0; d < n; ++d) {
+        ws[L.x + d] = ws[L.xt + d];
+        ws[L.g + d] = ws[L.gt + d];
+        ws[L.r + d] = ws[L.rt + d];
+      }
+      E = Et;
+      k = 0;
+      nh = 0;
+      head = 0;
+      gamma = 1.0;
+      start_iteration();
+      continue;
+    }
+    // line-search trial at xt = x + alpha d
+    int ok = 0;
+    {
+      double fin = 1.0;
+      for (int d = 0; d < n; ++d)
+        if (!isfinite(ws[L.gt + d])) fin = 0.0;
+      fin = c.grp.sum(fin);
+      if (fin == (double)S && isfinite(Et)) {
+        const double gtd = c.gdot(L.gt, L.d);
+        const bool armijo = Et <= E + kLsC1 * alpha * gd;
+        const bool approx = (Et <= E + kLsEps * fabs(E)) && (gtd <= (1.0 - 2.0 * kLsDelta) * fabs(gd));
+        ok = armijo || approx;
+      }
+    }
+    if (!ok) {
+      if (++trials >= kLsMax) {
+        finish(kLsFail);
+        continue;
+      }
+      alpha *= 0.5;
+      for (int d = 0; d < n; ++d) ws[L.xt + d] = fma(alpha, ws[L.d + d], ws[L.x + d]);
+      continue;
+    }
+    // accepted: curvature pair into the ring buffer
+    {
+      double sy = 0, ss = 0, yy = 0;
+      for (int d = 0; d < n; ++d) {
+        const double s_ = ws[L.xt + d] - ws[L.x + d], y_ = ws[L.gt + d] - ws[L.g + d];
+        sy = fma(s_, y_, sy);
+        ss = fma(s_, s_, ss);
+        yy = fma(y_, y_, yy);
+        ws[L.d + d] = y_;             // d is dead after acceptance: reuse for P y
+      }
+      sy = c.grp.sum(sy);
+      ss = c.grp.sum(ss);
+      yy = c.grp.sum(yy);
+      if (m > 0 && sy > kCurvEps * sqrt(ss) * sqrt(yy)) {
+        c.precond(L.d);
+        double yPy = 0;
+        for (int d = 0; d < n; ++d) yPy = fma(ws[L.gt + d] - ws[L.g + d], ws[L.d + d], yPy);
+        yPy = c.grp.sum(yPy);
+        for (int d = 0; d < n; ++d) {
+          ws[L.sh + head * n + d] = ws[L.xt + d] - ws[L.x + d];
+          ws[L.yh + head * n + d] = ws[L.gt + d] - ws[L.g + d];
+        }
+        ws[L.rho + head] = 1.0 / sy;
+        head = (head + 1) % m;
+        if (nh < m) ++nh;
+        gamma = sy / yPy;
+      }
+    }
+    for (int d = 0; d < n; ++d) {
+      ws[L.x + d] = ws[L.xt + d];
+      ws[L.g + d] = ws[L.gt + d];
+      ws[L.r + d] = ws[L.rt + d];
+    }
+    E = Et;
+    ++k;
+    ++iters_total;
+    start_iteration();
+  }
+  if (active && c.i == 0) {
+    if (A.status) A.status[B.inst_off + b] = worst;
+    if (A.iters) A.iters[B.inst_off + b] = iters_total;
+    if (A.evals) A.evals[B.inst_off + b] = evals_total;
+  }
+  if (active) {
+    for (int d = 0; d < n; ++d) {
+      if (c.i == 0) {
+        if (A.q_prev_out) A.q_prev_out[c.gdof(d)] = ws[L.qp + d];
+        if (A.q_cur_out) A.q_cur_out[c.gdof(d)] = ws[L.qc + d];
+      }
+    }
+  }
+}
+
+// ------------------------------------------------------------------------
+// FP64 FMA throughput probe (roofline denominator): dependent chains, 8
+// independent chains per thread.
+// ------------------------------------------------------------------------
+#if PBAD_S == 1
+__global__ void k_fp64_peak(double* out, int iters, double a, double b) {
+  double x[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) x[k] = threadIdx.x * 1e-3 + k;
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k) x[k] = fma(x[k], a, b);
+  }
+  double s = 0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += x[k];
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+#endif
+
+// Host-side launchers for the stage count this translation unit is built for
+// (PBAD_S): the library compiles this file once per stage count.
+#define PBAD_CAT2(a, b) a##b
+#define PBAD_CAT(a, b) PBAD_CAT2(a, b)
+cudaError_t PBAD_CAT(launch_eval_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
+  k_eval<PBAD_S><<<grid, 128, 0, s>>>(A);
+  return cudaGetLastError();
+}
+cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
+  k_rollout_lbfgs<PBAD_S><<<grid, 128, 0, s>>>(A);
+  return cudaGetLastError();
+}
+#if PBAD_S == 1
+cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters) {
+  k_fp64_peak<<<blocks, threads>>>(out, iters, 0.999999, 1e-7);
+  return cudaGetLastError();
+}
+#endif
+
+}  // namespace pbad

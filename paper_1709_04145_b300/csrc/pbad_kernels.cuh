@@ -1,0 +1,518 @@
+// The hot path of position-based articulated dynamics (Pan & Manocha):
+//   - per-step setup (Section 4.1): known-node combination C_i and the
+//     L-BFGS initial inverse Hessian from the joint-space mass matrix;
+//   - objective/residual pass (Eq. EQ for one stage, Eq. HOC/EQHOC for
+//     several): forward kinematics, per-link seeds, world wrench suffix sums
+//     and joint contraction (Algorithm DERIV, tree form, world frame);
+//   - tangent pass: d/de of the residual pass along r, giving
+//     grad E = 2 Jr^T r for Eq. EQHOC in O(N) (Table 1's second-derivative
+//     terms without forming any Hessian block);
+//   - a persistent L-BFGS rollout (Section 5: one optimisation per step,
+//     iteration-level scheduling of Fig. GPU inside each warp).
+#pragma once
+#include "pbad_device.cuh"
+
+namespace pbad {
+
+constexpr int kMaxBuckets = 8;
+constexpr double kLsC1 = 1e-4;     // Armijo constant
+constexpr double kLsDelta = 0.1;   // approximate-Wolfe delta (Hager-Zhang)
+constexpr double kLsEps = 1e-12;   // relative energy slack of approximate Wolfe
+constexpr int kLsMax = 40;         // backtracking trials
+constexpr double kCurvEps = 1e-14; // curvature-pair acceptance
+
+enum Phase { kFirst = 1, kTrial = 2, kDone = 3 };
+enum Status { kConverged = 0, kMaxIter = 1, kLsFail = 2, kCholFail = 3, kNonFinite = 4 };
+
+// Offsets (in doubles) of one lane's workspace.
+struct WsLayout {
+  int T, G, acc, axes, V, accd, C, Pb, x, g, d, xt, gt, r, rt, qp, qc, sh, yh, rho, total;
+  __host__ __device__ void make(int N, int n, int m) {
+    int o = 0;
+    T = o; o += 12 * N;
+    G = o; o += 12 * N;
+    acc = o; o += 6 * N;
+    axes = o; o += 9 * N;
+    V = o; o += 6 * N;
+    accd = o; o += 6 * N;
+    C = o; o += 12 * N;
+    Pb = o; o += 9 * N;
+    x = o; o += n;
+    g = o; o += n;
+    d = o; o += n;
+    xt = o; o += n;
+    gt = o; o += n;
+    r = o; o += n;
+    rt = o; o += n;
+    qp = o; o += n;
+    qc = o; o += n;
+    sh = o; o += m * n;
+    yh = o; o += m * n;
+    rho = o; o += (m > 0 ? m : 1);
+    total = o;
+  }
+};
+
+struct LaunchArgs {
+  int nb;
+  Bucket bk[kMaxBuckets];
+  Colloc K;
+  int history, max_iter, n_steps;
+  double tol;
+  int64_t D;               // total DOFs of the batch (row length of DOF-packed arrays)
+  const double* q_prev0;   // [D]
+  const double* q_cur0;    // [D]
+  const double* tau;       // [n_steps][D] or null
+  const double* q_star;    // eval: [S*D] stage-packed
+  double* E_out;           // eval: [instances]
+  double* grad_out;        // eval: [S*D]
+  double* resid_out;       // eval: [S*D] or null
+  double* q_prev_out;      // [D] or null
+  double* q_cur_out;       // [D] or null
+  double* traj_prev;       // [n_steps][D] or null
+  double* traj_cur;        // [n_steps][D] or null
+  double* q_stages_out;    // [S*D] or null (last step's stages)
+  int* status;             // [instances] or null
+  int* iters;              // [instances] or null
+  int* evals;              // [instances] or null (objective evaluations)
+};
+
+// ------------------------------------------------------------------------
+// per-lane context
+// ------------------------------------------------------------------------
+template <int S>
+struct Ctx {
+  const Bucket& B;
+  const Colloc& K;
+  Group<S> grp;
+  WsLayout L;
+  Lane ws;
+  int b;       // instance within the bucket (always a valid index)
+  int i;       // own stage
+  int N, n;
+
+  __device__ Ctx(const Bucket& B_, const Colloc& K_, int b_, int64_t lane_id, int m)
+      : B(B_), K(K_), b(b_) {
+    N = B.N;
+    n = B.n;
+    L.make(N, n, m);
+    ws.p = B.ws + lane_id;
+    ws.st = B.ws_stride;
+    i = grp.stage;
+  }
+
+  __device__ __forceinline__ double rest(int l, int k) const {
+    return B.rest[((int64_t)l * 12 + k) * B.count + b];
+  }
+  __device__ __forceinline__ MassMoment mass(int l) const {
+    MassMoment M;
+#pragma unroll
+    for (int k = 0; k < 10; ++k) M.s[k] = B.mm[((int64_t)l * 10 + k) * B.count + b];
+    return M;
+  }
+  __device__ __forceinline__ int ndof(int l) const { return B.jtype[l] == 0 ? 1 : 3; }
+  __device__ __forceinline__ int64_t gdof(int d) const { return B.dof_off + (int64_t)b * n + d; }
+  __device__ __forceinline__ int64_t gstage(int d) const {
+    return (int64_t)S * B.dof_off + ((int64_t)b * S + i) * n + d;
+  }
+
+  __device__ __forceinline__ void load12(int off, double* v) const {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) v[k] = ws[off + k];
+  }
+  __device__ __forceinline__ void store12(int off, const double* v) const {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) ws[off + k] = v[k];
+  }
+
+  // T_l = T_parent * X_l * Rot(q_l). Ball joints also return Jr(q_l).
+  __device__ __forceinline__ void link_fk(int l, const double* Tp, const double* ql, double* T,
+                                          double* Jr) const {
+    double X[12], R[9], XJ[12];
+#pragma unroll
+    for (int k = 0; k < 12; ++k) X[k] = rest(l, k);
+    const double u[3] = {B.axis[3 * l], B.axis[3 * l + 1], B.axis[3 * l + 2]};
+    joint_rotation(B.jtype[l], u, ql, R, Jr);
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+#pragma unroll
+      for (int c = 0; c < 3; ++c)
+        XJ[4 * r + c] = fma(X[4 * r], R[c], fma(X[4 * r + 1], R[3 + c], X[4 * r + 2] * R[6 + c]));
+      XJ[4 * r + 3] = X[4 * r + 3];
+    }
+    if (Tp) compose(Tp, XJ, T);
+    else {
+#pragma unroll
+      for (int k = 0; k < 12; ++k) T[k] = XJ[k];
+    }
+  }
+
+  // World axes of the joint of link l: hinge w = R u; ball w_k = R Jr e_k.
+  __device__ __forceinline__ void link_axes(int l, const double* T, const double* Jr, double* w) const {
+    if (B.jtype[l] == 0) {
+      const double u[3] = {B.axis[3 * l], B.axis[3 * l + 1], B.axis[3 * l + 2]};
+#pragma unroll
+      for (int r = 0; r < 3; ++r) w[r] = fma(T[4 * r], u[0], fma(T[4 * r + 1], u[1], T[4 * r + 2] * u[2]));
+    } else {
+      // column k of R Jr stored as w[3k..3k+2]
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          w[3 * k + r] = fma(T[4 * r], Jr[k], fma(T[4 * r + 1], Jr[3 + k], T[4 * r + 2] * Jr[6 + k]));
+    }
+  }
+
+  // ----------------------------------------------------------- step setup
+  // C_i,l = Wk[i][0] T_l(q_prev) + Wk[i][1] T_l(q_cur) for the own stage,
+  // the preconditioner blocks at q_cur and the initial guess (linear
+  // extrapolation through the two known nodes). q_prev/q_cur are read from
+  // the lane's workspace copies.
+  __device__ __noinline__ void setup() const {
+    double Tp[12], Tc[12], Jr[9], q3[3];
+    // forward: FK at both known nodes; parents' transforms live in T (prev)
+    // and G (cur) of the workspace during setup.
+    for (int l = 0; l < N; ++l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      double Pp[12], Pc[12];
+      if (p >= 0) {
+        load12(L.T + 12 * p, Pp);
+        load12(L.G + 12 * p, Pc);
+      }
+      for (int k = 0; k < nd; ++k) q3[k] = ws[L.qp + d0 + k];
+      link_fk(l, p >= 0 ? Pp : nullptr, q3, Tp, Jr);
+      for (int k = 0; k < nd; ++k) q3[k] = ws[L.qc + d0 + k];
+      link_fk(l, p >= 0 ? Pc : nullptr, q3, Tc, Jr);
+      store12(L.T + 12 * l, Tp);
+      store12(L.G + 12 * l, Tc);
+      double C[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) C[k] = fma(K.Wk[i][0], Tp[k], K.Wk[i][1] * Tc[k]);
+      store12(L.C + 12 * l, C);
+    }
+    // composite world mass moments at q_cur: [Sigma_w(6) h(3) m] per link in
+    // the T region (no longer needed)
+    for (int l = 0; l < N; ++l) {
+      double T[12];
+      load12(L.G + 12 * l, T);
+      const MassMoment M = mass(l);
+      const double* s = M.s;
+      // R Sigma R^T, R mc
+      double RS[9];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+        RS[3 * r + 0] = fma(T[4 * r], s[0], fma(T[4 * r + 1], s[1], T[4 * r + 2] * s[2]));
+        RS[3 * r + 1] = fma(T[4 * r], s[1], fma(T[4 * r + 1], s[3], T[4 * r + 2] * s[4]));
+        RS[3 * r + 2] = fma(T[4 * r], s[2], fma(T[4 * r + 1], s[4], T[4 * r + 2] * s[5]));
+      }
+      double Rm[3], t[3] = {T[3], T[7], T[11]};
+#pragma unroll
+      for (int r = 0; r < 3; ++r) Rm[r] = fma(T[4 * r], s[6], fma(T[4 * r + 1], s[7], T[4 * r + 2] * s[8]));
+      const double m = s[9];
+      const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+#pragma unroll
+      for (int e = 0; e < 6; ++e) {
+        const int r = ij[e][0], c = ij[e][1];
+        const double rsr = fma(RS[3 * r], T[4 * c], fma(RS[3 * r + 1], T[4 * c + 1], RS[3 * r + 2] * T[4 * c + 2]));
+        ws[L.T + 12 * l + e] = rsr + Rm[r] * t[c] + t[r] * Rm[c] + m * t[r] * t[c];
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r) ws[L.T + 12 * l + 6 + r] = fma(m, t[r], Rm[r]);
+      ws[L.T + 12 * l + 9] = m;
+    }
+    for (int l = N - 1; l >= 0; --l) {
+      const int p = B.parent[l];
+      if (p >= 0)
+        for (int k = 0; k < 10; ++k) ws[L.T + 12 * p + k] += ws[L.T + 12 * l + k];
+    }
+    // joint blocks B_j = W^T I_o W, I_o = tr(Sig_o) I - Sig_o about the joint
+    for (int l = 0; l < N; ++l) {
+      double T[12], Jr[9], w[9], q[3];
+      load12(L.G + 12 * l, T);
+      const int nd = ndof(l), d0 = B.dof[l];
+      if (nd == 3) {
+        for (int k = 0; k < 3; ++k) q[k] = ws[L.qc + d0 + k];
+        double R[9];
+        joint_rotation(1, nullptr, q, R, Jr);
+      }
+      link_axes(l, T, Jr, w);
+      double c[10];
+      for (int k = 0; k < 10; ++k) c[k] = ws[L.T + 12 * l + k];
+      const double o[3] = {T[3], T[7], T[11]};
+      const double h[3] = {c[6], c[7], c[8]}, m = c[9];
+      const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
+      double So[9];
+      for (int e = 0; e < 6; ++e) {
+        const int r = ij[e][0], q_ = ij[e][1];
+        const double v = c[e] - h[r] * o[q_] - o[r] * h[q_] + m * o[r] * o[q_];
+        So[3 * r + q_] = v;
+        So[3 * q_ + r] = v;
+      }
+      const double tr = So[0] + So[4] + So[8];
+      double Io[9];
+      for (int k = 0; k < 9; ++k) Io[k] = -So[k];
+      Io[0] += tr; Io[4] += tr; Io[8] += tr;
+      double Bj[9], Pj[9];
+      for (int a = 0; a < nd; ++a)
+        for (int bb = 0; bb < nd; ++bb) {
+          double s = 0;
+          for (int r = 0; r < 3; ++r)
+            for (int q_ = 0; q_ < 3; ++q_) s += w[3 * a + r] * Io[3 * r + q_] * w[3 * bb + q_];
+          Bj[nd * a + bb] = s;
+        }
+      if (nd == 1) {
+        Pj[0] = 1.0 / Bj[0];
+        if (S > 1) Pj[0] *= Pj[0];
+      } else {
+        const double a = Bj[0], b_ = Bj[1], c_ = Bj[2], d = Bj[3], e = Bj[4], f = Bj[5], g = Bj[6],
+                     hh = Bj[7], ii = Bj[8];
+        const double det = a * (e * ii - f * hh) - b_ * (d * ii - f * g) + c_ * (d * hh - e * g);
+        const double id = 1.0 / det;
+        double X[9] = {(e * ii - f * hh) * id, (c_ * hh - b_ * ii) * id, (b_ * f - c_ * e) * id,
+                       (f * g - d * ii) * id,  (a * ii - c_ * g) * id,  (c_ * d - a * f) * id,
+                       (d * hh - e * g) * id,  (b_ * g - a * hh) * id,  (a * e - b_ * d) * id};
+        if (S > 1) {
+          for (int r = 0; r < 3; ++r)
+            for (int q_ = 0; q_ < 3; ++q_)
+              Pj[3 * r + q_] = X[3 * r] * X[q_] + X[3 * r + 1] * X[3 + q_] + X[3 * r + 2] * X[6 + q_];
+        } else {
+          for (int k = 0; k < 9; ++k) Pj[k] = X[k];
+        }
+      }
+      for (int k = 0; k < nd * nd; ++k) ws[L.Pb + 9 * l + k] = Pj[k];
+    }
+    // initial guess for the own stage
+    const double sc = K.nodes[2 + i] / (0.0 - K.nodes[0]);
+    for (int d = 0; d < n; ++d) {
+      const double qc = ws[L.qc + d], qp = ws[L.qp + d];
+      ws[L.xt + d] = fma(sc, qc - qp, qc);
+    }
+  }
+
+  // --------------------------------------------------- residual (primal)
+  // Evaluates, at the own stage configuration xt: T, axes, seeds G and the
+  // wrench suffix sums; r_i = contraction - tau into rt. Returns the lane's
+  // share of E (energy for S = 1, |r_i|^2 otherwise); the caller sums over
+  // the group. Must be called convergently by the whole warp.
+  __device__ __noinline__ double primal(const double* tau) const {
+    double Eown = 0.0;
+    const double dt2 = K.dt * K.dt;
+    for (int l = 0; l < N; ++l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      double Tp[12], T[12], Jr[9], q3[3], w[9];
+      if (p >= 0) load12(L.T + 12 * p, Tp);
+      for (int k = 0; k < nd; ++k) q3[k] = ws[L.xt + d0 + k];
+      link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr);
+      store12(L.T + 12 * l, T);
+      link_axes(l, T, Jr, w);
+      for (int k = 0; k < 3 * nd; ++k) ws[L.axes + 9 * l + k] = w[k];
+      // A = C_i + sum_j Wu[i][j] T_j (stage coupling of Eq. HOC)
+      double A[12];
+      load12(L.C + 12 * l, A);
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const double wij = K.Wu[i][j];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) A[k] = fma(wij, grp.from_full(T[k], j), A[k]);
+      }
+      const MassMoment M = mass(l);
+      double G[12];
+      mul_mass(A, M, G);
+      const double mc4[4] = {M.s[6], M.s[7], M.s[8], M.s[9]};
+      if (S == 1) {
+        // Eq. EQ: tr(D M D^T)/(2 dt^2) with D = dt^2 A, and -g.(T [mc; m])
+        double ek = 0.0, eg = 0.0;
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ek = fma(A[k], G[k], ek);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          eg = fma(B.g[r], fma(T[4 * r], mc4[0], fma(T[4 * r + 1], mc4[1], fma(T[4 * r + 2], mc4[2], T[4 * r + 3] * mc4[3]))), eg);
+        Eown += 0.5 * dt2 * ek - eg;
+      }
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) G[4 * r + c] = fma(-B.g[r], mc4[c], G[4 * r + c]);
+      store12(L.G + 12 * l, G);
+      double w6[6];
+      wrench(G, T, w6);
+      for (int k = 0; k < 6; ++k) ws[L.acc + 6 * l + k] = w6[k];
+    }
+    // backward: subtree sums and joint contraction
+    double rr = 0.0, tq = 0.0;
+    for (int l = N - 1; l >= 0; --l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      double a[6];
+      for (int k = 0; k < 6; ++k) a[k] = ws[L.acc + 6 * l + k];
+      const double o[3] = {ws[L.T + 12 * l + 3], ws[L.T + 12 * l + 7], ws[L.T + 12 * l + 11]};
+      double of[3];
+      cross(o, a + 3, of);
+      const double mo[3] = {a[0] - of[0], a[1] - of[1], a[2] - of[2]};
+      for (int k = 0; k < nd; ++k) {
+        const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
+                             ws[L.axes + 9 * l + 3 * k + 2]};
+        const double tk = tau ? tau[gdof(d0 + k)] : 0.0;
+        const double rk = dot3(w, mo) - tk;
+        ws[L.rt + d0 + k] = rk;
+        rr = fma(rk, rk, rr);
+        tq = fma(tk, ws[L.xt + d0 + k], tq);
+      }
+      if (p >= 0)
+        for (int k = 0; k < 6; ++k) ws[L.acc + 6 * p + k] += a[k];
+    }
+    return (S == 1) ? (Eown - tq) : rr;
+  }
+
+  // ---------------------------------------------------- tangent (S >= 2)
+  // Tangent of the residual pass of the own stage k along v_k = r_k, with
+  // the seeds perturbed by B_k,l = sum_i Wu[i][k] Tdot_i,l M_l; gives
+  // (Jr^T r)_k into gt (times 2: the gradient of Eq. EQHOC). Needs the
+  // primal pass's T, G, axes and acc. Convergent across the warp.
+  __device__ __noinline__ void tangent() const {
+    for (int l = 0; l < N; ++l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      double V[6];
+      if (p >= 0) {
+        for (int k = 0; k < 6; ++k) V[k] = ws[L.V + 6 * p + k];
+      } else {
+        for (int k = 0; k < 6; ++k) V[k] = 0.0;
+      }
+      double T[12];
+      load12(L.T + 12 * l, T);
+      const double o[3] = {T[3], T[7], T[11]};
+      for (int k = 0; k < nd; ++k) {
+        const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
+                             ws[L.axes + 9 * l + 3 * k + 2]};
+        const double vk = ws[L.rt + d0 + k];
+        double ow[3];
+        cross(o, w, ow);
+        for (int c = 0; c < 3; ++c) {
+          V[c] = fma(vk, w[c], V[c]);
+          V[3 + c] = fma(vk, ow[c], V[3 + c]);
+        }
+      }
+      for (int k = 0; k < 6; ++k) ws[L.V + 6 * l + k] = V[k];
+      // Tdot = [w]x T + v at the world origin
+      double Td[12];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double col[3] = {T[c], T[4 + c], T[8 + c]};
+        double wc[3];
+        cross(V, col, wc);
+        Td[c] = wc[0];
+        Td[4 + c] = wc[1];
+        Td[8 + c] = wc[2];
+      }
+      Td[3] += V[3];
+      Td[7] += V[4];
+      Td[11] += V[5];
+      // B = (sum_i Wu[i][own] Tdot_i) M
+      double Bs[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) Bs[k] = 0.0;
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const double wji = K.Wu[j][i];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) Bs[k] = fma(wji, grp.from_full(Td[k], j), Bs[k]);
+      }
+      const MassMoment M = mass(l);
+      double Bm[12], G[12];
+      mul_mass(Bs, M, Bm);
+      load12(L.G + 12 * l, G);
+      double w6[6];
+      wrench_tangent(G, Bm, T, Td, w6);
+      for (int k = 0; k < 6; ++k) ws[L.accd + 6 * l + k] = w6[k];
+    }
+    for (int l = N - 1; l >= 0; --l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      double a[6], ad[6], V[6], T[12];
+      for (int k = 0; k < 6; ++k) {
+        a[k] = ws[L.acc + 6 * l + k];
+        ad[k] = ws[L.accd + 6 * l + k];
+        V[k] = ws[L.V + 6 * l + k];
+      }
+      load12(L.T + 12 * l, T);
+      const double o[3] = {T[3], T[7], T[11]};
+      double od[3];
+      cross(V, o, od);
+      od[0] += V[3];
+      od[1] += V[4];
+      od[2] += V[5];
+      double t1[3], t2[3], t3[3];
+      cross(o, a + 3, t1);
+      const double mo[3] = {a[0] - t1[0], a[1] - t1[1], a[2] - t1[2]};
+      cross(od, a + 3, t2);
+      cross(o, ad + 3, t3);
+      const double mdo[3] = {ad[0] - t2[0] - t3[0], ad[1] - t2[1] - t3[1], ad[2] - t2[2] - t3[2]};
+      double dJ[9];
+      if (nd == 3) {
+        double th[3], v[3];
+        for (int k = 0; k < 3; ++k) {
+          th[k] = ws[L.xt + d0 + k];
+          v[k] = ws[L.rt + d0 + k];
+        }
+        jr_tangent(th, v, dJ);
+      }
+      for (int k = 0; k < nd; ++k) {
+        const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
+                             ws[L.axes + 9 * l + 3 * k + 2]};
+        double wd[3];
+        cross(V, w, wd);
+        if (nd == 3) {
+          // + R dJr e_k
+          for (int r = 0; r < 3; ++r)
+            wd[r] += fma(T[4 * r], dJ[k], fma(T[4 * r + 1], dJ[3 + k], T[4 * r + 2] * dJ[6 + k]));
+        }
+        ws[L.gt + d0 + k] = 2.0 * (dot3(wd, mo) + dot3(w, mdo));
+      }
+      if (p >= 0)
+        for (int k = 0; k < 6; ++k) ws[L.accd + 6 * p + k] += ad[k];
+    }
+  }
+
+  // Full evaluation at xt: returns E (group total, identical on the group's
+  // lanes); rt = residual of the own stage; gt = dE/dq of the own stage.
+  __device__ double evaluate(const double* tau) const {
+    double e = primal(tau);
+    double E = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) E += grp.from_full(e, j);
+    if (S == 1) {
+      for (int d = 0; d < n; ++d) ws[L.gt + d] = ws[L.rt + d];
+    } else {
+      tangent();
+    }
+    return E;
+  }
+
+  // ------------------------------------------------- L-BFGS vector algebra
+  // (group-divergent code: group-mask shuffles only)
+  __device__ double gdot(int a, int b_) const {
+    double s = 0.0;
+    for (int d = 0; d < n; ++d) s = fma(ws[a + d], ws[b_ + d], s);
+    return grp.sum(s);
+  }
+  // v <- P v for the own slice of v at offset a (Kronecker: stage block Ps,
+  // joint blocks Pb).
+  __device__ __noinline__ void precond(int a) const {
+    for (int l = 0; l < N; ++l) {
+      const int d0 = B.dof[l], nd = ndof(l);
+      double u[3], t[3];
+      for (int k = 0; k < nd; ++k) u[k] = ws[a + d0 + k];
+      for (int r = 0; r < nd; ++r) {
+        double s = 0.0;
+        for (int c = 0; c < nd; ++c) s = fma(ws[L.Pb + 9 * l + nd * r + c], u[c], s);
+        t[r] = s;
+      }
+      for (int k = 0; k < nd; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) s = fma(K.Ps[i][j], grp.from(t[k], j), s);
+        ws[a + d0 + k] = s;
+      }
+    }
+  }
+};
+
+}  // namespace pbad

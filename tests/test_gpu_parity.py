@@ -1,0 +1,147 @@
+"""CUDA path vs the CPU oracle, element by element, through the C ABI."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1709_04145_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+# Relative tolerance of single objective/gradient evaluations (FP64 on both
+# sides; the CUDA path contracts to FMA and sums in another order).
+REL_EVAL = 1e-10
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _pbad():
+    import paper_1709_04145_b300 as P
+    return P
+
+
+def _relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def _specs():
+    return [
+        I.rod_chain(5, 3, name="rod3"),
+        I.ball_chain(7, 4, seed=11, radius=0.1),
+        I.humanoid(3, seed=12),
+        I.rod_chain(33, 7, name="rod7"),  # ragged count: spans several warps
+    ]
+
+
+def _random_case(spec, S, seed, dt):
+    rng = np.random.default_rng(seed)
+    B, n = spec.count, spec.n_dof
+    q_cur = rng.uniform(-0.6, 0.6, size=(B, n))
+    q_prev = q_cur + rng.normal(0, 0.02, size=(B, n))
+    tau = rng.normal(0, 0.3, size=(B, n))
+    qs = q_cur[:, None, :] + rng.normal(0, 0.03, size=(B, S, n))
+    return q_prev, q_cur, tau, qs
+
+
+@pytest.mark.parametrize("S", [1, 2, 3, 4])
+def test_eval_matches_oracle(S):
+    torch = _torch()
+    P = _pbad()
+    dt = 0.02
+    specs = _specs()
+    models = [P.Model.from_spec(s) for s in specs]
+    batch = P.Batch(models, max_stages=5, max_history=8)
+    cases = [_random_case(s, S, 100 + k, dt) for k, s in enumerate(specs)]
+    dev = torch.device("cuda:0")
+    cat = lambda idx: torch.tensor(np.concatenate([c[idx].reshape(-1) for c in cases]), device=dev)
+    q_prev, q_cur, tau, qs = cat(0), cat(1), cat(2), cat(3)
+    E, grad, resid = P.eval_objective_grad(batch, qs, q_prev, q_cur, tau, dt, S)
+    torch.cuda.synchronize()
+    E = E.cpu().numpy()
+    grads = batch.unpack(grad.cpu().numpy(), S)
+    resids = batch.unpack(resid.cpu().numpy(), S)
+    for k, spec in enumerate(specs):
+        qp, qc, ta, q_s = cases[k]
+        for b in range(spec.count):
+            om = O.OracleModel.from_spec(spec, b)
+            Eo, ro, go, _ = om.eval(S, dt, q_s[b], qp[b], qc[b], ta[b], True)
+            Eg = E[batch.inst_off[k] + b]
+            assert abs(Eg - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (spec.name, b, Eg, Eo)
+            assert _relerr(resids[k][b].reshape(-1), ro) < REL_EVAL, (spec.name, b)
+            assert _relerr(grads[k][b].reshape(-1), go) < REL_EVAL, (spec.name, b)
+
+
+def test_eval_without_tau_and_single_instance():
+    torch = _torch()
+    P = _pbad()
+    spec = I.rod_chain(1, 1, name="rod1")
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=2, max_history=0)
+    dev = torch.device("cuda:0")
+    q = torch.tensor([0.3], dtype=torch.float64, device=dev)
+    qs = torch.tensor([0.31, 0.33], dtype=torch.float64, device=dev)
+    E, grad, resid = P.eval_objective_grad(batch, qs, q - 0.01, q, None, 0.05, 2)
+    om = O.OracleModel.from_spec(spec, 0)
+    Eo, ro, go, _ = om.eval(2, 0.05, [0.31, 0.33], [0.29], [0.3], [0.0], True)
+    assert abs(E.item() - Eo) <= REL_EVAL * abs(Eo)
+    assert _relerr(grad.cpu().numpy(), go) < REL_EVAL
+    assert _relerr(resid.cpu().numpy(), ro) < REL_EVAL
+
+
+def test_pendulum_rollout_matches_oracle():
+    """3-link planar rod pendulum, dt = 0.01, one stage, L-BFGS history 5,
+    |grad| < 1e-10, 200 steps: max |dq| <= 1e-7 rad over the trajectory."""
+    torch = _torch()
+    P = _pbad()
+    w = I.pendulum3()
+    spec = w["spec"]
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=1, max_history=5)
+    dev = torch.device("cuda:0")
+    q0 = torch.tensor(w["q0"].reshape(-1), device=dev)
+    out = P.rollout(batch, q0, q0, None, w["n_steps"], w["dt"], 1, P.LBFGS, 5, w["tol"], 1000)
+    torch.cuda.synchronize()
+    om = O.OracleModel.from_spec(spec, 0)
+    ref = om.rollout(1, w["dt"], w["q0"][0], w["q0"][0], np.zeros((w["n_steps"], 3)), "lbfgs", 5,
+                     w["tol"], 1000)
+    assert ref["status"] == 0
+    assert int(out["status"][0]) == 0
+    dq = np.max(np.abs(out["traj_cur"].cpu().numpy() - ref["traj_cur"]))
+    assert dq <= 1e-7, dq
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_rollout_matches_oracle_chains(S):
+    """Hinge and ball chains with torques, L-BFGS, several steps."""
+    torch = _torch()
+    P = _pbad()
+    dt = 0.01
+    n_steps = 6
+    specs = [I.rod_chain(3, 4, name="rod4"), I.ball_chain(2, 3, seed=21, radius=0.2)]
+    models = [P.Model.from_spec(s) for s in specs]
+    batch = P.Batch(models, max_stages=3, max_history=8)
+    states = [I.random_state(s, 30 + k, pose_scale=0.4, vel_sigma=0.3) for k, s in enumerate(specs)]
+    taus = [I.torques(s, n_steps, 40 + k, sigma=0.1) for k, s in enumerate(specs)]
+    nodes, _ = O.colloc(S)
+    qps = [q0 + nodes[0] * dt * qd0 for q0, qd0 in states]
+    dev = torch.device("cuda:0")
+    q_cur = torch.tensor(np.concatenate([q0.reshape(-1) for q0, _ in states]), device=dev)
+    q_prev = torch.tensor(np.concatenate([qp.reshape(-1) for qp in qps]), device=dev)
+    tau = torch.tensor(np.concatenate([t.reshape(n_steps, -1) for t in taus], axis=1).reshape(-1),
+                       device=dev)
+    tol = 1e-9
+    out = P.rollout(batch, q_prev, q_cur, tau, n_steps, dt, S, P.LBFGS, 8, tol, 2000)
+    torch.cuda.synchronize()
+    traj = out["traj_cur"].cpu().numpy()
+    st = out["status"].cpu().numpy()
+    for k, spec in enumerate(specs):
+        for b in range(spec.count):
+            om = O.OracleModel.from_spec(spec, b)
+            ref = om.rollout(S, dt, qps[k][b], states[k][0][b], taus[k][:, b, :], "lbfgs", 8, tol, 2000)
+            a = batch.dof_off[k] + b * spec.n_dof
+            got = traj[:, a:a + spec.n_dof]
+            assert ref["status"] == st[batch.inst_off[k] + b]
+            if ref["status"] == 0:
+                assert np.max(np.abs(got - ref["traj_cur"])) <= 1e-7, (spec.name, b)
