@@ -154,6 +154,32 @@ PBAD_API int pbad_rollout(pbad_batch* batch, const double* q_prev0, const double
                  double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
                  int32_t* status, int32_t* iters, int32_t* evals, void* stream);
 
+/* Bytes of the fixed device scratch used by pbad_eval_objective_grad_static. */
+#define PBAD_STATIC_SCRATCH_BYTES (8 * 1024 * 1024)
+
+/* The same evaluation as pbad_eval_objective_grad for the instances of one
+ * model, without a batch: its scratch is a fixed array of
+ * PBAD_STATIC_SCRATCH_BYTES inside this library (every GPU that loads the
+ * library holds it until the process exits), so the call allocates nothing.
+ * The paper has no counterpart; this is for callers that cannot call
+ * cudaMalloc when they evaluate - a host application whose device memory is
+ * wholly owned by its own allocator, or a latency-bound control loop that
+ * cannot afford an allocation's implicit synchronisation.
+ *   Arrays as for pbad_eval_objective_grad with D = count * n of the model.
+ *   The first call on a device looks up the scratch's device address with
+ *   that device current; make that first call before any stream capture.
+ *   Every call shares the one scratch array and it keeps the last call's
+ *   contents (each evaluation writes every scratch word before reading it,
+ *   so nothing needs clearing); calls whose kernels overlap on the GPU race
+ *   on it, so serialise them (one stream, or events).
+ * Errors: PBAD_ERR_ARG when the model needs more scratch than
+ * PBAD_STATIC_SCRATCH_BYTES (the message gives both sizes), or for the
+ * argument errors of pbad_eval_objective_grad. */
+PBAD_API int pbad_eval_objective_grad_static(const pbad_model* model, const double* q_star,
+                                             const double* q_prev, const double* q_cur,
+                                             const double* tau, double dt, int32_t stages,
+                                             double* E, double* grad, double* resid, void* stream);
+
 /* Measures the device's FP64 FMA throughput (GFLOP/s, FMA = 2 flops) with
  * the library's own probe kernel; synchronises the device. */
 PBAD_API int pbad_fp64_peak(int32_t device, double* gflops);

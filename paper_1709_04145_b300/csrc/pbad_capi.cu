@@ -561,3 +561,43 @@ int pbad_fp64_peak(int32_t device, double* gflops) {
 }
 
 }  // extern "C"
+
+// Launch description of one model with a caller-provided lane workspace, for
+// entry points that do not own a batch. Returns PBAD_OK or an error code;
+// on success *lanes and *per_lane give the workspace the launch touches
+// (lanes * per_lane doubles from ws).
+namespace pbad {
+int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, LaunchArgs* A, int* grid,
+                       int64_t* lanes, int64_t* per_lane) {
+  if (!m) return fail(PBAD_ERR_ARG, "null model");
+  std::memset(A, 0, sizeof(LaunchArgs));
+  int rc = make_colloc(S, dt, &A->K);
+  if (rc != PBAD_OK) return rc;
+  const int64_t warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
+  const int64_t blocks = (warps + 3) / 4;
+  WsLayout L;
+  L.make(m->N, m->n, 0);
+  *lanes = blocks * 4 * 32;
+  *per_lane = L.total;
+  A->nb = 1;
+  A->D = m->count * m->n;
+  Bucket& B = A->bk[0];
+  B.N = m->N;
+  B.n = m->n;
+  B.count = (int)m->count;
+  B.parent = m->d_topo;
+  B.jtype = m->d_topo + m->N;
+  B.dof = m->d_topo + 2 * m->N;
+  B.axis = m->d_axis;
+  B.mm = m->d_mm;
+  B.rest = m->d_rest;
+  for (int c = 0; c < 3; ++c) B.g[c] = m->g[c];
+  B.ws = ws;
+  B.ws_stride = *lanes;
+  B.block_begin = 0;
+  *grid = (int)blocks;
+  return PBAD_OK;
+}
+int model_device(const pbad_model* m) { return m->device; }
+int set_error(int code, const char* msg) { return fail(code, msg); }
+}  // namespace pbad
