@@ -78,6 +78,8 @@ extern "C" {
 #define PBAD_CHOL_FAIL 3  /* Newton system not factorable for any damping */
 #define PBAD_NONFINITE 4  /* NaN or Inf in E, r or the gradient */
 
+#define PBAD_BATCH_NEWTON 1 /* batch flag: reserve the dense Newton/adjoint workspace */
+
 #define PBAD_MAX_STAGES 5
 #define PBAD_MAX_HISTORY 16
 #define PBAD_MAX_MODELS 8
@@ -114,9 +116,11 @@ PBAD_API int pbad_model_info(const pbad_model* model, int32_t* n_links, int32_t*
 
 /* Creates a batch over 1..PBAD_MAX_MODELS models (same device) and allocates
  * the solver workspace for up to max_stages stages and L-BFGS history
- * max_history. The models must outlive the batch. */
+ * max_history; flags = PBAD_BATCH_NEWTON also reserves the dense
+ * (S n)^2 Newton storage per lane (needed by the Newton solver). The models
+ * must outlive the batch. */
 PBAD_API int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_stages,
-                      int32_t max_history, pbad_batch** out);
+                      int32_t max_history, int32_t flags, pbad_batch** out);
 PBAD_API int pbad_batch_destroy(pbad_batch* batch);
 /* n_instances = sum count_m; n_dof_total = D; workspace_bytes = device bytes
  * the batch owns. Any output pointer may be NULL. */

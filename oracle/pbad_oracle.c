@@ -1064,9 +1064,12 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
  *   q <- q - [H + lambda I]^-1 grad,
  * H = Jr^T Jr and grad = Jr^T r for S >= 2 (Eq. EQHOC, sum of squares);
  * H = Hmass/dt^2 (Gauss-Newton of the integral of squares) and grad = dE/dq
- * for S == 1. lambda starts at 1e-8 max diag(H), is divided by 10 on an
- * accepted step and multiplied by 10 on a rejected step or a failed
- * factorisation. */
+ * for S == 1. lambda starts at 1e-12 max diag(H), is divided by 10 on an
+ * accepted step (floor 1e-20 max diag(H)) and multiplied by 10 on a rejected
+ * step or a failed factorisation. The paper only asks that lambda keep E
+ * decreasing; the small start and floor keep lambda below the smallest
+ * eigenvalues of Jr^T Jr, whose condition number reaches 1e12-1e16 for thin
+ * links on ball joints. */
 static int lm_solve(om_model *m, int S, double dt, const double *qp,
                     const double *qc, const double *tau, double tol,
                     int max_iter, double *x, int *iters, int *evals) {
@@ -1108,12 +1111,13 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
     }
     double hmax = 0;
     for (int i = 0; i < Sn; ++i) hmax = fmax(hmax, H[i * Sn + i]);
-    if (lambda < 0) lambda = 1e-8 * hmax;
-    int accepted = 0;
+    if (lambda < 0) lambda = 1e-12 * hmax;
+    int accepted = 0, last_chol_fail = 0;
     for (int t = 0; t < 60; ++t) {
       memcpy(A, H, sizeof(double) * Sn * Sn);
       for (int i = 0; i < Sn; ++i) A[i * Sn + i] += lambda;
-      if (cholesky(A, Sn) != 0) { lambda *= 10; continue; }
+      last_chol_fail = 0;
+      if (cholesky(A, Sn) != 0) { lambda *= 10; last_chol_fail = 1; continue; }
       for (int i = 0; i < Sn; ++i) dx[i] = -gr[i];
       chol_solve(A, Sn, dx);
       for (int i = 0; i < Sn; ++i) xt[i] = x[i] + dx[i];
@@ -1125,8 +1129,8 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
       if (ok) { accepted = 1; E = Et; break; }
       lambda *= 10;
     }
-    if (!accepted) { status = OM_LS_FAIL; break; }
-    lambda = fmax(lambda * 0.1, 1e-12 * hmax);
+    if (!accepted) { status = last_chol_fail ? OM_CHOL_FAIL : OM_LS_FAIL; break; }
+    lambda = fmax(lambda * 0.1, 1e-20 * hmax);
     memcpy(x, xt, sizeof(double) * Sn);
     E = om_eval(m, S, dt, x, qp, qc, tau, r, NULL, J);
     k++;

@@ -107,12 +107,12 @@ class Batch:
     use ``pack``/``unpack`` to convert from/to per-model (count, n) arrays.
     """
 
-    def __init__(self, models, max_stages: int = 5, max_history: int = 16):
+    def __init__(self, models, max_stages: int = 5, max_history: int = 16, newton: bool = False):
         self.models = list(models)
         arr = (C.c_void_p * len(self.models))(*[m._h for m in self.models])
         h = C.c_void_p()
-        check(lib().pbad_batch_create(len(self.models), arr, max_stages, max_history, C.byref(h)),
-              "pbad_batch_create")
+        check(lib().pbad_batch_create(len(self.models), arr, max_stages, max_history,
+                                      1 if newton else 0, C.byref(h)), "pbad_batch_create")
         self._h = h
         self.max_stages = max_stages
         self.max_history = max_history

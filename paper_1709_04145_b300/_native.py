@@ -42,7 +42,8 @@ def lib():
                                         C.POINTER(C.c_void_p)]
         L.pbad_model_destroy.argtypes = [vp]
         L.pbad_model_info.argtypes = [vp, C.POINTER(C.c_int32), C.POINTER(C.c_int32), i64p]
-        L.pbad_batch_create.argtypes = [i32, C.POINTER(C.c_void_p), i32, i32, C.POINTER(C.c_void_p)]
+        L.pbad_batch_create.argtypes = [i32, C.POINTER(C.c_void_p), i32, i32, i32,
+                                        C.POINTER(C.c_void_p)]
         L.pbad_batch_destroy.argtypes = [vp]
         L.pbad_batch_info.argtypes = [vp, i64p, i64p, i64p]
         L.pbad_eval_objective_grad.argtypes = [vp, dp, dp, dp, dp, f64, i32, dp, dp, dp, vp]

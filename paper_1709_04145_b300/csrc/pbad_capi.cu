@@ -57,7 +57,7 @@ struct pbad_model {
 };
 
 struct pbad_batch {
-  int device = 0, max_stages = 0, max_history = 0;
+  int device = 0, max_stages = 0, max_history = 0, flags = 0;
   std::vector<pbad_model*> models;
   std::vector<int64_t> inst_off, dof_off, lanes;
   std::vector<size_t> ws_off;  // in doubles
@@ -273,8 +273,9 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   if (!(tol >= 0.0)) return fail(PBAD_ERR_ARG, "tol must be >= 0");
   for (size_t k = 0; k < bt->models.size(); ++k) {
     const int sv = solvers ? solvers[k] : PBAD_LBFGS;
-    if (sv == PBAD_NEWTON) return fail(PBAD_ERR_UNSUPPORTED, "Newton solver not built");
-    if (sv != PBAD_LBFGS) return fail(PBAD_ERR_ARG, "unknown solver");
+    if (sv != PBAD_LBFGS && sv != PBAD_NEWTON) return fail(PBAD_ERR_ARG, "unknown solver");
+    if (sv == PBAD_NEWTON && !(bt->flags & PBAD_BATCH_NEWTON))
+      return fail(PBAD_ERR_ARG, "the Newton solver needs a batch created with PBAD_BATCH_NEWTON");
   }
   DeviceGuard dg(bt->device);
   LaunchArgs A;
@@ -295,6 +296,7 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   A.status = status;
   A.iters = iters;
   A.evals = evals;
+  A.dense_stages = (bt->flags & PBAD_BATCH_NEWTON) ? bt->max_stages : 0;
   cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e = launch_rollout(stages, A, grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
@@ -406,7 +408,7 @@ int pbad_model_info(const pbad_model* m, int32_t* n_links, int32_t* n_dof, int64
 }
 
 int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_stages,
-                      int32_t max_history, pbad_batch** out) {
+                      int32_t max_history, int32_t flags, pbad_batch** out) {
   if (!out) return fail(PBAD_ERR_ARG, "null out");
   *out = nullptr;
   if (n_models < 1 || n_models > PBAD_MAX_MODELS || !models)
@@ -417,8 +419,13 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
     return fail(PBAD_ERR_ARG, "max_history must be in 0..PBAD_MAX_HISTORY");
   auto* bt = new (std::nothrow) pbad_batch();
   if (!bt) return fail(PBAD_ERR_ALLOC, "host allocation");
+  if (flags & ~PBAD_BATCH_NEWTON) {
+    delete bt;
+    return fail(PBAD_ERR_ARG, "unknown batch flags");
+  }
   bt->max_stages = max_stages;
   bt->max_history = max_history;
+  bt->flags = flags;
   size_t ws = 0;
   for (int k = 0; k < n_models; ++k) {
     pbad_model* m = models[k];
@@ -444,7 +451,7 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
       if (l > lanes) lanes = l;
     }
     WsLayout L;
-    L.make(m->N, m->n, max_history);
+    L.make(m->N, m->n, max_history, (flags & PBAD_BATCH_NEWTON) ? max_stages : 0);
     bt->lanes.push_back(lanes);
     bt->ws_off.push_back(ws);
     ws += (size_t)lanes * L.total;

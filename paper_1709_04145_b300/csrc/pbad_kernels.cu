@@ -64,8 +64,7 @@ __global__ void __launch_bounds__(128) k_eval(const __grid_constant__ LaunchArgs
 // iteration-level scheduling of the paper's Fig. GPU, inside a warp.
 // ------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(128) k_rollout_lbfgs(const __grid_constant__ LaunchArgs A) {
-  const Bucket& B = A.bk[find_bucket(A)];
+__device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B) {
   const LaneId<S> id(B);
   const bool active = id.real && id.inst < B.count;
   const int b = active ? (int)id.inst : 0;
@@ -249,6 +248,169 @@ __global__ void __launch_bounds__(128) k_rollout_lbfgs(const __grid_constant__ L
 }
 
 // ------------------------------------------------------------------------
+// Persistent Newton (Levenberg-Marquardt) rollout, Section 5:
+//   q <- q - [H + lambda I]^-1 g,  H = Jr^T Jr, g = Jr^T r   (S >= 2)
+//                                  H = int dP/dq^T dP/dq / dt^2, g = dE/dq (S == 1)
+// lambda starts at 1e-12 max diag(H) per step, x0.1 (floor 1e-20 max diag)
+// after an accepted step, x10 after a rejected step or a failed Cholesky
+// factorisation; a step is accepted when E decreases. Each loop trip runs
+// the residual pass at every group's trial point; when any group of the warp
+// needs a new Jacobian, the warp builds it (S n tangent passes), then each
+// group forms H, factorises and solves on its own.
+// ------------------------------------------------------------------------
+constexpr int kLmMaxTrials = 60;
+
+template <int S>
+__device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B) {
+  const LaneId<S> id(B);
+  const bool active = id.real && id.inst < B.count;
+  const int b = active ? (int)id.inst : 0;
+  Ctx<S> c(B, A.K, b, id.lane_id, A.history, A.dense_stages);
+  const int n = c.n;
+  const auto& L = c.L;
+  const Lane& ws = c.ws;
+  const int64_t D = A.D;
+
+  for (int d = 0; d < n; ++d) {
+    ws[L.qp + d] = A.q_prev0[c.gdof(d)];
+    ws[L.qc + d] = A.q_cur0[c.gdof(d)];
+  }
+  int step = 0, phase = kFirst, k = 0, trials = 0;
+  int worst = kConverged, iters_total = 0, evals_total = 0;
+  double E = 0.0, lambda = -1.0, hmax = 0.0;
+  c.setup();
+  if (!active) phase = kDone;
+
+  auto finish = [&](int st) {
+    worst = max(worst, st);
+    for (int d = 0; d < n; ++d) {
+      const double xs = c.grp.from(ws[L.x + d], S - 1);
+      const double xp = (S == 1) ? ws[L.qc + d] : c.grp.from(ws[L.x + d], S - 2);
+      ws[L.qp + d] = xp;
+      ws[L.qc + d] = xs;
+      if (c.i == 0) {
+        if (A.traj_cur) A.traj_cur[(int64_t)step * D + c.gdof(d)] = xs;
+        if (A.traj_prev) A.traj_prev[(int64_t)step * D + c.gdof(d)] = xp;
+      }
+    }
+    if (A.q_stages_out && step == A.n_steps - 1)
+      for (int d = 0; d < n; ++d) A.q_stages_out[c.gstage(d)] = ws[L.x + d];
+    ++step;
+    if (step >= A.n_steps) {
+      phase = kDone;
+    } else {
+      c.setup();
+      phase = kFirst;
+    }
+  };
+
+  while (__any_sync(0xffffffffu, phase != kDone)) {
+    const double* tau = A.tau ? A.tau + (int64_t)min(step, A.n_steps - 1) * D : nullptr;
+    const double Et = c.evaluate_primal(tau);
+    // 0: nothing, 1: needs a Jacobian at x, 2: needs a new factorisation
+    int need = 0;
+    if (phase != kDone) {
+      ++evals_total;
+      if (phase == kFirst) {
+        for (int d = 0; d < n; ++d) {
+          ws[L.x + d] = ws[L.xt + d];
+          ws[L.r + d] = ws[L.rt + d];
+        }
+        E = Et;
+        k = 0;
+        lambda = -1.0;
+        need = 1;
+      } else {
+        double rr = 0.0, rrt = 0.0, fin = 1.0;
+        for (int d = 0; d < n; ++d) {
+          rr = fma(ws[L.r + d], ws[L.r + d], rr);
+          rrt = fma(ws[L.rt + d], ws[L.rt + d], rrt);
+          if (!isfinite(ws[L.rt + d])) fin = 0.0;
+        }
+        rr = c.grp.sum(rr);
+        rrt = c.grp.sum(rrt);
+        fin = c.grp.sum(fin);
+        const bool ok = fin == (double)S && isfinite(Et) &&
+                        (Et < E || (S == 1 && Et <= E + kLsEps * fabs(E) && rrt < rr));
+        if (ok) {
+          for (int d = 0; d < n; ++d) {
+            ws[L.x + d] = ws[L.xt + d];
+            ws[L.r + d] = ws[L.rt + d];
+          }
+          E = Et;
+          lambda = fmax(lambda * 0.1, 1e-20 * hmax);
+          ++k;
+          ++iters_total;
+          need = 1;
+        } else {
+          lambda *= 10.0;
+          if (++trials >= kLmMaxTrials) finish(kLsFail);
+          else need = 2;
+        }
+      }
+      if (need == 1) {
+        double rr = 0.0, fin = 1.0;
+        for (int d = 0; d < n; ++d) {
+          rr = fma(ws[L.r + d], ws[L.r + d], rr);
+          if (!isfinite(ws[L.r + d])) fin = 0.0;
+        }
+        rr = c.grp.sum(rr);
+        fin = c.grp.sum(fin);
+        if (fin != (double)S || !isfinite(E)) { finish(kNonFinite); need = 0; }
+        else if (sqrt(rr) < A.tol) { finish(kConverged); need = 0; }
+        else if (k >= A.max_iter) { finish(kMaxIter); need = 0; }
+      }
+    }
+    // Jacobian at x (= the point just evaluated) for every group that needs one
+    if (__any_sync(0xffffffffu, need == 1)) c.build_jacobian();
+    if (need == 1) {
+      hmax = c.gram();
+      if (lambda < 0.0) lambda = 1e-12 * hmax;
+      trials = 0;
+      need = 2;
+    }
+    if (need == 2) {
+      bool solved = false;
+      while (!solved) {
+        if (c.factor_solve(lambda)) {
+          solved = true;
+        } else {
+          lambda *= 10.0;
+          if (++trials >= kLmMaxTrials) break;
+        }
+      }
+      if (!solved) {
+        finish(kCholFail);
+      } else {
+        for (int d = 0; d < n; ++d) ws[L.xt + d] = ws[L.x + d] + ws[L.dl + c.i * n + d];
+        phase = kTrial;
+      }
+    }
+  }
+  if (active && c.i == 0) {
+    if (A.status) A.status[B.inst_off + b] = worst;
+    if (A.iters) A.iters[B.inst_off + b] = iters_total;
+    if (A.evals) A.evals[B.inst_off + b] = evals_total;
+  }
+  if (active && c.i == 0) {
+    for (int d = 0; d < n; ++d) {
+      if (A.q_prev_out) A.q_prev_out[c.gdof(d)] = ws[L.qp + d];
+      if (A.q_cur_out) A.q_cur_out[c.gdof(d)] = ws[L.qc + d];
+    }
+  }
+}
+
+// One launch serves every bucket of the batch; each block runs the solver of
+// its bucket (L-BFGS or Newton), so an uneven batch with mixed solvers is a
+// single persistent launch.
+template <int S>
+__global__ void __launch_bounds__(128) k_rollout(const __grid_constant__ LaunchArgs A) {
+  const Bucket& B = A.bk[find_bucket(A)];
+  if (B.solver == 1) rollout_newton<S>(A, B);
+  else rollout_lbfgs<S>(A, B);
+}
+
+// ------------------------------------------------------------------------
 // FP64 FMA throughput probe (roofline denominator): dependent chains, 8
 // independent chains per thread.
 // ------------------------------------------------------------------------
@@ -277,7 +439,7 @@ cudaError_t PBAD_CAT(launch_eval_s, PBAD_S)(const LaunchArgs& A, int grid, cudaS
   return cudaGetLastError();
 }
 cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
-  k_rollout_lbfgs<PBAD_S><<<grid, 128, 0, s>>>(A);
+  k_rollout<PBAD_S><<<grid, 128, 0, s>>>(A);
   return cudaGetLastError();
 }
 #if PBAD_S == 1

@@ -26,8 +26,10 @@ enum Status { kConverged = 0, kMaxIter = 1, kLsFail = 2, kCholFail = 3, kNonFini
 
 // Offsets (in doubles) of one lane's workspace.
 struct WsLayout {
-  int T, G, acc, axes, V, accd, C, Pb, x, g, d, xt, gt, r, rt, qp, qc, sh, yh, rho, total;
-  __host__ __device__ void make(int N, int n, int m) {
+  int T, G, acc, axes, V, accd, C, Pb, x, g, d, xt, gt, r, rt, qp, qc, sh, yh, rho;
+  int u, jc, J, H, A, gg, dl;  // dense Newton storage (Sd stages; absent when Sd == 0)
+  int64_t total;
+  __host__ __device__ void make(int N, int n, int m, int Sd = 0) {
     int o = 0;
     T = o; o += 12 * N;
     G = o; o += 12 * N;
@@ -49,6 +51,14 @@ struct WsLayout {
     sh = o; o += m * n;
     yh = o; o += m * n;
     rho = o; o += (m > 0 ? m : 1);
+    const int Sn = Sd * n;
+    u = o; o += (Sd ? n : 0);
+    jc = o; o += (Sd ? n : 0);
+    gg = o; o += Sn;
+    dl = o; o += Sn;
+    J = o; o += n * Sn;
+    H = o; o += Sn * Sn;
+    A = o; o += Sn * Sn;
     total = o;
   }
 };
@@ -58,6 +68,7 @@ struct LaunchArgs {
   Bucket bk[kMaxBuckets];
   Colloc K;
   int history, max_iter, n_steps;
+  int dense_stages;        // stages the dense Newton storage was sized for (0 = none)
   double tol;
   int64_t D;               // total DOFs of the batch (row length of DOF-packed arrays)
   const double* q_prev0;   // [D]
@@ -91,11 +102,11 @@ struct Ctx {
   int i;       // own stage
   int N, n;
 
-  __device__ Ctx(const Bucket& B_, const Colloc& K_, int b_, int64_t lane_id, int m)
+  __device__ Ctx(const Bucket& B_, const Colloc& K_, int b_, int64_t lane_id, int m, int Sd = 0)
       : B(B_), K(K_), b(b_) {
     N = B.N;
     n = B.n;
-    L.make(N, n, m);
+    L.make(N, n, m, Sd);
     ws.p = B.ws + lane_id;
     ws.st = B.ws_stride;
     i = grp.stage;
@@ -363,12 +374,19 @@ struct Ctx {
     return (S == 1) ? (Eown - tq) : rr;
   }
 
-  // ---------------------------------------------------- tangent (S >= 2)
-  // Tangent of the residual pass of the own stage k along v_k = r_k, with
-  // the seeds perturbed by B_k,l = sum_i Wu[i][k] Tdot_i,l M_l; gives
-  // (Jr^T r)_k into gt (times 2: the gradient of Eq. EQHOC). Needs the
-  // primal pass's T, G, axes and acc. Convergent across the warp.
-  __device__ __noinline__ void tangent() const {
+  // ------------------------------------------------------- tangent passes
+  // d/de of the residual pass of the own stage along a direction v (own
+  // stage slice at workspace offset `dir`), with the seeds perturbed by
+  //   kGrad: B_k,l = sum_i Wu[i][k] Tdot_i,l M_l  -> (Jr^T v)_k   (Eq. EQHOC gradient)
+  //   kJvp:  B_i,l = sum_j Wu[i][j] Tdot_j,l M_l  -> (Jr v)_i     (Jacobian columns)
+  //   kGn:   as kJvp but without the second-derivative terms of the
+  //          kinematics: the Gauss-Newton product int dP/dq^T dP/dq v / dt^2
+  //          of Eq. EQ (one stage).
+  // The result, times `scale`, goes to offset `out`. Needs the primal pass's
+  // T, G, axes and acc at the same point. Convergent across the warp.
+  enum TangentMode { kGrad = 0, kJvp = 1, kGn = 2 };
+  template <int MODE>
+  __device__ __noinline__ void tangent_pass(int dir, int out, double scale) const {
     for (int l = 0; l < N; ++l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
       double V[6];
@@ -383,7 +401,7 @@ struct Ctx {
       for (int k = 0; k < nd; ++k) {
         const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
                              ws[L.axes + 9 * l + 3 * k + 2]};
-        const double vk = ws[L.rt + d0 + k];
+        const double vk = ws[dir + d0 + k];
         double ow[3];
         cross(o, w, ow);
         for (int c = 0; c < 3; ++c) {
@@ -406,70 +424,89 @@ struct Ctx {
       Td[3] += V[3];
       Td[7] += V[4];
       Td[11] += V[5];
-      // B = (sum_i Wu[i][own] Tdot_i) M
       double Bs[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) Bs[k] = 0.0;
 #pragma unroll
       for (int j = 0; j < S; ++j) {
-        const double wji = K.Wu[j][i];
+        const double wgt = (MODE == kGrad) ? K.Wu[j][i] : K.Wu[i][j];
 #pragma unroll
-        for (int k = 0; k < 12; ++k) Bs[k] = fma(wji, grp.from_full(Td[k], j), Bs[k]);
+        for (int k = 0; k < 12; ++k) Bs[k] = fma(wgt, grp.from_full(Td[k], j), Bs[k]);
       }
       const MassMoment M = mass(l);
-      double Bm[12], G[12];
+      double Bm[12];
       mul_mass(Bs, M, Bm);
-      load12(L.G + 12 * l, G);
       double w6[6];
-      wrench_tangent(G, Bm, T, Td, w6);
+      if (MODE == kGn) {
+        wrench(Bm, T, w6);
+      } else {
+        double G[12];
+        load12(L.G + 12 * l, G);
+        wrench_tangent(G, Bm, T, Td, w6);
+      }
       for (int k = 0; k < 6; ++k) ws[L.accd + 6 * l + k] = w6[k];
     }
     for (int l = N - 1; l >= 0; --l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
-      double a[6], ad[6], V[6], T[12];
-      for (int k = 0; k < 6; ++k) {
-        a[k] = ws[L.acc + 6 * l + k];
-        ad[k] = ws[L.accd + 6 * l + k];
-        V[k] = ws[L.V + 6 * l + k];
-      }
+      double ad[6], T[12];
+      for (int k = 0; k < 6; ++k) ad[k] = ws[L.accd + 6 * l + k];
       load12(L.T + 12 * l, T);
       const double o[3] = {T[3], T[7], T[11]};
-      double od[3];
-      cross(V, o, od);
-      od[0] += V[3];
-      od[1] += V[4];
-      od[2] += V[5];
-      double t1[3], t2[3], t3[3];
-      cross(o, a + 3, t1);
-      const double mo[3] = {a[0] - t1[0], a[1] - t1[1], a[2] - t1[2]};
-      cross(od, a + 3, t2);
-      cross(o, ad + 3, t3);
-      const double mdo[3] = {ad[0] - t2[0] - t3[0], ad[1] - t2[1] - t3[1], ad[2] - t2[2] - t3[2]};
-      double dJ[9];
-      if (nd == 3) {
-        double th[3], v[3];
-        for (int k = 0; k < 3; ++k) {
-          th[k] = ws[L.xt + d0 + k];
-          v[k] = ws[L.rt + d0 + k];
+      if (MODE == kGn) {
+        double t3[3];
+        cross(o, ad + 3, t3);
+        const double mdo[3] = {ad[0] - t3[0], ad[1] - t3[1], ad[2] - t3[2]};
+        for (int k = 0; k < nd; ++k) {
+          const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
+                               ws[L.axes + 9 * l + 3 * k + 2]};
+          ws[out + d0 + k] = scale * dot3(w, mdo);
         }
-        jr_tangent(th, v, dJ);
-      }
-      for (int k = 0; k < nd; ++k) {
-        const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
-                             ws[L.axes + 9 * l + 3 * k + 2]};
-        double wd[3];
-        cross(V, w, wd);
+      } else {
+        double a[6], V[6];
+        for (int k = 0; k < 6; ++k) {
+          a[k] = ws[L.acc + 6 * l + k];
+          V[k] = ws[L.V + 6 * l + k];
+        }
+        double od[3];
+        cross(V, o, od);
+        od[0] += V[3];
+        od[1] += V[4];
+        od[2] += V[5];
+        double t1[3], t2[3], t3[3];
+        cross(o, a + 3, t1);
+        const double mo[3] = {a[0] - t1[0], a[1] - t1[1], a[2] - t1[2]};
+        cross(od, a + 3, t2);
+        cross(o, ad + 3, t3);
+        const double mdo[3] = {ad[0] - t2[0] - t3[0], ad[1] - t2[1] - t3[1], ad[2] - t2[2] - t3[2]};
+        double dJ[9];
         if (nd == 3) {
-          // + R dJr e_k
-          for (int r = 0; r < 3; ++r)
-            wd[r] += fma(T[4 * r], dJ[k], fma(T[4 * r + 1], dJ[3 + k], T[4 * r + 2] * dJ[6 + k]));
+          double th[3], v[3];
+          for (int k = 0; k < 3; ++k) {
+            th[k] = ws[L.xt + d0 + k];
+            v[k] = ws[dir + d0 + k];
+          }
+          jr_tangent(th, v, dJ);
         }
-        ws[L.gt + d0 + k] = 2.0 * (dot3(wd, mo) + dot3(w, mdo));
+        for (int k = 0; k < nd; ++k) {
+          const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
+                               ws[L.axes + 9 * l + 3 * k + 2]};
+          double wd[3];
+          cross(V, w, wd);
+          if (nd == 3) {
+            // + R dJr e_k
+            for (int r = 0; r < 3; ++r)
+              wd[r] += fma(T[4 * r], dJ[k], fma(T[4 * r + 1], dJ[3 + k], T[4 * r + 2] * dJ[6 + k]));
+          }
+          ws[out + d0 + k] = scale * (dot3(wd, mo) + dot3(w, mdo));
+        }
       }
       if (p >= 0)
         for (int k = 0; k < 6; ++k) ws[L.accd + 6 * p + k] += ad[k];
     }
   }
+
+  // gradient of Eq. EQHOC: 2 Jr^T r, into gt
+  __device__ __forceinline__ void tangent() const { tangent_pass<kGrad>(L.rt, L.gt, 2.0); }
 
   // Full evaluation at xt: returns E (group total, identical on the group's
   // lanes); rt = residual of the own stage; gt = dE/dq of the own stage.
@@ -484,6 +521,99 @@ struct Ctx {
       tangent();
     }
     return E;
+  }
+
+  // Residual pass only at xt: returns E (group total); rt = residual.
+  __device__ double evaluate_primal(const double* tau) const {
+    const double e = primal(tau);
+    double E = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) E += grp.from_full(e, j);
+    return E;
+  }
+
+  // ----------------------------------------------------------- Newton (LM)
+  // Jacobian rows of the own stage at the primal point: column c = (stage
+  // k, dof e) is the tangent of every stage's residual along the unit
+  // direction of q_{k,e} (S >= 2: Jr of Eq. HOC; S == 1: the Gauss-Newton
+  // matrix of Eq. EQ, int dP/dq^T dP/dq / dt^2). Row-major [n][S n] at J.
+  // S n tangent passes; convergent across the warp.
+  __device__ __noinline__ void build_jacobian() const {
+    const int Sn = S * n;
+    for (int k = 0; k < S; ++k)
+      for (int e = 0; e < n; ++e) {
+        for (int d = 0; d < n; ++d) ws[L.u + d] = (i == k && d == e) ? 1.0 : 0.0;
+        if (S == 1) tangent_pass<kGn>(L.u, L.jc, 1.0);
+        else tangent_pass<kJvp>(L.u, L.jc, 1.0);
+        for (int d = 0; d < n; ++d) ws[L.J + (int64_t)d * Sn + k * n + e] = ws[L.jc + d];
+      }
+  }
+
+  // H = Jr^T Jr and gg = Jr^T r (S >= 2) or H = the Gauss-Newton matrix and
+  // gg = r (S == 1), full symmetric H on every lane of the group. Returns
+  // max diag(H). Group-divergent (group-mask shuffles).
+  __device__ __noinline__ double gram() const {
+    const int Sn = S * n;
+    double hmax = 0.0;
+    if (S == 1) {
+      for (int a = 0; a < n; ++a)
+        for (int c = 0; c <= a; ++c) {
+          const double h = ws[L.J + (int64_t)a * Sn + c];
+          ws[L.H + (int64_t)a * Sn + c] = h;
+          ws[L.H + (int64_t)c * Sn + a] = h;
+        }
+      for (int a = 0; a < n; ++a) ws[L.gg + a] = ws[L.r + a];
+    } else {
+      for (int a = 0; a < Sn; ++a) {
+        for (int c = 0; c <= a; ++c) {
+          double h = 0.0;
+          for (int d = 0; d < n; ++d)
+            h = fma(ws[L.J + (int64_t)d * Sn + a], ws[L.J + (int64_t)d * Sn + c], h);
+          h = grp.sum(h);
+          ws[L.H + (int64_t)a * Sn + c] = h;
+          ws[L.H + (int64_t)c * Sn + a] = h;
+        }
+        double gsum = 0.0;
+        for (int d = 0; d < n; ++d) gsum = fma(ws[L.J + (int64_t)d * Sn + a], ws[L.r + d], gsum);
+        ws[L.gg + a] = grp.sum(gsum);
+      }
+    }
+    for (int a = 0; a < Sn; ++a) hmax = fmax(hmax, ws[L.H + (int64_t)a * Sn + a]);
+    return hmax;
+  }
+
+  // Cholesky of H + lambda I into A (lower triangle) and dl = -(H + lambda I)^-1 gg.
+  // Returns false if a pivot is not positive. Lane-local (same work on every
+  // lane of the group).
+  __device__ __noinline__ bool factor_solve(double lambda) const {
+    const int Sn = S * n;
+    for (int j = 0; j < Sn; ++j) {
+      double sjj = ws[L.H + (int64_t)j * Sn + j] + lambda;
+      for (int k = 0; k < j; ++k) {
+        const double l = ws[L.A + (int64_t)j * Sn + k];
+        sjj = fma(-l, l, sjj);
+      }
+      if (!(sjj > 0.0)) return false;
+      const double djj = sqrt(sjj);
+      ws[L.A + (int64_t)j * Sn + j] = djj;
+      const double inv = 1.0 / djj;
+      for (int r = j + 1; r < Sn; ++r) {
+        double t = ws[L.H + (int64_t)r * Sn + j];
+        for (int k = 0; k < j; ++k) t = fma(-ws[L.A + (int64_t)r * Sn + k], ws[L.A + (int64_t)j * Sn + k], t);
+        ws[L.A + (int64_t)r * Sn + j] = t * inv;
+      }
+    }
+    for (int r = 0; r < Sn; ++r) {
+      double t = -ws[L.gg + r];
+      for (int k = 0; k < r; ++k) t = fma(-ws[L.A + (int64_t)r * Sn + k], ws[L.dl + k], t);
+      ws[L.dl + r] = t / ws[L.A + (int64_t)r * Sn + r];
+    }
+    for (int r = Sn - 1; r >= 0; --r) {
+      double t = ws[L.dl + r];
+      for (int k = r + 1; k < Sn; ++k) t = fma(-ws[L.A + (int64_t)k * Sn + r], ws[L.dl + k], t);
+      ws[L.dl + r] = t / ws[L.A + (int64_t)r * Sn + r];
+    }
+    return true;
   }
 
   // ------------------------------------------------- L-BFGS vector algebra

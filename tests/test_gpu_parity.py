@@ -145,3 +145,80 @@ def test_rollout_matches_oracle_chains(S):
             assert ref["status"] == st[batch.inst_off[k] + b]
             if ref["status"] == 0:
                 assert np.max(np.abs(got - ref["traj_cur"])) <= 1e-7, (spec.name, b)
+
+
+def _rollout_case(specs, S, dt, n_steps, seed, pose=0.4, vel=0.3, sigma=0.1):
+    states = [I.random_state(s, seed + k, pose_scale=pose, vel_sigma=vel) for k, s in enumerate(specs)]
+    taus = [I.torques(s, n_steps, seed + 50 + k, sigma=sigma) for k, s in enumerate(specs)]
+    nodes, _ = O.colloc(S)
+    qps = [q0 + nodes[0] * dt * qd0 for q0, qd0 in states]
+    return states, taus, qps
+
+
+def _check_rollout(batch, specs, solvers, S, dt, n_steps, tol, max_iter, seed, dq_tol=1e-7, **kw):
+    torch = _torch()
+    P = _pbad()
+    states, taus, qps = _rollout_case(specs, S, dt, n_steps, seed, **kw)
+    dev = torch.device("cuda:0")
+    q_cur = torch.tensor(np.concatenate([q0.reshape(-1) for q0, _ in states]), device=dev)
+    q_prev = torch.tensor(np.concatenate([qp.reshape(-1) for qp in qps]), device=dev)
+    tau = torch.tensor(np.concatenate([t.reshape(n_steps, -1) for t in taus], axis=1).reshape(-1),
+                       device=dev)
+    out = P.rollout(batch, q_prev, q_cur, tau, n_steps, dt, S, solvers, 8, tol, max_iter)
+    torch.cuda.synchronize()
+    traj = out["traj_cur"].cpu().numpy()
+    st = out["status"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    n_conv = 0
+    for k, spec in enumerate(specs):
+        name = "lbfgs" if solvers[k] == P.LBFGS else "lm"
+        for b in range(spec.count):
+            om = O.OracleModel.from_spec(spec, b)
+            ref = om.rollout(S, dt, qps[k][b], states[k][0][b], taus[k][:, b, :], name, 8, tol,
+                             max_iter)
+            a = batch.dof_off[k] + b * spec.n_dof
+            got = traj[:, a:a + spec.n_dof]
+            assert ref["status"] == st[batch.inst_off[k] + b], (spec.name, b)
+            if ref["status"] == 0:
+                n_conv += 1
+                assert np.max(np.abs(got - ref["traj_cur"])) <= dq_tol, (spec.name, b)
+                if name == "lm":  # Newton: the same iterations, up to one per step at the tol
+                    assert abs(ref["iters"] - it[batch.inst_off[k] + b]) <= n_steps, (spec.name, b)
+    return n_conv
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_newton_rollout_matches_oracle(S):
+    P = _pbad()
+    specs = [I.rod_chain(3, 5, name="rod5"), I.ball_chain(4, 3, seed=23, radius=0.15),
+             I.humanoid(2, seed=24)]
+    batch = P.Batch([P.Model.from_spec(s) for s in specs], max_stages=3, max_history=8, newton=True)
+    n_conv = _check_rollout(batch, specs, [P.NEWTON] * 3, S, 0.02, 5, 1e-9, 100, 300)
+    assert n_conv >= 7
+
+
+def test_uneven_batch_mixed_solvers_one_launch():
+    """Trees on Newton, long and short hinge chains on L-BFGS, one launch."""
+    P = _pbad()
+    specs = [I.humanoid(3, seed=31), I.rod_chain(2, 12, name="rod12"), I.rod_chain(37, 3, name="rod3")]
+    batch = P.Batch([P.Model.from_spec(s) for s in specs], max_stages=2, max_history=8, newton=True)
+    n_conv = _check_rollout(batch, specs, [P.NEWTON, P.LBFGS, P.LBFGS], 2, 0.01, 4, 1e-9, 3000, 400,
+                            sigma=0.1)
+    assert n_conv >= 30
+
+
+def test_newton_status_codes():
+    """tol = 0 forces MAX_ITER; NaN torques give NONFINITE; both sides agree."""
+    torch = _torch()
+    P = _pbad()
+    spec = I.rod_chain(2, 3, name="rod3")
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=2, max_history=8, newton=True)
+    dev = torch.device("cuda:0")
+    q = torch.tensor(np.tile([0.3, -0.2, 0.1], 2), device=dev)
+    out = P.rollout(batch, q, q, None, 2, 0.02, 2, P.NEWTON, 8, 0.0, 5)
+    assert out["status"].cpu().tolist() == [1, 1]
+    tau = torch.full((2 * 6,), float("nan"), dtype=torch.float64, device=dev)
+    out = P.rollout(batch, q, q, tau, 2, 0.02, 2, P.NEWTON, 8, 1e-9, 50)
+    assert out["status"].cpu().tolist() == [4, 4]
+    out = P.rollout(batch, q, q, tau, 2, 0.02, 2, P.LBFGS, 8, 1e-9, 50)
+    assert out["status"].cpu().tolist() == [4, 4]
