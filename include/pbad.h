@@ -158,6 +158,28 @@ PBAD_API int pbad_rollout(pbad_batch* batch, const double* q_prev0, const double
                  double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
                  int32_t* status, int32_t* iters, int32_t* evals, void* stream);
 
+/* Implicit-function-theorem adjoint of one converged step (no counterpart
+ * in the paper, which has no adjoint; it differentiates the stage equations
+ * Eq. HOC, r(q_*; q_prev, q_cur, tau) = 0): given g_bar = dL/dq_*
+ * [S*D] at the converged stages q_star [S*D], solves Jr^T mu = g_bar and
+ * returns gq_prev = -(dr/dq_prev)^T mu, gq_cur = -(dr/dq_cur)^T mu and
+ * gtau = sum_i mu_i [D each]. Jr is exact (for one stage: the Hessian of
+ * Eq. EQ). status [instances] (NULL = skip): PBAD_CONVERGED, or
+ * PBAD_CHOL_FAIL when Jr is singular (outputs NaN). Needs a batch created
+ * with PBAD_BATCH_NEWTON. */
+PBAD_API int pbad_step_backward(pbad_batch* batch, const double* q_prev, const double* q_cur,
+                                const double* tau, const double* q_star, const double* g_bar,
+                                double dt, int32_t stages, double* gq_prev, double* gq_cur,
+                                double* gtau, int32_t* status, void* stream);
+
+/* World position of one body point per instance and its Jacobian:
+ * link[n_models] (host) is the link carrying the point in each model,
+ * point_local[instances][3] the point in that link's frame, q[D];
+ * pos[instances][3]; jac (NULL = skip) holds, model after model,
+ * [count][3][n] = dp/dq. */
+PBAD_API int pbad_link_points(pbad_batch* batch, const double* q, const int32_t* link,
+                              const double* point_local, double* pos, double* jac, void* stream);
+
 /* Bytes of the fixed device scratch used by pbad_eval_objective_grad_static. */
 #define PBAD_STATIC_SCRATCH_BYTES (8 * 1024 * 1024)
 

@@ -16,7 +16,7 @@ from . import inputs
 from ._native import PBADError, check, lib
 
 __all__ = ["Model", "Batch", "colloc", "eval_objective_grad", "step", "rollout", "fp64_peak",
-           "PBADError", "LBFGS", "NEWTON", "STATUS", "inputs"]
+           "step_backward", "PBADError", "LBFGS", "NEWTON", "STATUS", "inputs"]
 
 LBFGS = 0
 NEWTON = 1
@@ -224,3 +224,20 @@ def rollout(batch: Batch, q_prev0, q_cur0, tau_seq, n_steps: int, dt: float, sta
                              _tptr(out["q_cur"]), _tptr(out["status"]), _tptr(out["iters"]),
                              _tptr(out.get("evals")), _stream(stream)), "pbad_rollout")
     return out
+
+
+def step_backward(batch: Batch, q_prev, q_cur, tau, q_star, g_bar, dt: float, stages: int,
+                  stream=None):
+    """Implicit-function adjoint of one converged step: returns (gq_prev,
+    gq_cur, gtau, status) for g_bar = dL/dq_* (stage-packed)."""
+    import torch
+    dev = q_star.device
+    gp = torch.empty(batch.D, dtype=torch.float64, device=dev)
+    gc = torch.empty_like(gp)
+    gt = torch.empty_like(gp)
+    st = torch.empty(batch.n_instances, dtype=torch.int32, device=dev)
+    check(lib().pbad_step_backward(batch._h, _tptr(q_prev), _tptr(q_cur), _tptr(tau),
+                                   _tptr(q_star), _tptr(g_bar), float(dt), int(stages), _tptr(gp),
+                                   _tptr(gc), _tptr(gt), _tptr(st), _stream(stream)),
+          "pbad_step_backward")
+    return gp, gc, gt, st

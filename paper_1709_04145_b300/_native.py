@@ -16,7 +16,8 @@ ERRORS = {-1: "PBAD_ERR_ARG", -2: "PBAD_ERR_CUDA", -3: "PBAD_ERR_ALLOC", -4: "PB
 SYMBOLS = ("pbad_version", "pbad_last_error", "pbad_colloc", "pbad_model_create",
            "pbad_model_destroy", "pbad_model_info", "pbad_batch_create", "pbad_batch_destroy",
            "pbad_batch_info", "pbad_eval_objective_grad", "pbad_step", "pbad_rollout",
-           "pbad_fp64_peak", "pbad_eval_objective_grad_static")
+           "pbad_fp64_peak", "pbad_eval_objective_grad_static", "pbad_step_backward",
+           "pbad_link_points")
 
 
 class PBADError(RuntimeError):
@@ -52,6 +53,8 @@ def lib():
         L.pbad_rollout.argtypes = [vp, dp, dp, dp, i32, f64, i32, C.POINTER(C.c_int32), i32, f64,
                                    i32, dp, dp, dp, dp, ip, ip, ip, vp]
         L.pbad_fp64_peak.argtypes = [i32, C.POINTER(C.c_double)]
+        L.pbad_link_points.argtypes = [vp, dp, C.POINTER(C.c_int32), dp, dp, dp, vp]
+        L.pbad_step_backward.argtypes = [vp, dp, dp, dp, dp, dp, f64, i32, dp, dp, dp, ip, vp]
         L.pbad_eval_objective_grad_static.argtypes = [vp, dp, dp, dp, dp, f64, i32, dp, dp, dp, vp]
         for name in SYMBOLS:
             getattr(L, name).restype = C.c_char_p if name == "pbad_last_error" else C.c_int

@@ -14,12 +14,19 @@ namespace pbad {
 #define PBAD_DECL(S)                                                                \
   cudaError_t launch_eval_s##S(const LaunchArgs& A, int grid, cudaStream_t s);     \
   cudaError_t launch_rollout_s##S(const LaunchArgs& A, int grid, cudaStream_t s);
+#define PBAD_DECL_BWD(S) cudaError_t launch_backward_s##S(const LaunchArgs& A, int grid, cudaStream_t s);
+PBAD_DECL_BWD(1)
+PBAD_DECL_BWD(2)
+PBAD_DECL_BWD(3)
+PBAD_DECL_BWD(4)
+PBAD_DECL_BWD(5)
 PBAD_DECL(1)
 PBAD_DECL(2)
 PBAD_DECL(3)
 PBAD_DECL(4)
 PBAD_DECL(5)
 cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters);
+cudaError_t launch_link_points(const LaunchArgs& A, int grid, cudaStream_t s);
 
 cudaError_t launch_eval(int S, const LaunchArgs& A, int grid, cudaStream_t s) {
   switch (S) {
@@ -28,6 +35,16 @@ cudaError_t launch_eval(int S, const LaunchArgs& A, int grid, cudaStream_t s) {
     case 3: return launch_eval_s3(A, grid, s);
     case 4: return launch_eval_s4(A, grid, s);
     case 5: return launch_eval_s5(A, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_backward(int S, const LaunchArgs& A, int grid, cudaStream_t s) {
+  switch (S) {
+    case 1: return launch_backward_s1(A, grid, s);
+    case 2: return launch_backward_s2(A, grid, s);
+    case 3: return launch_backward_s3(A, grid, s);
+    case 4: return launch_backward_s4(A, grid, s);
+    case 5: return launch_backward_s5(A, grid, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -532,6 +549,59 @@ int pbad_step(pbad_batch* bt, const double* q_prev, const double* q_cur, const d
   return rollout_impl(bt, q_prev, q_cur, tau, 1, dt, stages, solvers, history, tol, max_iter,
                       nullptr, nullptr, q_prev_out, q_cur_out, q_stages_out, status, iters,
                       nullptr, stream);
+}
+
+int pbad_step_backward(pbad_batch* bt, const double* q_prev, const double* q_cur,
+                       const double* tau, const double* q_star, const double* g_bar, double dt,
+                       int32_t stages, double* gq_prev, double* gq_cur, double* gtau,
+                       int32_t* status, void* stream) {
+  int rc = check_common(bt, stages, dt);
+  if (rc != PBAD_OK) return rc;
+  if (!q_prev || !q_cur || !q_star || !g_bar || !gq_prev || !gq_cur || !gtau)
+    return fail(PBAD_ERR_ARG, "null array");
+  if (!(bt->flags & PBAD_BATCH_NEWTON))
+    return fail(PBAD_ERR_ARG, "the adjoint needs a batch created with PBAD_BATCH_NEWTON");
+  DeviceGuard dg(bt->device);
+  LaunchArgs A;
+  int grid = 0;
+  rc = fill_launch(bt, stages, dt, nullptr, 0, &A, &grid);
+  if (rc != PBAD_OK) return rc;
+  A.q_prev0 = q_prev;
+  A.q_cur0 = q_cur;
+  A.tau = tau;
+  A.q_star = q_star;
+  A.g_bar = g_bar;
+  A.gq_prev = gq_prev;
+  A.gq_cur = gq_cur;
+  A.gtau = gtau;
+  A.status = status;
+  A.n_steps = 1;
+  A.dense_stages = bt->max_stages;
+  const cudaError_t e = launch_backward(stages, A, grid, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "backward launch");
+  return PBAD_OK;
+}
+
+int pbad_link_points(pbad_batch* bt, const double* q, const int32_t* link,
+                     const double* point_local, double* pos, double* jac, void* stream) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (!q || !link || !point_local || !pos) return fail(PBAD_ERR_ARG, "null array");
+  for (size_t k = 0; k < bt->models.size(); ++k)
+    if (link[k] < 0 || link[k] >= bt->models[k]->N) return fail(PBAD_ERR_ARG, "link index out of range");
+  DeviceGuard dg(bt->device);
+  LaunchArgs A;
+  int grid = 0;
+  int rc = fill_launch(bt, 1, 1.0, nullptr, 0, &A, &grid);
+  if (rc != PBAD_OK) return rc;
+  static_assert(PBAD_MAX_MODELS <= kMaxBuckets, "bucket table");
+  A.q_cur0 = q;
+  A.point_local = point_local;
+  A.point_pos = pos;
+  A.point_jac = jac;
+  for (size_t k = 0; k < bt->models.size(); ++k) A.point_link[k] = link[k];  // in the parameter block
+  const cudaError_t e = launch_link_points(A, grid, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "points launch");
+  return PBAD_OK;
 }
 
 int pbad_fp64_peak(int32_t device, double* gflops) {

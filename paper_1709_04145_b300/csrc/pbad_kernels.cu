@@ -411,6 +411,113 @@ __global__ void __launch_bounds__(128) k_rollout(const __grid_constant__ LaunchA
 }
 
 // ------------------------------------------------------------------------
+// Implicit-function-theorem adjoint of one converged step. With
+// r(q_*; q_prev, q_cur, tau) = 0 at the solution, dq_* = -Jr^-1 dr, so for a
+// loss gradient gbar = dL/dq_*:  Jr^T mu = gbar, dL/dq_prev = -(dr/dq_prev)^T mu,
+// dL/dq_cur = -(dr/dq_cur)^T mu, dL/dtau = sum_i mu_i. Jr is built exactly
+// (S n tangent passes; the exact Hessian of Eq. EQ for one stage); the
+// known-node products are adjoint sweeps at q_prev and q_cur whose seeds
+// come from the stage transforms' tangents along mu.
+// ------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(128) k_step_backward(const __grid_constant__ LaunchArgs A) {
+  const Bucket& B = A.bk[find_bucket(A)];
+  const LaneId<S> id(B);
+  const bool active = id.real && id.inst < B.count;
+  const int b = active ? (int)id.inst : 0;
+  Ctx<S> c(B, A.K, b, id.lane_id, 0, A.dense_stages);
+  const int n = c.n;
+  const auto& L = c.L;
+  const Lane& ws = c.ws;
+  for (int d = 0; d < n; ++d) {
+    ws[L.qp + d] = A.q_prev0[c.gdof(d)];
+    ws[L.qc + d] = A.q_cur0[c.gdof(d)];
+  }
+  c.setup();
+  for (int d = 0; d < n; ++d) {
+    ws[L.xt + d] = A.q_star[c.gstage(d)];
+    ws[L.g + d] = A.g_bar[c.gstage(d)];
+  }
+  c.primal(A.tau);
+  c.build_jacobian(true);
+  bool ok = true;
+  if (active) ok = c.solve_transposed(L.g);
+  // own slice of mu into x
+  for (int d = 0; d < n; ++d) ws[L.x + d] = ws[L.dl + c.i * n + d];
+  c.transform_tangents(L.x);
+  c.known_node_vjp(0, L.qp, L.r);
+  c.known_node_vjp(1, L.qc, L.rt);
+  if (active) {
+    for (int d = 0; d < n; ++d) {
+      double gt = 0.0;
+      for (int s = 0; s < S; ++s) gt += ws[L.dl + s * n + d];
+      if (c.i == 0) {
+        A.gq_prev[c.gdof(d)] = ok ? -ws[L.r + d] : NAN;
+        A.gq_cur[c.gdof(d)] = ok ? -ws[L.rt + d] : NAN;
+        A.gtau[c.gdof(d)] = ok ? gt : NAN;
+      }
+    }
+    if (c.i == 0 && A.status) A.status[B.inst_off + b] = ok ? kConverged : kCholFail;
+  }
+}
+
+// ------------------------------------------------------------------------
+// World position of one body point per instance and its Jacobian dp/dq
+// (column d: w_d x (p - o_d) for the joints on the root-to-link path), from
+// the forward kinematics of Section 5. One lane per instance.
+// ------------------------------------------------------------------------
+#if PBAD_S == 1
+__global__ void __launch_bounds__(128) k_link_points(const __grid_constant__ LaunchArgs A) {
+  int bk = 0;
+  while (bk + 1 < A.nb && (int)blockIdx.x >= A.bk[bk + 1].block_begin) ++bk;
+  const Bucket& B = A.bk[bk];
+  const LaneId<1> id(B);
+  const bool active = id.real && id.inst < B.count;
+  const int b = active ? (int)id.inst : 0;
+  Ctx<1> c(B, A.K, b, id.lane_id, 0);
+  const int n = c.n;
+  const auto& L = c.L;
+  const Lane& ws = c.ws;
+  for (int d = 0; d < n; ++d) ws[L.xt + d] = A.q_cur0[c.gdof(d)];
+  for (int l = 0; l < c.N; ++l) {
+    const int p = B.parent[l], d0 = B.dof[l], nd = c.ndof(l);
+    double Tp[12], T[12], Jr[9], q3[3], w[9];
+    if (p >= 0) c.load12(L.T + 12 * p, Tp);
+    for (int k = 0; k < nd; ++k) q3[k] = ws[L.xt + d0 + k];
+    c.link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr);
+    c.store12(L.T + 12 * l, T);
+    c.link_axes(l, T, Jr, w);
+    for (int k = 0; k < 3 * nd; ++k) ws[L.axes + 9 * l + k] = w[k];
+  }
+  if (!active) return;
+  const int64_t g = B.inst_off + b;
+  const int lk = A.point_link[bk];
+  double T[12];
+  c.load12(L.T + 12 * lk, T);
+  const double* pl = A.point_local + 3 * g;
+  double pw[3];
+  for (int r = 0; r < 3; ++r) pw[r] = fma(T[4 * r], pl[0], fma(T[4 * r + 1], pl[1], fma(T[4 * r + 2], pl[2], T[4 * r + 3])));
+  for (int r = 0; r < 3; ++r) A.point_pos[3 * g + r] = pw[r];
+  if (A.point_jac) {
+    double* Jp = A.point_jac + 3 * (B.dof_off + (int64_t)b * n);
+    for (int k = 0; k < 3 * n; ++k) Jp[k] = 0.0;
+    for (int a = lk; a >= 0; a = B.parent[a]) {
+      const int d0 = B.dof[a], nd = c.ndof(a);
+      const double o[3] = {ws[L.T + 12 * a + 3], ws[L.T + 12 * a + 7], ws[L.T + 12 * a + 11]};
+      const double rel[3] = {pw[0] - o[0], pw[1] - o[1], pw[2] - o[2]};
+      for (int k = 0; k < nd; ++k) {
+        const double w[3] = {ws[L.axes + 9 * a + 3 * k], ws[L.axes + 9 * a + 3 * k + 1],
+                             ws[L.axes + 9 * a + 3 * k + 2]};
+        double v[3];
+        cross(w, rel, v);
+        for (int r = 0; r < 3; ++r) Jp[r * n + d0 + k] = v[r];
+      }
+    }
+  }
+}
+#endif
+
+// ------------------------------------------------------------------------
 // FP64 FMA throughput probe (roofline denominator): dependent chains, 8
 // independent chains per thread.
 // ------------------------------------------------------------------------
@@ -438,11 +545,19 @@ cudaError_t PBAD_CAT(launch_eval_s, PBAD_S)(const LaunchArgs& A, int grid, cudaS
   k_eval<PBAD_S><<<grid, 128, 0, s>>>(A);
   return cudaGetLastError();
 }
+cudaError_t PBAD_CAT(launch_backward_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
+  k_step_backward<PBAD_S><<<grid, 128, 0, s>>>(A);
+  return cudaGetLastError();
+}
 cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
   k_rollout<PBAD_S><<<grid, 128, 0, s>>>(A);
   return cudaGetLastError();
 }
 #if PBAD_S == 1
+cudaError_t launch_link_points(const LaunchArgs& A, int grid, cudaStream_t s) {
+  k_link_points<<<grid, 128, 0, s>>>(A);
+  return cudaGetLastError();
+}
 cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters) {
   k_fp64_peak<<<blocks, threads>>>(out, iters, 0.999999, 1e-7);
   return cudaGetLastError();

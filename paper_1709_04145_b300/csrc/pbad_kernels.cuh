@@ -86,6 +86,16 @@ struct LaunchArgs {
   int* status;             // [instances] or null
   int* iters;              // [instances] or null
   int* evals;              // [instances] or null (objective evaluations)
+  // step backward (implicit-function adjoint)
+  const double* g_bar;     // [S*D] dL/dq_* (stage-packed)
+  double* gq_prev;         // [D]
+  double* gq_cur;          // [D]
+  double* gtau;            // [D]
+  // link points
+  int point_link[kMaxBuckets];  // link index per model
+  const double* point_local;  // [instances][3] point in that link's frame
+  double* point_pos;       // [instances][3]
+  double* point_jac;       // [3 * D] per model block [count][3][n], or null
 };
 
 // ------------------------------------------------------------------------
@@ -538,12 +548,13 @@ struct Ctx {
   // direction of q_{k,e} (S >= 2: Jr of Eq. HOC; S == 1: the Gauss-Newton
   // matrix of Eq. EQ, int dP/dq^T dP/dq / dt^2). Row-major [n][S n] at J.
   // S n tangent passes; convergent across the warp.
-  __device__ __noinline__ void build_jacobian() const {
+  // exact = true gives Jr itself for S == 1 too (the exact Hessian of Eq. EQ).
+  __device__ __noinline__ void build_jacobian(bool exact = false) const {
     const int Sn = S * n;
     for (int k = 0; k < S; ++k)
       for (int e = 0; e < n; ++e) {
         for (int d = 0; d < n; ++d) ws[L.u + d] = (i == k && d == e) ? 1.0 : 0.0;
-        if (S == 1) tangent_pass<kGn>(L.u, L.jc, 1.0);
+        if (S == 1 && !exact) tangent_pass<kGn>(L.u, L.jc, 1.0);
         else tangent_pass<kJvp>(L.u, L.jc, 1.0);
         for (int d = 0; d < n; ++d) ws[L.J + (int64_t)d * Sn + k * n + e] = ws[L.jc + d];
       }
@@ -614,6 +625,154 @@ struct Ctx {
       ws[L.dl + r] = t / ws[L.A + (int64_t)r * Sn + r];
     }
     return true;
+  }
+
+  // ---------------------------------------------------- IFT adjoint helpers
+  // Solves Jr^T mu = gbar for the whole instance (every lane of the group
+  // gets all of mu in dl): the full Jr^T is gathered into A (from the
+  // lanes' rows in J) and solved by Gaussian elimination with partial
+  // pivoting; gbar is gathered from the lanes' slices at offset `gb`.
+  // Returns false on a zero pivot. Group-divergent (group-mask shuffles).
+  __device__ __noinline__ bool solve_transposed(int gb) const {
+    const int Sn = S * n;
+    for (int row = 0; row < Sn; ++row) {      // row of Jr
+      const int owner = row / n, d = row - owner * n;
+      for (int col = 0; col < Sn; ++col) {
+        const double v = grp.from(ws[L.J + (int64_t)d * Sn + col], owner);
+        ws[L.A + (int64_t)col * Sn + row] = v;  // A = Jr^T
+      }
+    }
+    for (int row = 0; row < Sn; ++row) {
+      const int owner = row / n, d = row - owner * n;
+      ws[L.dl + row] = grp.from(ws[gb + d], owner);
+    }
+    for (int c = 0; c < Sn; ++c) {
+      int piv = c;
+      double best = fabs(ws[L.A + (int64_t)c * Sn + c]);
+      for (int r = c + 1; r < Sn; ++r) {
+        const double v = fabs(ws[L.A + (int64_t)r * Sn + c]);
+        if (v > best) { best = v; piv = r; }
+      }
+      if (!(best > 0.0)) return false;
+      if (piv != c) {
+        for (int k = 0; k < Sn; ++k) {
+          const double t = ws[L.A + (int64_t)c * Sn + k];
+          ws[L.A + (int64_t)c * Sn + k] = ws[L.A + (int64_t)piv * Sn + k];
+          ws[L.A + (int64_t)piv * Sn + k] = t;
+        }
+        const double t = ws[L.dl + c];
+        ws[L.dl + c] = ws[L.dl + piv];
+        ws[L.dl + piv] = t;
+      }
+      const double inv = 1.0 / ws[L.A + (int64_t)c * Sn + c];
+      for (int r = c + 1; r < Sn; ++r) {
+        const double f = ws[L.A + (int64_t)r * Sn + c] * inv;
+        if (f == 0.0) continue;
+        for (int k = c; k < Sn; ++k)
+          ws[L.A + (int64_t)r * Sn + k] = fma(-f, ws[L.A + (int64_t)c * Sn + k], ws[L.A + (int64_t)r * Sn + k]);
+        ws[L.dl + r] = fma(-f, ws[L.dl + c], ws[L.dl + r]);
+      }
+    }
+    for (int r = Sn - 1; r >= 0; --r) {
+      double t = ws[L.dl + r];
+      for (int k = r + 1; k < Sn; ++k) t = fma(-ws[L.A + (int64_t)r * Sn + k], ws[L.dl + k], t);
+      ws[L.dl + r] = t / ws[L.A + (int64_t)r * Sn + r];
+    }
+    return true;
+  }
+
+  // Tangents Tdot_l of the own stage's transforms along the own slice of a
+  // direction (offset `dir`), into the G region (12 per link). Needs the
+  // primal pass's T and axes.
+  __device__ __noinline__ void transform_tangents(int dir) const {
+    for (int l = 0; l < N; ++l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      double V[6];
+      if (p >= 0) {
+        for (int k = 0; k < 6; ++k) V[k] = ws[L.V + 6 * p + k];
+      } else {
+        for (int k = 0; k < 6; ++k) V[k] = 0.0;
+      }
+      double T[12];
+      load12(L.T + 12 * l, T);
+      const double o[3] = {T[3], T[7], T[11]};
+      for (int k = 0; k < nd; ++k) {
+        const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
+                             ws[L.axes + 9 * l + 3 * k + 2]};
+        const double vk = ws[dir + d0 + k];
+        double ow[3];
+        cross(o, w, ow);
+        for (int c = 0; c < 3; ++c) {
+          V[c] = fma(vk, w[c], V[c]);
+          V[3 + c] = fma(vk, ow[c], V[3 + c]);
+        }
+      }
+      for (int k = 0; k < 6; ++k) ws[L.V + 6 * l + k] = V[k];
+      double Td[12];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const double col[3] = {T[c], T[4 + c], T[8 + c]};
+        double wc[3];
+        cross(V, col, wc);
+        Td[c] = wc[0];
+        Td[4 + c] = wc[1];
+        Td[8 + c] = wc[2];
+      }
+      Td[3] += V[3];
+      Td[7] += V[4];
+      Td[11] += V[5];
+      store12(L.G + 12 * l, Td);
+    }
+  }
+
+  // Vector-Jacobian product of the residuals with the known node j (0 =
+  // q_prev, 1 = q_cur) at configuration qj (offset): sum_i mu_i^T dr_i/dq_j
+  // = contraction of the twists at q_j with the seeds
+  //   B_l = (sum_i Wk[i][j] Tdot_i,l) M_l,
+  // Tdot_i,l from transform_tangents along mu. Result into `out` (n).
+  // Overwrites T, axes and acc. Convergent across the warp.
+  __device__ __noinline__ void known_node_vjp(int j, int qj, int out) const {
+    for (int l = 0; l < N; ++l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      double Tp[12], T[12], Jr[9], q3[3], w[9];
+      if (p >= 0) load12(L.T + 12 * p, Tp);
+      for (int k = 0; k < nd; ++k) q3[k] = ws[qj + d0 + k];
+      link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr);
+      store12(L.T + 12 * l, T);
+      link_axes(l, T, Jr, w);
+      for (int k = 0; k < 3 * nd; ++k) ws[L.axes + 9 * l + k] = w[k];
+      double Bs[12], Td[12];
+      load12(L.G + 12 * l, Td);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) Bs[k] = 0.0;
+#pragma unroll
+      for (int s = 0; s < S; ++s) {
+        const double wgt = K.Wk[s][j];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) Bs[k] = fma(wgt, grp.from_full(Td[k], s), Bs[k]);
+      }
+      const MassMoment M = mass(l);
+      double Bm[12], w6[6];
+      mul_mass(Bs, M, Bm);
+      wrench(Bm, T, w6);
+      for (int k = 0; k < 6; ++k) ws[L.acc + 6 * l + k] = w6[k];
+    }
+    for (int l = N - 1; l >= 0; --l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      double a[6];
+      for (int k = 0; k < 6; ++k) a[k] = ws[L.acc + 6 * l + k];
+      const double o[3] = {ws[L.T + 12 * l + 3], ws[L.T + 12 * l + 7], ws[L.T + 12 * l + 11]};
+      double of[3];
+      cross(o, a + 3, of);
+      const double mo[3] = {a[0] - of[0], a[1] - of[1], a[2] - of[2]};
+      for (int k = 0; k < nd; ++k) {
+        const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
+                             ws[L.axes + 9 * l + 3 * k + 2]};
+        ws[out + d0 + k] = dot3(w, mo);
+      }
+      if (p >= 0)
+        for (int k = 0; k < 6; ++k) ws[L.acc + 6 * p + k] += a[k];
+    }
   }
 
   // ------------------------------------------------- L-BFGS vector algebra

@@ -1,0 +1,155 @@
+"""Implicit-function adjoint of converged steps and differentiable rollouts
+on the CUDA path, against the oracle's dense adjoint and finite differences."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1709_04145_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_step_backward_matches_oracle(S):
+    import torch
+
+    import paper_1709_04145_b300 as P
+    dev = torch.device("cuda:0")
+    specs = [I.rod_chain(3, 4, name="rod4"), I.ball_chain(3, 3, seed=41, radius=0.15),
+             I.humanoid(2, seed=42)]
+    batch = P.Batch([P.Model.from_spec(s) for s in specs], max_stages=3, max_history=8, newton=True)
+    dt = 0.02
+    nodes, _ = O.colloc(S)
+    rng = np.random.default_rng(5)
+    states = [I.random_state(s, 50 + k, pose_scale=0.4, vel_sigma=0.3) for k, s in enumerate(specs)]
+    q0 = np.concatenate([st[0].reshape(-1) for st in states])
+    qd0 = np.concatenate([st[1].reshape(-1) for st in states])
+    qp = q0 + nodes[0] * dt * qd0
+    tau = rng.normal(0, 0.1, batch.D)
+    t = lambda a: torch.tensor(a, device=dev)
+    out = P.step(batch, t(qp), t(q0), t(tau), dt, S, P.NEWTON, 8, 1e-10, 100)
+    assert (out["status"] == 0).all()
+    qs = out["q_stages"]
+    gbar = rng.normal(size=S * batch.D)
+    gp, gc, gt, st = P.step_backward(batch, t(qp), t(q0), t(tau), qs, t(gbar), dt, S)
+    torch.cuda.synchronize()
+    assert (st == 0).all()
+    qs_h = qs.cpu().numpy()
+    gp, gc, gt = gp.cpu().numpy(), gc.cpu().numpy(), gt.cpu().numpy()
+    for k, spec in enumerate(specs):
+        for b in range(spec.count):
+            om = O.OracleModel.from_spec(spec, b)
+            a = batch.dof_off[k] + b * spec.n_dof
+            sl = slice(a, a + spec.n_dof)
+            ssl = slice(S * a, S * (a + spec.n_dof))
+            rp, rc, rt = om.step_adjoint(S, dt, qp[sl], q0[sl], tau[sl], qs_h[ssl], gbar[ssl])
+            tol = 1e-7
+            assert _relerr(gp[sl], rp) < tol, (spec.name, b, _relerr(gp[sl], rp))
+            assert _relerr(gc[sl], rc) < tol, (spec.name, b)
+            assert _relerr(gt[sl], rt) < tol, (spec.name, b)
+
+
+def _ee_problem(count=2, n_steps=6):
+    spec = I.humanoid(count, seed=61)
+    q0, qd0 = I.random_state(spec, 62, pose_scale=0.3, vel_sigma=0.3)
+    tau = I.torques(spec, n_steps, 63, sigma=0.1)
+    # end effector: tip of limb 1's last link (link 4), target in a 1 m ball
+    link = 4
+    tip = np.zeros((count, 3))
+    tip[:, 2] = -spec.length[:, link]
+    return spec, q0, qd0, tau, link, tip
+
+
+def test_rollout_gradient_matches_finite_differences():
+    import torch
+
+    import paper_1709_04145_b300 as P
+    from paper_1709_04145_b300.autograd import points_differentiable, rollout_differentiable
+    dev = torch.device("cuda:0")
+    S, dt, n_steps = 2, 0.033, 6
+    spec, q0, qd0, tau, link, tip = _ee_problem(2, n_steps)
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    target = torch.tensor(np.random.default_rng(64).normal(0, 0.3, (spec.count, 3)), device=dev)
+    tip_t = torch.tensor(tip, device=dev)
+    kw = dict(dt=dt, stages=S, solver=P.NEWTON, tol=1e-10, max_iter=100, checkpoint_every=4)
+
+    def loss(q0_, qd0_, tau_):
+        qc, qp, st = rollout_differentiable(batch, q0_, qd0_, tau_, **kw)
+        assert (st == 0).all()
+        p = points_differentiable(batch, qc, [link], tip_t)
+        return ((p - target) ** 2).sum()
+
+    x0 = torch.tensor(q0.reshape(-1), device=dev, requires_grad=True)
+    v0 = torch.tensor(qd0.reshape(-1), device=dev, requires_grad=True)
+    tt = torch.tensor(tau.reshape(n_steps, -1), device=dev, requires_grad=True)
+    L = loss(x0, v0, tt)
+    L.backward()
+    h = 1e-5
+    rng = np.random.default_rng(65)
+    with torch.no_grad():
+        for name, var, grad in (("q0", x0, x0.grad), ("qd0", v0, v0.grad), ("tau", tt, tt.grad)):
+            flat = var.view(-1)
+            for idx in rng.choice(flat.numel(), size=4, replace=False):
+                old = flat[idx].item()
+                flat[idx] = old + h
+                Lp = loss(x0, v0, tt).item()
+                flat[idx] = old - h
+                Lm = loss(x0, v0, tt).item()
+                flat[idx] = old
+                fd = (Lp - Lm) / (2 * h)
+                g = grad.view(-1)[idx].item()
+                assert abs(g - fd) <= 1e-4 * max(1.0, abs(fd)), (name, idx, g, fd)
+
+
+def test_rollout_gradient_matches_oracle_dense_adjoint():
+    """Chains the oracle's dense per-step adjoint over the same trajectory."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    from paper_1709_04145_b300.autograd import rollout_differentiable
+    dev = torch.device("cuda:0")
+    S, dt, n_steps = 2, 0.033, 5
+    spec = I.ball_chain(2, 4, seed=71, radius=0.15)
+    q0, qd0 = I.random_state(spec, 72, pose_scale=0.3, vel_sigma=0.3)
+    tau = I.torques(spec, n_steps, 73, sigma=0.1)
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    w_c = np.random.default_rng(74).normal(size=batch.D)
+    x0 = torch.tensor(q0.reshape(-1), device=dev, requires_grad=True)
+    v0 = torch.tensor(qd0.reshape(-1), device=dev, requires_grad=True)
+    tt = torch.tensor(tau.reshape(n_steps, -1), device=dev, requires_grad=True)
+    qc, qp, st = rollout_differentiable(batch, x0, v0, tt, dt, S, P.NEWTON, tol=1e-10,
+                                        max_iter=100, checkpoint_every=2)
+    (qc * torch.tensor(w_c, device=dev)).sum().backward()
+    nodes, _ = O.colloc(S)
+    n = spec.n_dof
+    for b in range(spec.count):
+        om = O.OracleModel.from_spec(spec, b)
+        sl = slice(b * n, (b + 1) * n)
+        # forward with the oracle, keeping every step's state and stages
+        qprev = q0[b] + nodes[0] * dt * qd0[b]
+        qcur = q0[b].copy()
+        hist = []
+        for t in range(n_steps):
+            qs, status, *_ = om.step(S, dt, qprev, qcur, tau[t, b], "lm", 8, 1e-10, 100)
+            assert status == 0
+            hist.append((qprev, qcur, qs))
+            qprev, qcur = qs[S - 2], qs[S - 1]
+        a_cur, a_prev = w_c[sl].copy(), np.zeros(n)
+        g_tau = np.zeros((n_steps, n))
+        for t in range(n_steps - 1, -1, -1):
+            qpv, qcv, qs = hist[t]
+            gbar = np.zeros((S, n))
+            gbar[S - 1] += a_cur
+            gbar[S - 2] += a_prev
+            gp, gc, gt = om.step_adjoint(S, dt, qpv, qcv, tau[t, b], qs, gbar)
+            a_prev, a_cur = gp, gc
+            g_tau[t] = gt
+        assert _relerr(x0.grad[sl].cpu().numpy(), a_prev + a_cur) < 1e-6
+        assert _relerr(v0.grad[sl].cpu().numpy(), nodes[0] * dt * a_prev) < 1e-6
+        assert _relerr(tt.grad[:, sl].cpu().numpy(), g_tau) < 1e-6
