@@ -127,6 +127,10 @@ PBAD_API int pbad_batch_destroy(pbad_batch* batch);
 PBAD_API int pbad_batch_info(const pbad_batch* batch, int64_t* n_instances, int64_t* n_dof_total,
                     int64_t* workspace_bytes);
 
+/* Threads per block of the solver kernels (32, 64, 96 or 128; default 32):
+ * the instance-to-warp mapping knob the autotuner sets. */
+PBAD_API int pbad_batch_set_threads(pbad_batch* batch, int32_t threads);
+
 /* Objective and gradient of one step at given stage configurations
  * (Eq. EQ / Eq. EQHOC; gradient by Algorithm DERIV in world coordinates and,
  * for S >= 2, its tangent sweep: grad = 2 Jr^T r in O(N)).

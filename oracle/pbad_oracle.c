@@ -945,7 +945,10 @@ static double eval_point(om_model *m, int S, double dt, const double *x,
 }
 
 /* One step of L-BFGS with history mh. x: in = initial guess, out = result.
- * Returns the status; *iters = accepted iterations, *evals = evaluations. */
+ * Returns the status; *iters = accepted iterations, *evals = evaluations.
+ * Besides max_iter accepted iterations, a step may use at most
+ * 4 max_iter + LS_MAX objective evaluations (line-search trials included);
+ * reaching either cap gives MAX_ITER. */
 static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
                        const double *qc, const double *tau, int mh, double tol,
                        int max_iter, int use_precond, double *x, int *iters,
@@ -1012,9 +1015,10 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
     }
     /* backtracking line search with Armijo or approximate-Wolfe acceptance */
     double a = 1.0;
-    int accepted = 0;
+    int accepted = 0, capped = 0;
     double Et = 0;
     for (int t = 0; t < LS_MAX; ++t) {
+      if (ne >= 4 * max_iter + LS_MAX) { capped = 1; break; }
       for (int i = 0; i < Sn; ++i) xt[i] = x[i] + a * d[i];
       Et = eval_point(m, S, dt, xt, qp, qc, tau, rt, gt);
       ne++;
@@ -1027,6 +1031,7 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
       }
       a *= LS_SHRINK;
     }
+    if (capped) { status = OM_MAX_ITER; break; }
     if (!accepted) { status = OM_LS_FAIL; break; }
     /* curvature pair */
     double sy = 0, ss = 0, yy = 0, yPy = 0;

@@ -131,6 +131,11 @@ class Batch:
             lib().pbad_batch_destroy(h)
             self._h = None
 
+    def set_threads(self, threads: int):
+        """Threads per block of the solver kernels (32, 64, 96, 128)."""
+        check(lib().pbad_batch_set_threads(self._h, int(threads)), "pbad_batch_set_threads")
+        self.threads = int(threads)
+
     def pack(self, per_model, stages: int = 0):
         """Concatenates per-model arrays (count, n) (or (count, S, n)) into one
         flat array (numpy or torch, whatever was given)."""

@@ -63,7 +63,7 @@ cudaError_t launch_rollout(int S, const LaunchArgs& A, int grid, cudaStream_t s)
 using namespace pbad;
 
 struct pbad_model {
-  int N = 0, n = 0, device = 0;
+  int N = 0, n = 0, device = 0, chain = 1;
   int64_t count = 0;
   std::vector<int> parent, jtype, dof;
   double g[3] = {0, 0, 0};
@@ -75,6 +75,7 @@ struct pbad_model {
 
 struct pbad_batch {
   int device = 0, max_stages = 0, max_history = 0, flags = 0;
+  int threads = 32;  // threads per block of the solver kernels
   std::vector<pbad_model*> models;
   std::vector<int64_t> inst_off, dof_off, lanes;
   std::vector<size_t> ws_off;  // in doubles
@@ -238,6 +239,8 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
   A->nb = (int)bt->models.size();
   A->D = bt->D;
   A->history = history;
+  A->threads = bt->threads;
+  const int wpb = bt->threads / 32;
   int blocks = 0;
   for (int k = 0; k < A->nb; ++k) {
     const pbad_model* m = bt->models[k];
@@ -258,8 +261,9 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.ws_stride = bt->lanes[k];
     B.block_begin = blocks;
     B.solver = solvers ? solvers[k] : PBAD_LBFGS;
+    B.chain = m->chain;
     const int64_t warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
-    blocks += (int)((warps + 3) / 4);
+    blocks += (int)((warps + wpb - 1) / wpb);
   }
   *grid = blocks;
   return PBAD_OK;
@@ -360,6 +364,7 @@ int pbad_model_create(int32_t n_links, const int32_t* parent, const int32_t* joi
       return fail(PBAD_ERR_ARG, "unknown joint type");
     }
     m->parent.push_back(parent[l]);
+    if (parent[l] != l - 1) m->chain = 0;
     m->jtype.push_back(joint_type[l]);
     m->dof.push_back(off);
     off += joint_type[l] == PBAD_HINGE ? 1 : 3;
@@ -604,6 +609,14 @@ int pbad_link_points(pbad_batch* bt, const double* q, const int32_t* link,
   return PBAD_OK;
 }
 
+int pbad_batch_set_threads(pbad_batch* bt, int32_t threads) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (threads != 32 && threads != 64 && threads != 96 && threads != 128)
+    return fail(PBAD_ERR_ARG, "threads per block must be 32, 64, 96 or 128");
+  bt->threads = threads;
+  return PBAD_OK;
+}
+
 int pbad_fp64_peak(int32_t device, double* gflops) {
   if (!gflops) return fail(PBAD_ERR_ARG, "null output");
   DeviceGuard dg(device);
@@ -658,6 +671,7 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   *per_lane = L.total;
   A->nb = 1;
   A->D = m->count * m->n;
+  A->threads = 128;
   Bucket& B = A->bk[0];
   B.N = m->N;
   B.n = m->n;
@@ -672,6 +686,7 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   B.ws = ws;
   B.ws_stride = *lanes;
   B.block_begin = 0;
+  B.chain = m->chain;
   *grid = (int)blocks;
   return PBAD_OK;
 }

@@ -41,6 +41,7 @@ struct Bucket {
   int64_t ws_stride;     // lanes in the workspace (>= groups * S)
   int block_begin;       // first block of the launch that serves this bucket
   int solver;            // 0 L-BFGS, 1 Newton
+  int chain;             // 1 if parent[l] == l - 1 for every link (serial chain)
 };
 
 // Collocation constants of one launch (all in units of 1/dt^2 already).

@@ -79,14 +79,16 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     ws[L.qp + d] = A.q_prev0[c.gdof(d)];
     ws[L.qc + d] = A.q_cur0[c.gdof(d)];
   }
-  int step = 0, phase = kFirst, k = 0, trials = 0, nh = 0, head = 0;
+  int step = 0, phase = kFirst, k = 0, trials = 0, nh = 0, head = 0, step_evals = 0;
   int worst = kConverged, iters_total = 0, evals_total = 0;
   double E = 0.0, alpha = 1.0, gd = 0.0, gamma = 1.0;
+  const int max_evals = 4 * A.max_iter + kLsMax;  // evaluations per step
   c.setup();
   if (!active) phase = kDone;
 
   auto finish = [&](int st) {
     worst = max(worst, st);
+    step_evals = 0;
     // new state: q_prev' = stage S-2 (or q_cur when S = 1), q_cur' = stage S-1
     for (int d = 0; d < n; ++d) {
       const double xs = c.grp.from(ws[L.x + d], S - 1);
@@ -121,7 +123,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     bad = (int)c.grp.sum((double)bad);
     if (bad || !isfinite(E) || !isfinite(rr)) { finish(kNonFinite); return; }
     if (sqrt(rr) < A.tol) { finish(kConverged); return; }
-    if (k >= A.max_iter) { finish(kMaxIter); return; }
+    if (k >= A.max_iter || step_evals >= max_evals) { finish(kMaxIter); return; }
     // two-loop recursion with H0 = gamma * P
     double al[kMaxHistory];
     for (int d = 0; d < n; ++d) ws[L.d + d] = -ws[L.g + d];
@@ -157,6 +159,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     const double Et = c.evaluate(tau);
     if (phase == kDone) continue;
     ++evals_total;
+    ++step_evals;
     if (phase == kFirst) {
       for (int d = 0; d < n; ++d) {
         ws[L.x + d] = ws[L.xt + d];
@@ -186,6 +189,10 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
       }
     }
     if (!ok) {
+      if (step_evals >= max_evals) {
+        finish(kMaxIter);
+        continue;
+      }
       if (++trials >= kLsMax) {
         finish(kLsFail);
         continue;
@@ -542,20 +549,20 @@ __global__ void k_fp64_peak(double* out, int iters, double a, double b) {
 #define PBAD_CAT2(a, b) a##b
 #define PBAD_CAT(a, b) PBAD_CAT2(a, b)
 cudaError_t PBAD_CAT(launch_eval_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
-  k_eval<PBAD_S><<<grid, 128, 0, s>>>(A);
+  k_eval<PBAD_S><<<grid, A.threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 cudaError_t PBAD_CAT(launch_backward_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
-  k_step_backward<PBAD_S><<<grid, 128, 0, s>>>(A);
+  k_step_backward<PBAD_S><<<grid, A.threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
-  k_rollout<PBAD_S><<<grid, 128, 0, s>>>(A);
+  k_rollout<PBAD_S><<<grid, A.threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 #if PBAD_S == 1
 cudaError_t launch_link_points(const LaunchArgs& A, int grid, cudaStream_t s) {
-  k_link_points<<<grid, 128, 0, s>>>(A);
+  k_link_points<<<grid, A.threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters) {

@@ -65,6 +65,7 @@ struct WsLayout {
 
 struct LaunchArgs {
   int nb;
+  int threads;             // threads per block (32, 64, 96 or 128)
   Bucket bk[kMaxBuckets];
   Colloc K;
   int history, max_iter, n_steps;
@@ -318,10 +319,12 @@ struct Ctx {
   __device__ __noinline__ double primal(const double* tau) const {
     double Eown = 0.0;
     const double dt2 = K.dt * K.dt;
+    const bool chain = B.chain;
+    double Tp[12];  // parent transform (kept in registers along a chain)
     for (int l = 0; l < N; ++l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
-      double Tp[12], T[12], Jr[9], q3[3], w[9];
-      if (p >= 0) load12(L.T + 12 * p, Tp);
+      double T[12], Jr[9], q3[3], w[9];
+      if (p >= 0 && !chain) load12(L.T + 12 * p, Tp);
       for (int k = 0; k < nd; ++k) q3[k] = ws[L.xt + d0 + k];
       link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr);
       store12(L.T + 12 * l, T);
@@ -358,13 +361,16 @@ struct Ctx {
       double w6[6];
       wrench(G, T, w6);
       for (int k = 0; k < 6; ++k) ws[L.acc + 6 * l + k] = w6[k];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) Tp[k] = T[k];
     }
     // backward: subtree sums and joint contraction
     double rr = 0.0, tq = 0.0;
+    double carry[6] = {0, 0, 0, 0, 0, 0};  // child subtree sum along a chain
     for (int l = N - 1; l >= 0; --l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
       double a[6];
-      for (int k = 0; k < 6; ++k) a[k] = ws[L.acc + 6 * l + k];
+      for (int k = 0; k < 6; ++k) a[k] = ws[L.acc + 6 * l + k] + carry[k];
       const double o[3] = {ws[L.T + 12 * l + 3], ws[L.T + 12 * l + 7], ws[L.T + 12 * l + 11]};
       double of[3];
       cross(o, a + 3, of);
@@ -378,8 +384,14 @@ struct Ctx {
         rr = fma(rk, rk, rr);
         tq = fma(tk, ws[L.xt + d0 + k], tq);
       }
-      if (p >= 0)
+      if (chain) {
+        for (int k = 0; k < 6; ++k) {
+          carry[k] = a[k];
+          ws[L.acc + 6 * l + k] = a[k];  // subtree sums are reused by the tangent pass
+        }
+      } else if (p >= 0) {
         for (int k = 0; k < 6; ++k) ws[L.acc + 6 * p + k] += a[k];
+      }
     }
     return (S == 1) ? (Eown - tq) : rr;
   }
@@ -397,13 +409,16 @@ struct Ctx {
   enum TangentMode { kGrad = 0, kJvp = 1, kGn = 2 };
   template <int MODE>
   __device__ __noinline__ void tangent_pass(int dir, int out, double scale) const {
+    const bool chain = B.chain;
+    double V[6] = {0, 0, 0, 0, 0, 0};  // parent twist (kept in registers along a chain)
     for (int l = 0; l < N; ++l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
-      double V[6];
-      if (p >= 0) {
-        for (int k = 0; k < 6; ++k) V[k] = ws[L.V + 6 * p + k];
-      } else {
-        for (int k = 0; k < 6; ++k) V[k] = 0.0;
+      if (!chain) {
+        if (p >= 0) {
+          for (int k = 0; k < 6; ++k) V[k] = ws[L.V + 6 * p + k];
+        } else {
+          for (int k = 0; k < 6; ++k) V[k] = 0.0;
+        }
       }
       double T[12];
       load12(L.T + 12 * l, T);
@@ -456,10 +471,11 @@ struct Ctx {
       }
       for (int k = 0; k < 6; ++k) ws[L.accd + 6 * l + k] = w6[k];
     }
+    double carry[6] = {0, 0, 0, 0, 0, 0};
     for (int l = N - 1; l >= 0; --l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
       double ad[6], T[12];
-      for (int k = 0; k < 6; ++k) ad[k] = ws[L.accd + 6 * l + k];
+      for (int k = 0; k < 6; ++k) ad[k] = ws[L.accd + 6 * l + k] + carry[k];
       load12(L.T + 12 * l, T);
       const double o[3] = {T[3], T[7], T[11]};
       if (MODE == kGn) {
@@ -510,8 +526,11 @@ struct Ctx {
           ws[out + d0 + k] = scale * (dot3(wd, mo) + dot3(w, mdo));
         }
       }
-      if (p >= 0)
+      if (chain) {
+        for (int k = 0; k < 6; ++k) carry[k] = ad[k];
+      } else if (p >= 0) {
         for (int k = 0; k < 6; ++k) ws[L.accd + 6 * p + k] += ad[k];
+      }
     }
   }
 

@@ -234,10 +234,10 @@ def pendulum3(seed_base: int = 1000):
 
 
 def ball_chains(count: int = 4096, n_links: int = 10, seed_base: int = 2000,
-                n_steps: int = 100):
-    """Batched 3D ball-joint capsule chains: dt = 0.033, three stages (K = 4),
-    L-BFGS history 8, 100 steps."""
-    spec = ball_chain(count, n_links, seed_base + 1)
+                n_steps: int = 100, radius: float = 0.15):
+    """Batched 3D ball-joint capsule chains (capsule radius 0.15 m): dt =
+    0.033, three stages (K = 4), L-BFGS history 8, 100 steps."""
+    spec = ball_chain(count, n_links, seed_base + 1, radius=radius)
     q0, qd0 = random_state(spec, seed_base + 2)
     return dict(spec=spec, q0=q0, qd0=qd0, dt=0.033, stages=3, history=8,
                 tol=1e-8, n_steps=n_steps, solver="lbfgs")
