@@ -73,16 +73,42 @@ def parse():
     p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     p.add_argument("--threads", type=int, default=0,
                    help="threads per block (0 = autotune over 32/64/128 on a short rollout)")
+    p.add_argument("--plain-instances", type=int, default=8,
+                   help="instances timed in the plain form (one launch per instance-step)")
+    p.add_argument("--plain-timesteps", type=int, default=10)
+    p.add_argument("--adjoint-steps", type=int, default=8,
+                   help="steps of the differentiable humanoid rollout timed forward and forward+adjoint "
+                        "(0 = skip; the workload defines 64)")
     return p.parse_args()
 
 
 def workload(args, rank=0):
     from paper_1709_04145_b300 import inputs as I
-    w = I.ball_chains(count=args.instances, n_links=args.links, seed_base=2000 + 17 * rank,
+    w = I.ball_chains(count=args.instances, n_links=args.links, seed_base=shard_seed_base(rank),
                       n_steps=args.timesteps)
     w["max_iter"] = args.max_iter
     w["tol"] = args.tol
     return w
+
+
+# ------------------------------------------------------------- multi-rank
+def shard_seed_base(rank: int) -> int:
+    """Every rank integrates its own seeded batch (weak scaling: instances are
+    independent, so the path shards with no data-path collective)."""
+    return 2000 + 17 * rank
+
+
+def max_over_ranks(x: float, dist, device) -> float:
+    """The slowest rank's time (the job ends when the last rank ends)."""
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(units_per_rank: float, world: int, ms_max: float) -> float:
+    """Whole-job units/s: all ranks' units over the slowest rank's time."""
+    return units_per_rank * world / (ms_max / 1e3)
 
 
 # ------------------------------------------------------------------ clocks
@@ -205,6 +231,85 @@ def autotune(P, batch, args, w):
     return best
 
 
+def measure_plain(P, w, args, dev):
+    """Plain form: the same kernels with one instance per launch and one launch
+    per instance-step (pbad_step on a batch of one), no graph; returns
+    link-steps/s over the first instances of the workload."""
+    import torch
+    spec = w["spec"]
+    S, dt, m = w["stages"], w["dt"], w["history"]
+    nodes, _ = P.colloc(S)
+    n_inst = min(args.plain_instances, spec.count)
+    T = args.plain_timesteps
+    jobs = []
+    for b in range(n_inst):
+        model = P.Model.from_spec(spec.select([b]), device=dev.index)
+        batch = P.Batch([model], max_stages=S, max_history=m)
+        qp = torch.tensor((w["q0"][b] + nodes[0] * dt * w["qd0"][b]), device=dev)
+        qc = torch.tensor(w["q0"][b], device=dev)
+        jobs.append((model, batch, qp, qc))
+    for model, batch, qp, qc in jobs[:1]:  # warm-up
+        P.step(batch, qp, qc, None, dt, S, P.LBFGS, m, w["tol"], w["max_iter"])
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for model, batch, qp, qc in jobs:
+        for _ in range(T):
+            out = P.step(batch, qp, qc, None, dt, S, P.LBFGS, m, w["tol"], w["max_iter"])
+            qp, qc = out["q_prev"], out["q_cur"]
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    return {"value": n_inst * spec.n_links * T / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "sample": f"{n_inst} instances x {T} time steps, one pbad_step launch per "
+                      "instance-step, no graph"}
+
+
+def measure_adjoint(P, args, dev):
+    """Forward and forward+adjoint wall time (CUDA events) of the differentiable
+    humanoid rollout: 1024 humanoids, dt = 0.033, two stages, Newton,
+    checkpoint every 8 steps, end-effector loss at the last step."""
+    import numpy as np
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    from paper_1709_04145_b300.autograd import points_differentiable, rollout_differentiable
+    steps = args.adjoint_steps
+    w = I.humanoid_adjoint(n_steps=steps)
+    spec = w["spec"]
+    S = w["stages"]
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=S, max_history=8,
+                    newton=True)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a), device=dev)
+    x0 = t(w["q0"].reshape(-1)).requires_grad_()
+    v0 = t(w["qd0"].reshape(-1)).requires_grad_()
+    tt = t(w["tau"].reshape(steps, -1)).requires_grad_()
+    tip = t(w["ee_point"])
+    target = t(np.random.default_rng(w["target_seed"]).normal(0, 0.3, (spec.count, 3)))
+    kw = dict(dt=w["dt"], stages=S, solver=P.NEWTON, tol=w["tol"], max_iter=100,
+              checkpoint_every=w["checkpoint_every"])
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a, b = ev(), ev()
+    a.record()
+    with torch.no_grad():
+        _, _, st = rollout_differentiable(batch, x0, v0, tt, **kw)
+    b.record()
+    torch.cuda.synchronize()
+    fwd = a.elapsed_time(b)
+    a, b = ev(), ev()
+    a.record()
+    qc, _, st = rollout_differentiable(batch, x0, v0, tt, **kw)
+    loss = ((points_differentiable(batch, qc, [w["ee_link"]], tip) - target) ** 2).sum()
+    loss.backward()
+    b.record()
+    torch.cuda.synchronize()
+    stc = st.cpu().numpy()
+    return {"fwd_ms": fwd, "fwd_adjoint_ms": a.elapsed_time(b), "steps": steps,
+            "workload_steps": 64, "instances": spec.count,
+            "converged_fraction": float((stc == 0).mean()),
+            "note": f"{steps} of the workload's 64 steps timed"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -284,15 +389,13 @@ def run_ours(args):
     clk = clocks.stop() if not args.no_clocks else None
     ms = sum(ms_steps) / len(ms_steps)
     if world > 1:
-        t = torch.tensor([ms], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = t.item()
+        ms = max_over_ranks(ms, dist, dev)
 
     status = out["status"].cpu().numpy()
     iters = out["iters"].cpu().numpy()
     evals = out["evals"].cpu().numpy()
     link_steps = spec.count * spec.n_links * T
-    value = link_steps * world / (ms / 1e3)
+    value = job_throughput(link_steps, world, ms)
 
     # roofline of the rollout kernel (the only kernel of the timed region)
     fe = flops_per_eval(spec.jtype.tolist(), S)
@@ -327,10 +430,8 @@ def run_ours(args):
             t_e2e.append(e0.elapsed_time(e1))
         ms_e = sum(t_e2e) / len(t_e2e)
         if world > 1:
-            t = torch.tensor([ms_e], device=dev, dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms_e = t.item()
-        e2e = {"value": link_steps * world / (ms_e / 1e3), "unit": UNIT,
+            ms_e = max_over_ranks(ms_e, dist, dev)
+        e2e = {"value": job_throughput(link_steps, world, ms_e), "unit": UNIT,
                "h2d_bytes_per_step": 2 * batch.D * 8,
                "d2h_bytes_per_step": batch.D * 8 + batch.n_instances * 4,
                "ms_per_step": ms_e}
@@ -360,6 +461,12 @@ def run_ours(args):
         "e2e": e2e,
         "clocks": clk,
     }
+    if rank == 0 and args.plain_instances > 0:
+        plain = measure_plain(P, w, args, dev)
+        line["plain"] = plain
+        line["batched_vs_plain"] = value / world / plain["value"]
+    if rank == 0 and args.adjoint_steps > 0:
+        line["fwd_adjoint"] = measure_adjoint(P, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(w, n_inst=min(os.cpu_count() or 1, 16), n_steps=1,
                                               budget_s=args.cpu_sample_seconds)

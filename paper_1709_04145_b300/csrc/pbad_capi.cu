@@ -67,7 +67,7 @@ struct pbad_model {
   int64_t count = 0;
   std::vector<int> parent, jtype, dof;
   double g[3] = {0, 0, 0};
-  int* d_topo = nullptr;     // parent[N] | jtype[N] | dof[N]
+  int* d_topo = nullptr;     // parent[N] | jtype[N] | dof[N] | rest_eye[N]
   double* d_axis = nullptr;  // [N][3]
   double* d_mm = nullptr;    // [N][10][count]
   double* d_rest = nullptr;  // [N][12][count]
@@ -82,6 +82,12 @@ struct pbad_batch {
   int64_t n_inst = 0, D = 0;
   double* d_ws = nullptr;
   size_t ws_doubles = 0;
+  // dense Newton/adjoint storage (PBAD_BATCH_NEWTON): per bucket
+  // count * dense_stride doubles from dense_off
+  double* d_dense = nullptr;
+  size_t dense_doubles = 0;
+  std::vector<size_t> dense_off;
+  std::vector<int64_t> dense_stride;
 };
 
 namespace {
@@ -231,8 +237,11 @@ int make_colloc(int S, double dt, Colloc* K) {
 
 int groups_per_warp(int S) { return 32 / S; }
 
+// Launch description over every bucket. Buckets solved by Newton (and every
+// bucket when all_warp is set: the adjoint) use one warp per instance; the
+// others one group of S lanes per instance, floor(32/S) instances per warp.
 int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int history,
-                LaunchArgs* A, int* grid) {
+                LaunchArgs* A, int* grid, bool all_warp = false) {
   std::memset(A, 0, sizeof(LaunchArgs));
   int rc = make_colloc(S, dt, &A->K);
   if (rc != PBAD_OK) return rc;
@@ -240,6 +249,7 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
   A->D = bt->D;
   A->history = history;
   A->threads = bt->threads;
+  A->dense_stages = (bt->flags & PBAD_BATCH_NEWTON) ? bt->max_stages : 0;
   const int wpb = bt->threads / 32;
   int blocks = 0;
   for (int k = 0; k < A->nb; ++k) {
@@ -251,6 +261,7 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.parent = m->d_topo;
     B.jtype = m->d_topo + m->N;
     B.dof = m->d_topo + 2 * m->N;
+    B.rest_eye = m->d_topo + 3 * m->N;
     B.axis = m->d_axis;
     B.mm = m->d_mm;
     B.rest = m->d_rest;
@@ -262,13 +273,15 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.block_begin = blocks;
     B.solver = solvers ? solvers[k] : PBAD_LBFGS;
     B.chain = m->chain;
-    const int64_t warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
+    B.dense = bt->d_dense ? bt->d_dense + bt->dense_off[k] : nullptr;
+    B.dense_stride = bt->d_dense ? bt->dense_stride[k] : 0;
+    const bool warp_map = all_warp || B.solver == PBAD_NEWTON;
+    const int64_t warps = warp_map ? m->count : (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
     blocks += (int)((warps + wpb - 1) / wpb);
   }
   *grid = blocks;
   return PBAD_OK;
 }
-
 
 int check_common(pbad_batch* bt, int32_t stages, double dt) {
   if (!bt) return fail(PBAD_ERR_ARG, "null batch");
@@ -317,7 +330,6 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   A.status = status;
   A.iters = iters;
   A.evals = evals;
-  A.dense_stages = (bt->flags & PBAD_BATCH_NEWTON) ? bt->max_stages : 0;
   cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e = launch_rollout(stages, A, grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
@@ -376,11 +388,18 @@ int pbad_model_create(int32_t n_links, const int32_t* parent, const int32_t* joi
     delete m;
     return fail(PBAD_ERR_CUDA, "cudaSetDevice failed");
   }
-  std::vector<int> topo(3 * n_links);
+  std::vector<int> topo(4 * n_links);
   for (int l = 0; l < n_links; ++l) {
     topo[l] = m->parent[l];
     topo[n_links + l] = m->jtype[l];
     topo[2 * n_links + l] = m->dof[l];
+    // identity rest rotation in every instance (exact comparison)
+    int eye = 1;
+    for (int64_t b = 0; b < count && eye; ++b)
+      for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c)
+          if (rest[((size_t)b * n_links + l) * 12 + 4 * r + c] != (r == c ? 1.0 : 0.0)) eye = 0;
+    topo[3 * n_links + l] = eye;
   }
   // SoA over instances: [l][k][instance]
   std::vector<double> mm((size_t)n_links * 10 * count), rs((size_t)n_links * 12 * count);
@@ -465,12 +484,24 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
     bt->dof_off.push_back(bt->D);
     bt->n_inst += m->count;
     bt->D += m->count * m->n;
-    // the widest lane layout over the admissible stage counts
+    // the widest lane layout over the admissible stage counts (group
+    // mapping) and, for Newton batches, one warp per instance
+    // (warps rounded up to a multiple of 12 so that every block size of 1..4
+    // warps launches whole blocks inside the allocation)
     int64_t lanes = 0;
     for (int S = 1; S <= max_stages; ++S) {
       const int64_t warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
-      const int64_t l = ((warps + 3) / 4) * 4 * 32;
+      const int64_t l = ((warps + 11) / 12) * 12 * 32;
       if (l > lanes) lanes = l;
+    }
+    if (flags & PBAD_BATCH_NEWTON) {
+      const int64_t l = ((m->count + 11) / 12) * 12 * 32;
+      if (l > lanes) lanes = l;
+      DenseLayout DL;
+      DL.make(max_stages * m->n);
+      bt->dense_off.push_back(bt->dense_doubles);
+      bt->dense_stride.push_back(DL.total);
+      bt->dense_doubles += (size_t)m->count * DL.total;
     }
     WsLayout L;
     L.make(m->N, m->n, max_history, (flags & PBAD_BATCH_NEWTON) ? max_stages : 0);
@@ -491,6 +522,16 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
     delete bt;
     return cuda_fail(e, "cudaMemset");
   }
+  if (bt->dense_doubles) {
+    e = cudaMalloc(&bt->d_dense, sizeof(double) * bt->dense_doubles);
+    if (e == cudaSuccess) e = cudaMemset(bt->d_dense, 0, sizeof(double) * bt->dense_doubles);
+    if (e != cudaSuccess) {
+      cudaFree(bt->d_ws);
+      cudaFree(bt->d_dense);
+      delete bt;
+      return fail(PBAD_ERR_ALLOC, std::string("dense cudaMalloc: ") + cudaGetErrorString(e));
+    }
+  }
   *out = bt;
   return PBAD_OK;
 }
@@ -499,6 +540,7 @@ int pbad_batch_destroy(pbad_batch* bt) {
   if (!bt) return PBAD_OK;
   DeviceGuard dg(bt->device);
   cudaFree(bt->d_ws);
+  cudaFree(bt->d_dense);
   delete bt;
   return PBAD_OK;
 }
@@ -508,7 +550,8 @@ int pbad_batch_info(const pbad_batch* bt, int64_t* n_instances, int64_t* n_dof_t
   if (!bt) return fail(PBAD_ERR_ARG, "null batch");
   if (n_instances) *n_instances = bt->n_inst;
   if (n_dof_total) *n_dof_total = bt->D;
-  if (workspace_bytes) *workspace_bytes = (int64_t)(bt->ws_doubles * sizeof(double));
+  if (workspace_bytes)
+    *workspace_bytes = (int64_t)((bt->ws_doubles + bt->dense_doubles) * sizeof(double));
   return PBAD_OK;
 }
 
@@ -569,7 +612,7 @@ int pbad_step_backward(pbad_batch* bt, const double* q_prev, const double* q_cur
   DeviceGuard dg(bt->device);
   LaunchArgs A;
   int grid = 0;
-  rc = fill_launch(bt, stages, dt, nullptr, 0, &A, &grid);
+  rc = fill_launch(bt, stages, dt, nullptr, 0, &A, &grid, true);
   if (rc != PBAD_OK) return rc;
   A.q_prev0 = q_prev;
   A.q_cur0 = q_cur;
@@ -581,7 +624,6 @@ int pbad_step_backward(pbad_batch* bt, const double* q_prev, const double* q_cur
   A.gtau = gtau;
   A.status = status;
   A.n_steps = 1;
-  A.dense_stages = bt->max_stages;
   const cudaError_t e = launch_backward(stages, A, grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "backward launch");
   return PBAD_OK;
@@ -679,6 +721,7 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   B.parent = m->d_topo;
   B.jtype = m->d_topo + m->N;
   B.dof = m->d_topo + 2 * m->N;
+  B.rest_eye = m->d_topo + 3 * m->N;
   B.axis = m->d_axis;
   B.mm = m->d_mm;
   B.rest = m->d_rest;

@@ -31,6 +31,7 @@ struct Bucket {
   const int* parent;     // [N]
   const int* jtype;      // [N] 0 hinge, 1 ball
   const int* dof;        // [N] first DOF of each joint
+  const int* rest_eye;   // [N] 1 if every instance's rest rotation is the identity
   const double* axis;    // [N][3] hinge axes (joint frame)
   const double* mm;      // [N][10][count] mass moments (SoA over instances)
   const double* rest;    // [N][12][count] rest transforms (SoA over instances)
@@ -42,6 +43,8 @@ struct Bucket {
   int block_begin;       // first block of the launch that serves this bucket
   int solver;            // 0 L-BFGS, 1 Newton
   int chain;             // 1 if parent[l] == l - 1 for every link (serial chain)
+  double* dense;         // per-instance dense Newton/adjoint storage (or null)
+  int64_t dense_stride;  // doubles per instance in `dense`
 };
 
 // Collocation constants of one launch (all in units of 1/dt^2 already).
@@ -99,8 +102,11 @@ __device__ __forceinline__ void rodrigues(const double* v, double c0, double c1,
 struct ExpCoef {
   double c, a, b, h, db, dh;
 };
+template <bool DERIV = true>
 __device__ __forceinline__ ExpCoef exp_coef(double x) {
   ExpCoef e;
+  e.db = 0.0;
+  e.dh = 0.0;
   if (x < 0.25) {
     // Horner in x; terms through x^9 (remainder < 1e-21 at x = 0.25)
     // a = sum (-1)^k x^k/(2k+1)!, b = sum (-1)^k x^k/(2k+2)!, h = sum (-1)^k x^k/(2k+3)!
@@ -120,16 +126,18 @@ __device__ __forceinline__ ExpCoef exp_coef(double x) {
       B = fma(B, x, ib[k]);
       H = fma(H, x, ih[k]);
     }
+    if (DERIV) {
 #pragma unroll
-    for (int k = 8; k >= 1; --k) {
-      dB = fma(dB, x, k * ib[k]);
-      dH = fma(dH, x, k * ih[k]);
+      for (int k = 8; k >= 1; --k) {
+        dB = fma(dB, x, k * ib[k]);
+        dH = fma(dH, x, k * ih[k]);
+      }
+      e.db = dB;
+      e.dh = dH;
     }
     e.a = A;
     e.b = B;
     e.h = H;
-    e.db = dB;
-    e.dh = dH;
     e.c = fma(-B, x, 1.0);  // cos phi = 1 - x b
   } else {
     const double phi = sqrt(x);
@@ -140,8 +148,10 @@ __device__ __forceinline__ ExpCoef exp_coef(double x) {
     e.a = s / phi;
     e.b = (1.0 - c) * ix;
     e.h = (phi - s) * ix / phi;
-    e.db = (phi * s - 2.0 * (1.0 - c)) * 0.5 * ix * ix;
-    e.dh = (3.0 * s - phi * (2.0 + c)) * 0.5 * ix * ix / phi;
+    if (DERIV) {
+      e.db = (phi * s - 2.0 * (1.0 - c)) * 0.5 * ix * ix;
+      e.dh = (3.0 * s - phi * (2.0 + c)) * 0.5 * ix * ix / phi;
+    }
   }
   return e;
 }
@@ -157,7 +167,7 @@ __device__ __forceinline__ void joint_rotation(int jt, const double* u, const do
     rodrigues(u, c, s, 1.0 - c, R);
   } else {
     const double x = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
-    const ExpCoef e = exp_coef(x);
+    const ExpCoef e = exp_coef<false>(x);
     rodrigues(q, e.c, e.a, e.b, R);
     // Jr = (1 - h x) I - b [theta]x + h theta theta^T
     rodrigues(q, fma(-e.h, x, 1.0), -e.b, e.h, Jr);
@@ -168,7 +178,7 @@ __device__ __forceinline__ void joint_rotation(int jt, const double* u, const do
 // with K = [theta]x and K^2 = theta theta^T - x I.
 __device__ __forceinline__ void jr_tangent(const double* th, const double* v, double* dJ) {
   const double x = fma(th[0], th[0], fma(th[1], th[1], th[2] * th[2]));
-  const ExpCoef e = exp_coef(x);
+  const ExpCoef e = exp_coef<true>(x);
   const double tv = dot3(th, v);
   const double cb = -2.0 * tv * e.db, ch = 2.0 * tv * e.dh;
   // [v]x K + K [v]x = v th^T + th v^T - 2 (v.th) I

@@ -260,23 +260,44 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
 //                                  H = int dP/dq^T dP/dq / dt^2, g = dE/dq (S == 1)
 // lambda starts at 1e-12 max diag(H) per step, x0.1 (floor 1e-20 max diag)
 // after an accepted step, x10 after a rejected step or a failed Cholesky
-// factorisation; a step is accepted when E decreases. Each loop trip runs
-// the residual pass at every group's trial point; when any group of the warp
-// needs a new Jacobian, the warp builds it (S n tangent passes), then each
-// group forms H, factorises and solves on its own.
+// factorisation; a step is accepted when E decreases. One warp per instance:
+// R = 32/S replicas of the stage group evaluate the same point and split the
+// S n Jacobian columns; the Gram matrix, Cholesky and solves are shared by
+// the warp's lanes (the paper's workgroup per trajectory, Fig. GPU).
 // ------------------------------------------------------------------------
 constexpr int kLmMaxTrials = 60;
 
+// Lane identity of the warp-per-instance mapping.
+template <int S>
+struct WarpId {
+  int64_t lane_id, inst;
+  int rep, R;
+  __device__ WarpId(const Bucket& B) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)(blockIdx.x - B.block_begin) * blockDim.x + threadIdx.x) >> 5;
+    lane_id = warp * 32 + lane;
+    inst = warp;
+    R = 32 / S;
+    rep = lane / S;  // rep == R: surplus lanes (S = 3, 5)
+  }
+};
+
+__device__ __forceinline__ double bcast0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
+
 template <int S>
 __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B) {
-  const LaneId<S> id(B);
-  const bool active = id.real && id.inst < B.count;
+  const WarpId<S> id(B);
+  const bool active = id.inst < B.count;
   const int b = active ? (int)id.inst : 0;
   Ctx<S> c(B, A.K, b, id.lane_id, A.history, A.dense_stages);
   const int n = c.n;
   const auto& L = c.L;
   const Lane& ws = c.ws;
   const int64_t D = A.D;
+  const bool writer = active && id.rep == 0;  // replica 0 writes the outputs
+  double* Dn = B.dense + (int64_t)b * B.dense_stride;
+  DenseLayout DL;
+  DL.make(S * n);
 
   for (int d = 0; d < n; ++d) {
     ws[L.qp + d] = A.q_prev0[c.gdof(d)];
@@ -286,21 +307,28 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
   int worst = kConverged, iters_total = 0, evals_total = 0;
   double E = 0.0, lambda = -1.0, hmax = 0.0;
   c.setup();
-  if (!active) phase = kDone;
+  if (!active) phase = kDone;  // warp-uniform
+
+  auto gsum_bcast = [&](double v) {
+    double t = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) t += c.grp.from_full(v, j);
+    return bcast0(t);
+  };
 
   auto finish = [&](int st) {
     worst = max(worst, st);
     for (int d = 0; d < n; ++d) {
-      const double xs = c.grp.from(ws[L.x + d], S - 1);
-      const double xp = (S == 1) ? ws[L.qc + d] : c.grp.from(ws[L.x + d], S - 2);
+      const double xs = c.grp.from_full(ws[L.x + d], S - 1);
+      const double xp = (S == 1) ? ws[L.qc + d] : c.grp.from_full(ws[L.x + d], S - 2);
       ws[L.qp + d] = xp;
       ws[L.qc + d] = xs;
-      if (c.i == 0) {
+      if (writer && c.i == 0) {
         if (A.traj_cur) A.traj_cur[(int64_t)step * D + c.gdof(d)] = xs;
         if (A.traj_prev) A.traj_prev[(int64_t)step * D + c.gdof(d)] = xp;
       }
     }
-    if (A.q_stages_out && step == A.n_steps - 1)
+    if (writer && A.q_stages_out && step == A.n_steps - 1)
       for (int d = 0; d < n; ++d) A.q_stages_out[c.gstage(d)] = ws[L.x + d];
     ++step;
     if (step >= A.n_steps) {
@@ -311,67 +339,63 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     }
   };
 
-  while (__any_sync(0xffffffffu, phase != kDone)) {
+  while (phase != kDone) {
     const double* tau = A.tau ? A.tau + (int64_t)min(step, A.n_steps - 1) * D : nullptr;
-    const double Et = c.evaluate_primal(tau);
-    // 0: nothing, 1: needs a Jacobian at x, 2: needs a new factorisation
-    int need = 0;
-    if (phase != kDone) {
-      ++evals_total;
-      if (phase == kFirst) {
+    const double Et = bcast0(c.evaluate_primal(tau));
+    ++evals_total;
+    double rrt = 0.0, fint = 1.0;
+    for (int d = 0; d < n; ++d) {
+      rrt = fma(ws[L.rt + d], ws[L.rt + d], rrt);
+      if (!isfinite(ws[L.rt + d])) fint = 0.0;
+    }
+    rrt = gsum_bcast(rrt);
+    fint = gsum_bcast(fint);
+    int need = 0;  // 1: Jacobian at x, 2: new factorisation
+    double rr = 0.0;
+    if (phase == kFirst) {
+      for (int d = 0; d < n; ++d) {
+        ws[L.x + d] = ws[L.xt + d];
+        ws[L.r + d] = ws[L.rt + d];
+      }
+      E = Et;
+      rr = rrt;
+      k = 0;
+      lambda = -1.0;
+      need = 1;
+    } else {
+      double rr0 = 0.0;
+      for (int d = 0; d < n; ++d) rr0 = fma(ws[L.r + d], ws[L.r + d], rr0);
+      rr0 = gsum_bcast(rr0);
+      const bool ok = fint == (double)S && isfinite(Et) &&
+                      (Et < E || (S == 1 && Et <= E + kLsEps * fabs(E) && rrt < rr0));
+      if (ok) {
         for (int d = 0; d < n; ++d) {
           ws[L.x + d] = ws[L.xt + d];
           ws[L.r + d] = ws[L.rt + d];
         }
         E = Et;
-        k = 0;
-        lambda = -1.0;
+        rr = rrt;
+        lambda = fmax(lambda * 0.1, 1e-20 * hmax);
+        ++k;
+        ++iters_total;
         need = 1;
       } else {
-        double rr = 0.0, rrt = 0.0, fin = 1.0;
-        for (int d = 0; d < n; ++d) {
-          rr = fma(ws[L.r + d], ws[L.r + d], rr);
-          rrt = fma(ws[L.rt + d], ws[L.rt + d], rrt);
-          if (!isfinite(ws[L.rt + d])) fin = 0.0;
-        }
-        rr = c.grp.sum(rr);
-        rrt = c.grp.sum(rrt);
-        fin = c.grp.sum(fin);
-        const bool ok = fin == (double)S && isfinite(Et) &&
-                        (Et < E || (S == 1 && Et <= E + kLsEps * fabs(E) && rrt < rr));
-        if (ok) {
-          for (int d = 0; d < n; ++d) {
-            ws[L.x + d] = ws[L.xt + d];
-            ws[L.r + d] = ws[L.rt + d];
-          }
-          E = Et;
-          lambda = fmax(lambda * 0.1, 1e-20 * hmax);
-          ++k;
-          ++iters_total;
-          need = 1;
-        } else {
-          lambda *= 10.0;
-          if (++trials >= kLmMaxTrials) finish(kLsFail);
-          else need = 2;
-        }
-      }
-      if (need == 1) {
-        double rr = 0.0, fin = 1.0;
-        for (int d = 0; d < n; ++d) {
-          rr = fma(ws[L.r + d], ws[L.r + d], rr);
-          if (!isfinite(ws[L.r + d])) fin = 0.0;
-        }
-        rr = c.grp.sum(rr);
-        fin = c.grp.sum(fin);
-        if (fin != (double)S || !isfinite(E)) { finish(kNonFinite); need = 0; }
-        else if (sqrt(rr) < A.tol) { finish(kConverged); need = 0; }
-        else if (k >= A.max_iter) { finish(kMaxIter); need = 0; }
+        lambda *= 10.0;
+        if (++trials >= kLmMaxTrials) finish(kLsFail);
+        else need = 2;
       }
     }
-    // Jacobian at x (= the point just evaluated) for every group that needs one
-    if (__any_sync(0xffffffffu, need == 1)) c.build_jacobian();
     if (need == 1) {
-      hmax = c.gram();
+      if (fint != (double)S || !isfinite(E)) { finish(kNonFinite); need = 0; }
+      else if (sqrt(rr) < A.tol) { finish(kConverged); need = 0; }
+      else if (k >= A.max_iter) { finish(kMaxIter); need = 0; }
+    }
+    if (need == 1) {
+      if (id.rep == 0)
+        for (int d = 0; d < n; ++d) Dn[DL.r + c.i * n + d] = ws[L.r + d];
+      __syncwarp();
+      c.build_jacobian_warp(Dn, DL, id.rep, id.R, false);
+      hmax = c.gram_warp(Dn, DL);
       if (lambda < 0.0) lambda = 1e-12 * hmax;
       trials = 0;
       need = 2;
@@ -379,7 +403,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     if (need == 2) {
       bool solved = false;
       while (!solved) {
-        if (c.factor_solve(lambda)) {
+        if (c.factor_solve_warp(Dn, DL, lambda)) {
           solved = true;
         } else {
           lambda *= 10.0;
@@ -389,17 +413,16 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
       if (!solved) {
         finish(kCholFail);
       } else {
-        for (int d = 0; d < n; ++d) ws[L.xt + d] = ws[L.x + d] + ws[L.dl + c.i * n + d];
+        for (int d = 0; d < n; ++d) ws[L.xt + d] = ws[L.x + d] + Dn[DL.dl + c.i * n + d];
         phase = kTrial;
       }
+      __syncwarp();
     }
   }
-  if (active && c.i == 0) {
+  if (writer && c.i == 0) {
     if (A.status) A.status[B.inst_off + b] = worst;
     if (A.iters) A.iters[B.inst_off + b] = iters_total;
     if (A.evals) A.evals[B.inst_off + b] = evals_total;
-  }
-  if (active && c.i == 0) {
     for (int d = 0; d < n; ++d) {
       if (A.q_prev_out) A.q_prev_out[c.gdof(d)] = ws[L.qp + d];
       if (A.q_cur_out) A.q_cur_out[c.gdof(d)] = ws[L.qc + d];
@@ -422,49 +445,51 @@ __global__ void __launch_bounds__(128) k_rollout(const __grid_constant__ LaunchA
 // r(q_*; q_prev, q_cur, tau) = 0 at the solution, dq_* = -Jr^-1 dr, so for a
 // loss gradient gbar = dL/dq_*:  Jr^T mu = gbar, dL/dq_prev = -(dr/dq_prev)^T mu,
 // dL/dq_cur = -(dr/dq_cur)^T mu, dL/dtau = sum_i mu_i. Jr is built exactly
-// (S n tangent passes; the exact Hessian of Eq. EQ for one stage); the
-// known-node products are adjoint sweeps at q_prev and q_cur whose seeds
-// come from the stage transforms' tangents along mu.
+// (S n tangent passes split over the warp's replicas; the exact Hessian of
+// Eq. EQ for one stage) and solved by the warp's pivoted elimination; the
+// known-node products are adjoint sweeps at q_prev and q_cur whose seeds come
+// from the stage transforms' tangents along mu. One warp per instance.
 // ------------------------------------------------------------------------
 template <int S>
 __global__ void __launch_bounds__(128) k_step_backward(const __grid_constant__ LaunchArgs A) {
   const Bucket& B = A.bk[find_bucket(A)];
-  const LaneId<S> id(B);
-  const bool active = id.real && id.inst < B.count;
-  const int b = active ? (int)id.inst : 0;
+  const WarpId<S> id(B);
+  const bool active = id.inst < B.count;
+  if (!active) return;  // warp-uniform
+  const int b = (int)id.inst;
   Ctx<S> c(B, A.K, b, id.lane_id, 0, A.dense_stages);
   const int n = c.n;
   const auto& L = c.L;
   const Lane& ws = c.ws;
+  const bool writer = id.rep == 0;
+  double* Dn = B.dense + (int64_t)b * B.dense_stride;
+  DenseLayout DL;
+  DL.make(S * n);
   for (int d = 0; d < n; ++d) {
     ws[L.qp + d] = A.q_prev0[c.gdof(d)];
     ws[L.qc + d] = A.q_cur0[c.gdof(d)];
   }
   c.setup();
-  for (int d = 0; d < n; ++d) {
-    ws[L.xt + d] = A.q_star[c.gstage(d)];
-    ws[L.g + d] = A.g_bar[c.gstage(d)];
-  }
+  for (int d = 0; d < n; ++d) ws[L.xt + d] = A.q_star[c.gstage(d)];
+  if (writer)
+    for (int d = 0; d < n; ++d) Dn[DL.gb + c.i * n + d] = A.g_bar[c.gstage(d)];
   c.primal(A.tau);
-  c.build_jacobian(true);
-  bool ok = true;
-  if (active) ok = c.solve_transposed(L.g);
-  // own slice of mu into x
-  for (int d = 0; d < n; ++d) ws[L.x + d] = ws[L.dl + c.i * n + d];
+  __syncwarp();
+  c.build_jacobian_warp(Dn, DL, id.rep, id.R, true);
+  const bool ok = c.lu_solve_transposed_warp(Dn, DL);
+  for (int d = 0; d < n; ++d) ws[L.x + d] = Dn[DL.dl + c.i * n + d];
   c.transform_tangents(L.x);
   c.known_node_vjp(0, L.qp, L.r);
   c.known_node_vjp(1, L.qc, L.rt);
-  if (active) {
+  if (writer && c.i == 0) {
     for (int d = 0; d < n; ++d) {
       double gt = 0.0;
-      for (int s = 0; s < S; ++s) gt += ws[L.dl + s * n + d];
-      if (c.i == 0) {
-        A.gq_prev[c.gdof(d)] = ok ? -ws[L.r + d] : NAN;
-        A.gq_cur[c.gdof(d)] = ok ? -ws[L.rt + d] : NAN;
-        A.gtau[c.gdof(d)] = ok ? gt : NAN;
-      }
+      for (int s = 0; s < S; ++s) gt += Dn[DL.dl + s * n + d];
+      A.gq_prev[c.gdof(d)] = ok ? -ws[L.r + d] : NAN;
+      A.gq_cur[c.gdof(d)] = ok ? -ws[L.rt + d] : NAN;
+      A.gtau[c.gdof(d)] = ok ? gt : NAN;
     }
-    if (c.i == 0 && A.status) A.status[B.inst_off + b] = ok ? kConverged : kCholFail;
+    if (A.status) A.status[B.inst_off + b] = ok ? kConverged : kCholFail;
   }
 }
 

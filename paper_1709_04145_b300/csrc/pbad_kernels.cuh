@@ -27,7 +27,7 @@ enum Status { kConverged = 0, kMaxIter = 1, kLsFail = 2, kCholFail = 3, kNonFini
 // Offsets (in doubles) of one lane's workspace.
 struct WsLayout {
   int T, G, acc, axes, V, accd, C, Pb, x, g, d, xt, gt, r, rt, qp, qc, sh, yh, rho;
-  int u, jc, J, H, A, gg, dl;  // dense Newton storage (Sd stages; absent when Sd == 0)
+  int u, jc;  // Jacobian-column scratch (present when Sd > 0)
   int64_t total;
   __host__ __device__ void make(int N, int n, int m, int Sd = 0) {
     int o = 0;
@@ -51,15 +51,20 @@ struct WsLayout {
     sh = o; o += m * n;
     yh = o; o += m * n;
     rho = o; o += (m > 0 ? m : 1);
-    const int Sn = Sd * n;
     u = o; o += (Sd ? n : 0);
     jc = o; o += (Sd ? n : 0);
-    gg = o; o += Sn;
-    dl = o; o += Sn;
-    J = o; o += n * Sn;
-    H = o; o += Sn * Sn;
-    A = o; o += Sn * Sn;
     total = o;
+  }
+};
+
+// Per-instance dense storage of Newton and the adjoint (Sn = stages * n):
+// J column-major [Sn][Sn] (column c contiguous; read row-major it is Jr^T),
+// H and A row-major [Sn][Sn], then r, gg, dl, gb [Sn] each.
+struct DenseLayout {
+  int64_t J, H, A, r, gg, dl, gb, total;
+  __host__ __device__ void make(int Sn) {
+    const int64_t q = (int64_t)Sn * Sn;
+    J = 0; H = q; A = 2 * q; r = 3 * q; gg = r + Sn; dl = gg + Sn; gb = dl + Sn; total = gb + Sn;
   }
 };
 
@@ -147,20 +152,47 @@ struct Ctx {
     for (int k = 0; k < 12; ++k) ws[off + k] = v[k];
   }
 
+  // L1 prefetch hints for the next link's operands (issued one link ahead;
+  // only valid addresses are touched).
+  __device__ __forceinline__ void pf_g(const double* a) const {
+    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
+  }
+  __device__ __forceinline__ void pf_ws(int64_t k) const { pf_g(&ws[k]); }
+  __device__ __forceinline__ void prefetch_model(int l) const {
+#pragma unroll
+    for (int k = 0; k < 12; ++k) pf_g(&B.rest[((int64_t)l * 12 + k) * B.count + b]);
+#pragma unroll
+    for (int k = 0; k < 10; ++k) pf_g(&B.mm[((int64_t)l * 10 + k) * B.count + b]);
+  }
+  __device__ __forceinline__ void prefetch_ws(int off, int cnt) const {
+    for (int k = 0; k < cnt; ++k) pf_ws(off + k);
+  }
+
   // T_l = T_parent * X_l * Rot(q_l). Ball joints also return Jr(q_l).
   __device__ __forceinline__ void link_fk(int l, const double* Tp, const double* ql, double* T,
                                           double* Jr) const {
-    double X[12], R[9], XJ[12];
-#pragma unroll
-    for (int k = 0; k < 12; ++k) X[k] = rest(l, k);
+    double R[9], XJ[12];
     const double u[3] = {B.axis[3 * l], B.axis[3 * l + 1], B.axis[3 * l + 2]};
     joint_rotation(B.jtype[l], u, ql, R, Jr);
+    if (B.rest_eye[l]) {
+      // identity rest rotation: X_l Rot = [Rot | t_X]
 #pragma unroll
-    for (int r = 0; r < 3; ++r) {
+      for (int r = 0; r < 3; ++r) {
 #pragma unroll
-      for (int c = 0; c < 3; ++c)
-        XJ[4 * r + c] = fma(X[4 * r], R[c], fma(X[4 * r + 1], R[3 + c], X[4 * r + 2] * R[6 + c]));
-      XJ[4 * r + 3] = X[4 * r + 3];
+        for (int c = 0; c < 3; ++c) XJ[4 * r + c] = R[3 * r + c];
+        XJ[4 * r + 3] = rest(l, 4 * r + 3);
+      }
+    } else {
+      double X[12];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) X[k] = rest(l, k);
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+          XJ[4 * r + c] = fma(X[4 * r], R[c], fma(X[4 * r + 1], R[3 + c], X[4 * r + 2] * R[6 + c]));
+        XJ[4 * r + 3] = X[4 * r + 3];
+      }
     }
     if (Tp) compose(Tp, XJ, T);
     else {
@@ -321,8 +353,15 @@ struct Ctx {
     const double dt2 = K.dt * K.dt;
     const bool chain = B.chain;
     double Tp[12];  // parent transform (kept in registers along a chain)
+    prefetch_model(0);
+    prefetch_ws(L.C, 12);
     for (int l = 0; l < N; ++l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      if (l + 1 < N) {
+        prefetch_model(l + 1);
+        prefetch_ws(L.C + 12 * (l + 1), 12);
+        prefetch_ws(L.xt + B.dof[l + 1], ndof(l + 1));
+      }
       double T[12], Jr[9], q3[3], w[9];
       if (p >= 0 && !chain) load12(L.T + 12 * p, Tp);
       for (int k = 0; k < nd; ++k) q3[k] = ws[L.xt + d0 + k];
@@ -369,6 +408,11 @@ struct Ctx {
     double carry[6] = {0, 0, 0, 0, 0, 0};  // child subtree sum along a chain
     for (int l = N - 1; l >= 0; --l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      if (l > 0) {
+        prefetch_ws(L.acc + 6 * (l - 1), 6);
+        prefetch_ws(L.T + 12 * (l - 1), 12);
+        prefetch_ws(L.axes + 9 * (l - 1), 3 * ndof(l - 1));
+      }
       double a[6];
       for (int k = 0; k < 6; ++k) a[k] = ws[L.acc + 6 * l + k] + carry[k];
       const double o[3] = {ws[L.T + 12 * l + 3], ws[L.T + 12 * l + 7], ws[L.T + 12 * l + 11]};
@@ -413,6 +457,14 @@ struct Ctx {
     double V[6] = {0, 0, 0, 0, 0, 0};  // parent twist (kept in registers along a chain)
     for (int l = 0; l < N; ++l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      if (l + 1 < N) {
+        prefetch_ws(L.T + 12 * (l + 1), 12);
+        prefetch_ws(L.G + 12 * (l + 1), 12);
+        prefetch_ws(L.axes + 9 * (l + 1), 3 * ndof(l + 1));
+        prefetch_ws(dir + B.dof[l + 1], ndof(l + 1));
+#pragma unroll
+        for (int k = 0; k < 10; ++k) pf_g(&B.mm[((int64_t)(l + 1) * 10 + k) * B.count + b]);
+      }
       if (!chain) {
         if (p >= 0) {
           for (int k = 0; k < 6; ++k) V[k] = ws[L.V + 6 * p + k];
@@ -474,6 +526,13 @@ struct Ctx {
     double carry[6] = {0, 0, 0, 0, 0, 0};
     for (int l = N - 1; l >= 0; --l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      if (l > 0) {
+        prefetch_ws(L.accd + 6 * (l - 1), 6);
+        prefetch_ws(L.acc + 6 * (l - 1), 6);
+        prefetch_ws(L.V + 6 * (l - 1), 6);
+        prefetch_ws(L.T + 12 * (l - 1), 12);
+        prefetch_ws(L.axes + 9 * (l - 1), 3 * ndof(l - 1));
+      }
       double ad[6], T[12];
       for (int k = 0; k < 6; ++k) ad[k] = ws[L.accd + 6 * l + k] + carry[k];
       load12(L.T + 12 * l, T);
@@ -561,141 +620,179 @@ struct Ctx {
     return E;
   }
 
-  // ----------------------------------------------------------- Newton (LM)
-  // Jacobian rows of the own stage at the primal point: column c = (stage
-  // k, dof e) is the tangent of every stage's residual along the unit
-  // direction of q_{k,e} (S >= 2: Jr of Eq. HOC; S == 1: the Gauss-Newton
-  // matrix of Eq. EQ, int dP/dq^T dP/dq / dt^2). Row-major [n][S n] at J.
-  // S n tangent passes; convergent across the warp.
-  // exact = true gives Jr itself for S == 1 too (the exact Hessian of Eq. EQ).
-  __device__ __noinline__ void build_jacobian(bool exact = false) const {
+  // ----------------------------------------------------- Newton (LM), adjoint
+  // Warp-cooperative dense algebra. One warp owns one instance: R = 32/S
+  // replicas of the S-lane stage group evaluate the residual pass at the same
+  // point and split the Jacobian columns; the Gram matrix, the factorisation
+  // and the solves are shared by all 32 lanes through the instance's dense
+  // region (D). All these functions are called convergently by the warp.
+
+  // Column c = (stage k = c / n, dof e = c % n) of Jr at the primal point
+  // (S >= 2: the stage residuals of Eq. HOC; S == 1 with exact = false: the
+  // Gauss-Newton matrix of Eq. EQ, int dP/dq^T dP/dq / dt^2; exact = true:
+  // the Hessian of Eq. EQ). Replica `rep` of R computes columns rep, rep+R,
+  // ...; every lane writes its stage's rows. S n tangent passes in total.
+  __device__ __noinline__ void build_jacobian_warp(double* D, const DenseLayout& DL, int rep, int R,
+                                                   bool exact) const {
     const int Sn = S * n;
-    for (int k = 0; k < S; ++k)
-      for (int e = 0; e < n; ++e) {
-        for (int d = 0; d < n; ++d) ws[L.u + d] = (i == k && d == e) ? 1.0 : 0.0;
-        if (S == 1 && !exact) tangent_pass<kGn>(L.u, L.jc, 1.0);
-        else tangent_pass<kJvp>(L.u, L.jc, 1.0);
-        for (int d = 0; d < n; ++d) ws[L.J + (int64_t)d * Sn + k * n + e] = ws[L.jc + d];
-      }
+    const int rounds = (Sn + R - 1) / R;
+    for (int t = 0; t < rounds; ++t) {
+      const int c = rep + t * R;
+      const bool real = c < Sn && rep < R;
+      const int cc = real ? c : 0;  // surplus replicas repeat column 0 and discard it
+      const int k = cc / n, e = cc - k * n;
+      for (int d = 0; d < n; ++d) ws[L.u + d] = (i == k && d == e) ? 1.0 : 0.0;
+      if (S == 1 && !exact) tangent_pass<kGn>(L.u, L.jc, 1.0);
+      else tangent_pass<kJvp>(L.u, L.jc, 1.0);
+      if (real)
+        for (int d = 0; d < n; ++d) D[DL.J + (int64_t)c * Sn + i * n + d] = ws[L.jc + d];
+    }
+    __syncwarp();
   }
 
-  // H = Jr^T Jr and gg = Jr^T r (S >= 2) or H = the Gauss-Newton matrix and
-  // gg = r (S == 1), full symmetric H on every lane of the group. Returns
-  // max diag(H). Group-divergent (group-mask shuffles).
-  __device__ __noinline__ double gram() const {
+  // H = Jr^T Jr, gg = Jr^T r (S >= 2) or H = the Gauss-Newton matrix, gg = r
+  // (S == 1). Needs r in D (written by replica 0 before). Returns max diag(H)
+  // (same value on every lane).
+  __device__ __noinline__ double gram_warp(double* D, const DenseLayout& DL) const {
     const int Sn = S * n;
-    double hmax = 0.0;
+    const int lane = threadIdx.x & 31;
     if (S == 1) {
-      for (int a = 0; a < n; ++a)
-        for (int c = 0; c <= a; ++c) {
-          const double h = ws[L.J + (int64_t)a * Sn + c];
-          ws[L.H + (int64_t)a * Sn + c] = h;
-          ws[L.H + (int64_t)c * Sn + a] = h;
-        }
-      for (int a = 0; a < n; ++a) ws[L.gg + a] = ws[L.r + a];
+      for (int a = lane; a < Sn; a += 32) {
+        for (int c = 0; c < Sn; ++c) D[DL.H + (int64_t)a * Sn + c] = D[DL.J + (int64_t)c * Sn + a];
+        D[DL.gg + a] = D[DL.r + a];
+      }
     } else {
-      for (int a = 0; a < Sn; ++a) {
-        for (int c = 0; c <= a; ++c) {
-          double h = 0.0;
-          for (int d = 0; d < n; ++d)
-            h = fma(ws[L.J + (int64_t)d * Sn + a], ws[L.J + (int64_t)d * Sn + c], h);
-          h = grp.sum(h);
-          ws[L.H + (int64_t)a * Sn + c] = h;
-          ws[L.H + (int64_t)c * Sn + a] = h;
-        }
-        double gsum = 0.0;
-        for (int d = 0; d < n; ++d) gsum = fma(ws[L.J + (int64_t)d * Sn + a], ws[L.r + d], gsum);
-        ws[L.gg + a] = grp.sum(gsum);
+      const int npairs = Sn * (Sn + 1) / 2;
+      for (int pidx = lane; pidx < npairs; pidx += 32) {
+        // pair (a, c), a >= c, row-major over the lower triangle
+        int a = (int)((sqrt(8.0 * pidx + 1.0) - 1.0) * 0.5);
+        while ((a + 1) * (a + 2) / 2 <= pidx) ++a;
+        while (a * (a + 1) / 2 > pidx) --a;
+        const int c = pidx - a * (a + 1) / 2;
+        const double* ja = D + DL.J + (int64_t)a * Sn;
+        const double* jb = D + DL.J + (int64_t)c * Sn;
+        double h = 0.0;
+        for (int rr = 0; rr < Sn; ++rr) h = fma(ja[rr], jb[rr], h);
+        D[DL.H + (int64_t)a * Sn + c] = h;
+        D[DL.H + (int64_t)c * Sn + a] = h;
+      }
+      for (int a = lane; a < Sn; a += 32) {
+        const double* ja = D + DL.J + (int64_t)a * Sn;
+        double g = 0.0;
+        for (int rr = 0; rr < Sn; ++rr) g = fma(ja[rr], D[DL.r + rr], g);
+        D[DL.gg + a] = g;
       }
     }
-    for (int a = 0; a < Sn; ++a) hmax = fmax(hmax, ws[L.H + (int64_t)a * Sn + a]);
+    __syncwarp();
+    double hmax = 0.0;
+    for (int a = lane; a < Sn; a += 32) hmax = fmax(hmax, D[DL.H + (int64_t)a * Sn + a]);
+    for (int o = 16; o > 0; o >>= 1) hmax = fmax(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
     return hmax;
   }
 
-  // Cholesky of H + lambda I into A (lower triangle) and dl = -(H + lambda I)^-1 gg.
-  // Returns false if a pivot is not positive. Lane-local (same work on every
-  // lane of the group).
-  __device__ __noinline__ bool factor_solve(double lambda) const {
+  __device__ __forceinline__ static double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+  }
+
+  // Cholesky of H + lambda I into A (lower triangle, row-major) and
+  // dl = -(H + lambda I)^-1 gg. Returns false (on every lane) if a pivot is
+  // not positive.
+  __device__ __noinline__ bool factor_solve_warp(double* D, const DenseLayout& DL, double lambda) const {
     const int Sn = S * n;
+    const int lane = threadIdx.x & 31;
+    double* A = D + DL.A;
+    const double* H = D + DL.H;
     for (int j = 0; j < Sn; ++j) {
-      double sjj = ws[L.H + (int64_t)j * Sn + j] + lambda;
-      for (int k = 0; k < j; ++k) {
-        const double l = ws[L.A + (int64_t)j * Sn + k];
-        sjj = fma(-l, l, sjj);
+      double s = 0.0;
+      for (int k = lane; k < j; k += 32) s = fma(A[(int64_t)j * Sn + k], A[(int64_t)j * Sn + k], s);
+      s = warp_sum(s);
+      const double dj = H[(int64_t)j * Sn + j] + lambda - s;
+      if (!(dj > 0.0)) return false;
+      const double ljj = sqrt(dj), inv = 1.0 / ljj;
+      for (int r = j + 1 + lane; r < Sn; r += 32) {
+        double t = H[(int64_t)r * Sn + j];
+        for (int k = 0; k < j; ++k) t = fma(-A[(int64_t)r * Sn + k], A[(int64_t)j * Sn + k], t);
+        A[(int64_t)r * Sn + j] = t * inv;
       }
-      if (!(sjj > 0.0)) return false;
-      const double djj = sqrt(sjj);
-      ws[L.A + (int64_t)j * Sn + j] = djj;
-      const double inv = 1.0 / djj;
-      for (int r = j + 1; r < Sn; ++r) {
-        double t = ws[L.H + (int64_t)r * Sn + j];
-        for (int k = 0; k < j; ++k) t = fma(-ws[L.A + (int64_t)r * Sn + k], ws[L.A + (int64_t)j * Sn + k], t);
-        ws[L.A + (int64_t)r * Sn + j] = t * inv;
-      }
+      if (lane == 0) A[(int64_t)j * Sn + j] = ljj;
+      __syncwarp();
     }
+    double* y = D + DL.dl;
     for (int r = 0; r < Sn; ++r) {
-      double t = -ws[L.gg + r];
-      for (int k = 0; k < r; ++k) t = fma(-ws[L.A + (int64_t)r * Sn + k], ws[L.dl + k], t);
-      ws[L.dl + r] = t / ws[L.A + (int64_t)r * Sn + r];
+      double s = 0.0;
+      for (int k = lane; k < r; k += 32) s = fma(A[(int64_t)r * Sn + k], y[k], s);
+      s = warp_sum(s);
+      const double v = (-D[DL.gg + r] - s) / A[(int64_t)r * Sn + r];
+      __syncwarp();
+      if (lane == 0) y[r] = v;
+      __syncwarp();
     }
     for (int r = Sn - 1; r >= 0; --r) {
-      double t = ws[L.dl + r];
-      for (int k = r + 1; k < Sn; ++k) t = fma(-ws[L.A + (int64_t)k * Sn + r], ws[L.dl + k], t);
-      ws[L.dl + r] = t / ws[L.A + (int64_t)r * Sn + r];
+      double s = 0.0;
+      for (int k = r + 1 + lane; k < Sn; k += 32) s = fma(A[(int64_t)k * Sn + r], y[k], s);
+      s = warp_sum(s);
+      const double v = (y[r] - s) / A[(int64_t)r * Sn + r];
+      __syncwarp();
+      if (lane == 0) y[r] = v;
+      __syncwarp();
     }
     return true;
   }
 
-  // ---------------------------------------------------- IFT adjoint helpers
-  // Solves Jr^T mu = gbar for the whole instance (every lane of the group
-  // gets all of mu in dl): the full Jr^T is gathered into A (from the
-  // lanes' rows in J) and solved by Gaussian elimination with partial
-  // pivoting; gbar is gathered from the lanes' slices at offset `gb`.
-  // Returns false on a zero pivot. Group-divergent (group-mask shuffles).
-  __device__ __noinline__ bool solve_transposed(int gb) const {
+  // Solves Jr^T mu = gb by Gaussian elimination with partial pivoting on the
+  // J region (column-major J read row-major is Jr^T), mu into dl. Returns
+  // false on a zero pivot. Destroys J.
+  __device__ __noinline__ bool lu_solve_transposed_warp(double* D, const DenseLayout& DL) const {
     const int Sn = S * n;
-    for (int row = 0; row < Sn; ++row) {      // row of Jr
-      const int owner = row / n, d = row - owner * n;
-      for (int col = 0; col < Sn; ++col) {
-        const double v = grp.from(ws[L.J + (int64_t)d * Sn + col], owner);
-        ws[L.A + (int64_t)col * Sn + row] = v;  // A = Jr^T
-      }
-    }
-    for (int row = 0; row < Sn; ++row) {
-      const int owner = row / n, d = row - owner * n;
-      ws[L.dl + row] = grp.from(ws[gb + d], owner);
-    }
+    const int lane = threadIdx.x & 31;
+    double* M = D + DL.J;
+    double* b = D + DL.gb;
     for (int c = 0; c < Sn; ++c) {
-      int piv = c;
-      double best = fabs(ws[L.A + (int64_t)c * Sn + c]);
-      for (int r = c + 1; r < Sn; ++r) {
-        const double v = fabs(ws[L.A + (int64_t)r * Sn + c]);
+      double best = -1.0;
+      int piv = Sn;
+      for (int r = c + lane; r < Sn; r += 32) {
+        const double v = fabs(M[(int64_t)r * Sn + c]);
         if (v > best) { best = v; piv = r; }
+      }
+      for (int o = 16; o > 0; o >>= 1) {
+        const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+        const int op = __shfl_xor_sync(0xffffffffu, piv, o);
+        if (ob > best || (ob == best && op < piv)) { best = ob; piv = op; }
       }
       if (!(best > 0.0)) return false;
       if (piv != c) {
-        for (int k = 0; k < Sn; ++k) {
-          const double t = ws[L.A + (int64_t)c * Sn + k];
-          ws[L.A + (int64_t)c * Sn + k] = ws[L.A + (int64_t)piv * Sn + k];
-          ws[L.A + (int64_t)piv * Sn + k] = t;
+        for (int k = lane; k < Sn; k += 32) {
+          const double t = M[(int64_t)c * Sn + k];
+          M[(int64_t)c * Sn + k] = M[(int64_t)piv * Sn + k];
+          M[(int64_t)piv * Sn + k] = t;
         }
-        const double t = ws[L.dl + c];
-        ws[L.dl + c] = ws[L.dl + piv];
-        ws[L.dl + piv] = t;
+        if (lane == 0) {
+          const double t = b[c];
+          b[c] = b[piv];
+          b[piv] = t;
+        }
       }
-      const double inv = 1.0 / ws[L.A + (int64_t)c * Sn + c];
-      for (int r = c + 1; r < Sn; ++r) {
-        const double f = ws[L.A + (int64_t)r * Sn + c] * inv;
-        if (f == 0.0) continue;
-        for (int k = c; k < Sn; ++k)
-          ws[L.A + (int64_t)r * Sn + k] = fma(-f, ws[L.A + (int64_t)c * Sn + k], ws[L.A + (int64_t)r * Sn + k]);
-        ws[L.dl + r] = fma(-f, ws[L.dl + c], ws[L.dl + r]);
+      __syncwarp();
+      const double inv = 1.0 / M[(int64_t)c * Sn + c];
+      for (int r = c + 1 + lane; r < Sn; r += 32) {
+        const double f = M[(int64_t)r * Sn + c] * inv;
+        if (f != 0.0) {
+          for (int k = c + 1; k < Sn; ++k) M[(int64_t)r * Sn + k] = fma(-f, M[(int64_t)c * Sn + k], M[(int64_t)r * Sn + k]);
+          b[r] = fma(-f, b[c], b[r]);
+        }
       }
+      __syncwarp();
     }
+    double* mu = D + DL.dl;
     for (int r = Sn - 1; r >= 0; --r) {
-      double t = ws[L.dl + r];
-      for (int k = r + 1; k < Sn; ++k) t = fma(-ws[L.A + (int64_t)r * Sn + k], ws[L.dl + k], t);
-      ws[L.dl + r] = t / ws[L.A + (int64_t)r * Sn + r];
+      double s = 0.0;
+      for (int k = r + 1 + lane; k < Sn; k += 32) s = fma(M[(int64_t)r * Sn + k], mu[k], s);
+      s = warp_sum(s);
+      const double v = (b[r] - s) / M[(int64_t)r * Sn + r];
+      __syncwarp();
+      if (lane == 0) mu[r] = v;
+      __syncwarp();
     }
     return true;
   }

@@ -241,3 +241,40 @@ def ball_chains(count: int = 4096, n_links: int = 10, seed_base: int = 2000,
     q0, qd0 = random_state(spec, seed_base + 2)
     return dict(spec=spec, q0=q0, qd0=qd0, dt=0.033, stages=3, history=8,
                 tol=1e-8, n_steps=n_steps, solver="lbfgs")
+
+
+def uneven_batch(seed_base: int = 3000, n_steps: int = 10):
+    """One launch over three buckets: 1024 humanoid trees (Newton), 1024
+    chains of 50 hinge rods and 2048 chains of 5 hinge rods (L-BFGS m = 8);
+    torques N(0, 0.1^2) per DOF per step, dt = 0.05, two stages."""
+    specs = [humanoid(1024, seed_base + 1), rod_chain(1024, 50, name="rod_chain50"),
+             rod_chain(2048, 5, name="rod_chain5")]
+    states = [random_state(s, seed_base + 10 + k) for k, s in enumerate(specs)]
+    taus = [torques(s, n_steps, seed_base + 20 + k, sigma=0.1) for k, s in enumerate(specs)]
+    return dict(specs=specs, states=states, taus=taus, dt=0.05, stages=2, history=8,
+                solvers=("newton", "lbfgs", "lbfgs"), n_steps=n_steps, tol=1e-8)
+
+
+def humanoid_adjoint(count: int = 1024, seed_base: int = 4000, n_steps: int = 64):
+    """Differentiation workload: humanoids, 64 steps at dt = 0.033 with two
+    stages; loss = squared distance of the end effector (tip of limb 1's last
+    link) to a target in a 1 m ball around its rest position at the final
+    step; states checkpointed every 8 steps."""
+    spec = humanoid(count, seed_base + 1)
+    q0, qd0 = random_state(spec, seed_base + 2, pose_scale=np.pi / 8, vel_sigma=0.5)
+    tau = torques(spec, n_steps, seed_base + 3, sigma=0.1)
+    link = 4
+    tip = np.zeros((count, 3))
+    tip[:, 2] = -spec.length[:, link]
+    return dict(spec=spec, q0=q0, qd0=qd0, tau=tau, dt=0.033, stages=2, n_steps=n_steps,
+                checkpoint_every=8, ee_link=link, ee_point=tip, target_seed=seed_base + 4,
+                tol=1e-8)
+
+
+def scaling_chains(n_links: int, count: int = 256, seed_base: int = 5000, n_steps: int = 50):
+    """Scaling study: hinge rod chains of n_links links, batch 256, dt = 0.1,
+    four stages; L-BFGS (m = 8) against Newton on the same inputs."""
+    spec = rod_chain(count, n_links, name=f"rod_chain{n_links}")
+    q0, qd0 = random_state(spec, seed_base + n_links)
+    return dict(spec=spec, q0=q0, qd0=qd0, dt=0.1, stages=4, history=8, n_steps=n_steps,
+                tol=1e-8)

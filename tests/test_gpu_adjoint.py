@@ -33,7 +33,8 @@ def test_step_backward_matches_oracle(S):
     qp = q0 + nodes[0] * dt * qd0
     tau = rng.normal(0, 0.1, batch.D)
     t = lambda a: torch.tensor(a, device=dev)
-    out = P.step(batch, t(qp), t(q0), t(tau), dt, S, P.NEWTON, 8, 1e-10, 100)
+    # tolerance above the FP64 floor of r (~1e-10 for three stages at this dt)
+    out = P.step(batch, t(qp), t(q0), t(tau), dt, S, P.NEWTON, 8, 1e-10 if S < 3 else 1e-9, 100)
     assert (out["status"] == 0).all()
     qs = out["q_stages"]
     gbar = rng.normal(size=S * batch.D)
