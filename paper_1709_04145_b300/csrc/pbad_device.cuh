@@ -98,7 +98,8 @@ __device__ __forceinline__ void rodrigues(const double* v, double c0, double c1,
 
 // Scalar functions of x = |theta|^2 for the exponential map:
 //   b(x) = (1 - cos phi)/x, h(x) = (phi - sin phi)/phi^3 and their x-derivatives,
-//   plus cos phi and a = sin(phi)/phi. Power series below x = 0.25.
+//   plus cos phi and a = sin(phi)/phi. Power series below x = 1 (terms
+//   through x^9; the remainder is below 2e-20), closed forms above.
 struct ExpCoef {
   double c, a, b, h, db, dh;
 };
@@ -107,8 +108,8 @@ __device__ __forceinline__ ExpCoef exp_coef(double x) {
   ExpCoef e;
   e.db = 0.0;
   e.dh = 0.0;
-  if (x < 0.25) {
-    // Horner in x; terms through x^9 (remainder < 1e-21 at x = 0.25)
+  if (x < 1.0) {
+    // Horner in x; terms through x^9
     // a = sum (-1)^k x^k/(2k+1)!, b = sum (-1)^k x^k/(2k+2)!, h = sum (-1)^k x^k/(2k+3)!
     const double ia[10] = {1.0, -1.0 / 6, 1.0 / 120, -1.0 / 5040, 1.0 / 362880, -1.0 / 39916800,
                            1.0 / 6227020800.0, -1.0 / 1307674368000.0, 1.0 / 355687428096000.0,
@@ -159,15 +160,18 @@ __device__ __forceinline__ ExpCoef exp_coef(double x) {
 // Joint rotation (and, for balls, the right Jacobian Jr) of one joint.
 //   hinge: R = Rot(u, q), world axis w = R_link u
 //   ball:  R = exp([theta]x), world axes w_k = R_link Jr(theta) e_k
+// ec (optional) receives the exponential-map coefficients with their
+// derivatives, for the tangent passes at the same configuration.
 __device__ __forceinline__ void joint_rotation(int jt, const double* u, const double* q, double* R,
-                                               double* Jr) {
+                                               double* Jr, ExpCoef* ec = nullptr) {
   if (jt == 0) {
     double s, c;
     sincos(q[0], &s, &c);
     rodrigues(u, c, s, 1.0 - c, R);
   } else {
     const double x = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
-    const ExpCoef e = exp_coef<false>(x);
+    const ExpCoef e = ec ? exp_coef<true>(x) : exp_coef<false>(x);
+    if (ec) *ec = e;
     rodrigues(q, e.c, e.a, e.b, R);
     // Jr = (1 - h x) I - b [theta]x + h theta theta^T
     rodrigues(q, fma(-e.h, x, 1.0), -e.b, e.h, Jr);
@@ -176,9 +180,15 @@ __device__ __forceinline__ void joint_rotation(int jt, const double* u, const do
 
 // Derivative of Jr along v: -2 (theta.v) b' K - b [v]x + 2 (theta.v) h' K^2 + h ([v]x K + K [v]x)
 // with K = [theta]x and K^2 = theta theta^T - x I.
-__device__ __forceinline__ void jr_tangent(const double* th, const double* v, double* dJ) {
+// (b, h, db, dh) of the exponential map at th, as cached by the residual pass.
+__device__ __forceinline__ void jr_tangent(const double* th, const double* v, const double* bh,
+                                           double* dJ) {
   const double x = fma(th[0], th[0], fma(th[1], th[1], th[2] * th[2]));
-  const ExpCoef e = exp_coef<true>(x);
+  ExpCoef e;
+  e.b = bh[0];
+  e.h = bh[1];
+  e.db = bh[2];
+  e.dh = bh[3];
   const double tv = dot3(th, v);
   const double cb = -2.0 * tv * e.db, ch = 2.0 * tv * e.dh;
   // [v]x K + K [v]x = v th^T + th v^T - 2 (v.th) I

@@ -26,7 +26,7 @@ enum Status { kConverged = 0, kMaxIter = 1, kLsFail = 2, kCholFail = 3, kNonFini
 
 // Offsets (in doubles) of one lane's workspace.
 struct WsLayout {
-  int T, G, acc, axes, V, accd, C, Pb, x, g, d, xt, gt, r, rt, qp, qc, sh, yh, rho;
+  int T, G, acc, axes, V, accd, C, Pb, ec, x, g, d, xt, gt, r, rt, qp, qc, sh, yh, rho;
   int u, jc;  // Jacobian-column scratch (present when Sd > 0)
   int64_t total;
   __host__ __device__ void make(int N, int n, int m, int Sd = 0) {
@@ -39,6 +39,7 @@ struct WsLayout {
     accd = o; o += 6 * N;
     C = o; o += 12 * N;
     Pb = o; o += 9 * N;
+    ec = o; o += 4 * N;
     x = o; o += n;
     g = o; o += n;
     d = o; o += n;
@@ -170,10 +171,10 @@ struct Ctx {
 
   // T_l = T_parent * X_l * Rot(q_l). Ball joints also return Jr(q_l).
   __device__ __forceinline__ void link_fk(int l, const double* Tp, const double* ql, double* T,
-                                          double* Jr) const {
+                                          double* Jr, ExpCoef* ec = nullptr) const {
     double R[9], XJ[12];
     const double u[3] = {B.axis[3 * l], B.axis[3 * l + 1], B.axis[3 * l + 2]};
-    joint_rotation(B.jtype[l], u, ql, R, Jr);
+    joint_rotation(B.jtype[l], u, ql, R, Jr, ec);
     if (B.rest_eye[l]) {
       // identity rest rotation: X_l Rot = [Rot | t_X]
 #pragma unroll
@@ -365,7 +366,14 @@ struct Ctx {
       double T[12], Jr[9], q3[3], w[9];
       if (p >= 0 && !chain) load12(L.T + 12 * p, Tp);
       for (int k = 0; k < nd; ++k) q3[k] = ws[L.xt + d0 + k];
-      link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr);
+      ExpCoef ec;
+      link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr, nd == 3 ? &ec : nullptr);
+      if (nd == 3) {  // cached for the tangent passes at this point
+        ws[L.ec + 4 * l] = ec.b;
+        ws[L.ec + 4 * l + 1] = ec.h;
+        ws[L.ec + 4 * l + 2] = ec.db;
+        ws[L.ec + 4 * l + 3] = ec.dh;
+      }
       store12(L.T + 12 * l, T);
       link_axes(l, T, Jr, w);
       for (int k = 0; k < 3 * nd; ++k) ws[L.axes + 9 * l + k] = w[k];
@@ -565,12 +573,13 @@ struct Ctx {
         const double mdo[3] = {ad[0] - t2[0] - t3[0], ad[1] - t2[1] - t3[1], ad[2] - t2[2] - t3[2]};
         double dJ[9];
         if (nd == 3) {
-          double th[3], v[3];
+          double th[3], v[3], bh[4];
           for (int k = 0; k < 3; ++k) {
             th[k] = ws[L.xt + d0 + k];
             v[k] = ws[dir + d0 + k];
           }
-          jr_tangent(th, v, dJ);
+          for (int k = 0; k < 4; ++k) bh[k] = ws[L.ec + 4 * l + k];
+          jr_tangent(th, v, bh, dJ);
         }
         for (int k = 0; k < nd; ++k) {
           const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
