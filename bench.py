@@ -76,6 +76,9 @@ def parse():
     p.add_argument("--plain-instances", type=int, default=8,
                    help="instances timed in the plain form (one launch per instance-step)")
     p.add_argument("--plain-timesteps", type=int, default=10)
+    p.add_argument("--throughput-instances", type=int, default=65536,
+                   help="instances of the large-batch throughput point (0 = skip)")
+    p.add_argument("--throughput-timesteps", type=int, default=20)
     p.add_argument("--adjoint-steps", type=int, default=8,
                    help="steps of the differentiable humanoid rollout timed forward and forward+adjoint "
                         "(0 = skip; the workload defines 64)")
@@ -229,6 +232,41 @@ def autotune(P, batch, args, w):
         if ms < best_ms:
             best, best_ms = threads, ms
     return best
+
+
+def measure_throughput_point(P, args, dev, threads):
+    """The same rollout on a large batch (65536 ten-link ball chains, 20
+    steps): every FP64 sub-partition busy. Returns link-steps/s and the FP64
+    roofline fraction."""
+    import numpy as np
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    w = I.ball_chains(count=args.throughput_instances, n_links=args.links, seed_base=2500,
+                      n_steps=args.throughput_timesteps)
+    w["max_iter"], w["tol"] = args.max_iter, args.tol
+    spec = w["spec"]
+    S, dt, m = w["stages"], w["dt"], w["history"]
+    nodes, _ = P.colloc(S)
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=S, max_history=m)
+    batch.set_threads(threads)
+    qp = torch.tensor((w["q0"] + nodes[0] * dt * w["qd0"]).reshape(-1), device=dev)
+    qc = torch.tensor(w["q0"].reshape(-1), device=dev)
+    T = w["n_steps"]
+    P.rollout(batch, qp, qc, None, 1, dt, S, P.LBFGS, m, w["tol"], w["max_iter"], want_traj=False)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = P.rollout(batch, qp, qc, None, T, dt, S, P.LBFGS, m, w["tol"], w["max_iter"], want_traj=False)
+    e1.record()
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ev = out["evals"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    flops = float(ev.sum()) * flops_per_eval(spec.jtype.tolist(), S) + \
+        float(it.sum()) * lbfgs_flops_per_iter(spec.n_dof, S, m)
+    return {"value": spec.count * spec.n_links * T / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "instances": spec.count, "timesteps": T, "achieved_tflops": flops / (ms / 1e3) / 1e12,
+            "evals_per_step": float(ev.mean() / T)}
 
 
 def measure_plain(P, w, args, dev):
@@ -465,6 +503,10 @@ def run_ours(args):
         plain = measure_plain(P, w, args, dev)
         line["plain"] = plain
         line["batched_vs_plain"] = value / world / plain["value"]
+    if rank == 0 and args.throughput_instances > 0:
+        tp = measure_throughput_point(P, args, dev, tuned)
+        tp["frac_of_fp64_peak"] = tp["achieved_tflops"] / peak
+        line["throughput_point"] = tp
     if rank == 0 and args.adjoint_steps > 0:
         line["fwd_adjoint"] = measure_adjoint(P, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

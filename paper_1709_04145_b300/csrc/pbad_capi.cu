@@ -77,7 +77,7 @@ struct pbad_batch {
   int device = 0, max_stages = 0, max_history = 0, flags = 0;
   int threads = 32;  // threads per block of the solver kernels
   std::vector<pbad_model*> models;
-  std::vector<int64_t> inst_off, dof_off, lanes;
+  std::vector<int64_t> inst_off, dof_off, lanes, lane_doubles;
   std::vector<size_t> ws_off;  // in doubles
   int64_t n_inst = 0, D = 0;
   double* d_ws = nullptr;
@@ -269,7 +269,7 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.inst_off = bt->inst_off[k];
     B.dof_off = bt->dof_off[k];
     B.ws = bt->d_ws + bt->ws_off[k];
-    B.ws_stride = bt->lanes[k];
+    B.ws_lane = bt->lane_doubles[k];
     B.block_begin = blocks;
     B.solver = solvers ? solvers[k] : PBAD_LBFGS;
     B.chain = m->chain;
@@ -506,6 +506,7 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
     WsLayout L;
     L.make(m->N, m->n, max_history, (flags & PBAD_BATCH_NEWTON) ? max_stages : 0);
     bt->lanes.push_back(lanes);
+    bt->lane_doubles.push_back(L.total);
     bt->ws_off.push_back(ws);
     ws += (size_t)lanes * L.total;
   }
@@ -727,7 +728,7 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   B.rest = m->d_rest;
   for (int c = 0; c < 3; ++c) B.g[c] = m->g[c];
   B.ws = ws;
-  B.ws_stride = *lanes;
+  B.ws_lane = L.total;
   B.block_begin = 0;
   B.chain = m->chain;
   *grid = (int)blocks;

@@ -17,8 +17,9 @@ namespace pbad {
 constexpr int kMaxStages = 5;
 constexpr int kMaxHistory = 16;
 
-// Per-lane array in a lane-interleaved workspace: element k of lane L lives at
-// base[k * stride + L], so that the lanes of a warp touch consecutive words.
+// Per-lane array in a warp-blocked workspace: element k of lane l of warp w
+// lives at base[(w * per_lane + k) * 32 + l], so that the lanes of a warp
+// touch consecutive words and each warp's working set is contiguous.
 struct Lane {
   double* p;
   int64_t st;
@@ -39,7 +40,7 @@ struct Bucket {
   int64_t inst_off;      // first instance of the bucket in the batch
   int64_t dof_off;       // offset of the bucket's block in DOF-packed arrays
   double* ws;            // lane workspace
-  int64_t ws_stride;     // lanes in the workspace (>= groups * S)
+  int64_t ws_lane;       // doubles per lane in the workspace (its layout's total)
   int block_begin;       // first block of the launch that serves this bucket
   int solver;            // 0 L-BFGS, 1 Newton
   int chain;             // 1 if parent[l] == l - 1 for every link (serial chain)

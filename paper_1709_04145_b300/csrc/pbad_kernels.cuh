@@ -124,8 +124,8 @@ struct Ctx {
     N = B.N;
     n = B.n;
     L.make(N, n, m, Sd);
-    ws.p = B.ws + lane_id;
-    ws.st = B.ws_stride;
+    ws.p = B.ws + ((lane_id >> 5) * B.ws_lane) * 32 + (lane_id & 31);
+    ws.st = 32;
     i = grp.stage;
   }
 
