@@ -79,6 +79,15 @@ def parse():
     p.add_argument("--throughput-instances", type=int, default=65536,
                    help="instances of the large-batch throughput point (0 = skip)")
     p.add_argument("--throughput-timesteps", type=int, default=20)
+    p.add_argument("--uneven-steps", type=int, default=4,
+                   help="steps of the uneven three-bucket batch (0 = skip)")
+    p.add_argument("--max-iter-uneven", type=int, default=100)
+    p.add_argument("--scaling-steps", type=int, default=1,
+                   help="steps per rollout of the hinge-chain scaling study (0 = skip)")
+    p.add_argument("--scaling-links", type=int, nargs="+", default=[25, 50, 100, 200])
+    p.add_argument("--max-iter-scaling", type=int, default=3,
+                   help="iteration cap per step of the scaling study (a fixed budget: the study "
+                        "compares the cost per iteration of the two solvers)")
     p.add_argument("--adjoint-steps", type=int, default=8,
                    help="steps of the differentiable humanoid rollout timed forward and forward+adjoint "
                         "(0 = skip; the workload defines 64)")
@@ -348,6 +357,119 @@ def measure_adjoint(P, args, dev):
             "note": f"{steps} of the workload's 64 steps timed"}
 
 
+def _state_tensors(P, spec_states, S, dt, dev):
+    """DOF-packed (q_prev0, q_cur0) device tensors of several buckets."""
+    import numpy as np
+    import torch
+    nodes, _ = P.colloc(S)
+    qc = np.concatenate([q0.reshape(-1) for q0, _ in spec_states])
+    qp = np.concatenate([(q0 + nodes[0] * dt * qd0).reshape(-1) for q0, qd0 in spec_states])
+    return torch.tensor(qp, device=dev), torch.tensor(qc, device=dev)
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), r
+
+
+def measure_uneven(P, args, dev):
+    """Uneven batch in one persistent launch: 1024 humanoid trees (Newton),
+    1024 chains of 50 hinge rods and 2048 chains of 5 (L-BFGS m = 8), dt =
+    0.05, two stages, torques N(0, 0.1^2). Threads per block autotuned over
+    32/64/128 on one step; then one rollout of args.uneven_steps steps."""
+    import numpy as np
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    T = args.uneven_steps
+    u = I.uneven_batch(n_steps=T)
+    S, dt, m = u["stages"], u["dt"], u["history"]
+    batch = P.Batch([P.Model.from_spec(s, device=dev.index) for s in u["specs"]], max_stages=S,
+                    max_history=m, newton=True)
+    qp, qc = _state_tensors(P, u["states"], S, dt, dev)
+    tau = torch.tensor(np.concatenate([t.reshape(T, -1) for t in u["taus"]], axis=1), device=dev)
+    solvers = [P.NEWTON if sv == "newton" else P.LBFGS for sv in u["solvers"]]
+    run = lambda steps: P.rollout(batch, qp, qc, tau[:steps].reshape(-1).contiguous(), steps, dt, S,
+                                  solvers, m, u["tol"], args.max_iter_uneven, want_traj=False)
+    tuned = {}
+    for threads in (32, 64, 128):
+        batch.set_threads(threads)
+        tuned[threads] = _timed(lambda: run(1))[0]
+    best = min(tuned, key=tuned.get)
+    batch.set_threads(best)
+    ms, out = _timed(lambda: run(T))
+    st = out["status"].cpu().numpy()
+    it = out["iters"].cpu().numpy()
+    evl = out["evals"].cpu().numpy()
+    buckets = []
+    link_steps = 0
+    for k, spec in enumerate(u["specs"]):
+        a, b = int(batch.inst_off[k]), int(batch.inst_off[k + 1])
+        link_steps += spec.count * spec.n_links * T
+        buckets.append({"model": spec.name, "instances": spec.count, "links": spec.n_links,
+                        "dofs": spec.n_dof, "solver": u["solvers"][k],
+                        "converged_fraction": float((st[a:b] == 0).mean()),
+                        "iters_per_step": float(it[a:b].mean() / T),
+                        "evals_per_step": float(evl[a:b].mean() / T)})
+    return {"value": link_steps / (ms / 1e3), "unit": UNIT, "ms": ms, "timesteps": T,
+            "launches": 1, "threads_per_block": best,
+            "autotune_ms_per_step": {str(k): v for k, v in tuned.items()},
+            "max_iter_per_step": args.max_iter_uneven, "tol": u["tol"], "buckets": buckets}
+
+
+def measure_scaling(P, args, dev):
+    """Scaling study: serial hinge-rod chains of N links, batch 256, dt = 0.1,
+    four stages; L-BFGS (m = 8) and Newton on the same inputs; a forward
+    rollout and a forward + adjoint pass (end-state loss) of
+    args.scaling_steps steps each."""
+    import numpy as np
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    from paper_1709_04145_b300.autograd import rollout_differentiable
+    T = args.scaling_steps
+    rows = []
+    for N in args.scaling_links:
+        w = I.scaling_chains(N, n_steps=T)
+        spec = w["spec"]
+        S, dt, m = w["stages"], w["dt"], w["history"]
+        batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=S, max_history=m,
+                        newton=True)
+        qp, qc = _state_tensors(P, [(w["q0"], w["qd0"])], S, dt, dev)
+        x0 = torch.tensor(w["q0"].reshape(-1), device=dev)
+        v0 = torch.tensor(w["qd0"].reshape(-1), device=dev)
+        tau = torch.zeros((T, batch.D), dtype=torch.float64, device=dev)
+        for name, sv in (("lbfgs", P.LBFGS), ("newton", P.NEWTON)):
+            ms, out = _timed(lambda: P.rollout(batch, qp, qc, None, T, dt, S, sv, m, w["tol"],
+                                               args.max_iter_scaling, want_traj=False))
+            st = out["status"].cpu().numpy()
+
+            def fwd_adj():
+                xg = x0.clone().requires_grad_()
+                vg = v0.clone().requires_grad_()
+                tg = tau.clone().requires_grad_()
+                qe, _, _ = rollout_differentiable(batch, xg, vg, tg, dt, S, solver=sv, history=m,
+                                                  tol=w["tol"], max_iter=args.max_iter_scaling,
+                                                  checkpoint_every=8)
+                (qe ** 2).sum().backward()
+                return tg.grad
+            ms_fa, _ = _timed(fwd_adj)
+            its = float(out["iters"].float().mean().item() / T)
+            rows.append({"links": N, "solver": name, "instances": spec.count, "timesteps": T,
+                         "fwd_ms": ms, "fwd_adjoint_ms": ms_fa,
+                         "fwd_ms_per_iteration": ms / max(its * T, 1e-9),
+                         "fwd_link_steps_per_s": spec.count * N * T / (ms / 1e3),
+                         "converged_fraction": float((st == 0).mean()),
+                         "iters_per_step": its})
+        del batch
+        torch.cuda.empty_cache()
+    return {"rows": rows, "dt": 0.1, "stages": 4, "max_iter_per_step": args.max_iter_scaling}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -509,6 +631,10 @@ def run_ours(args):
         line["throughput_point"] = tp
     if rank == 0 and args.adjoint_steps > 0:
         line["fwd_adjoint"] = measure_adjoint(P, args, dev)
+    if rank == 0 and args.uneven_steps > 0:
+        line["uneven_batch"] = measure_uneven(P, args, dev)
+    if rank == 0 and args.scaling_steps > 0:
+        line["scaling_study"] = measure_scaling(P, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(w, n_inst=min(os.cpu_count() or 1, 16), n_steps=1,
                                               budget_s=args.cpu_sample_seconds)

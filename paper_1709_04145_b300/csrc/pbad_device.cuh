@@ -21,9 +21,9 @@ constexpr int kMaxHistory = 16;
 // lives at base[(w * per_lane + k) * 32 + l], so that the lanes of a warp
 // touch consecutive words and each warp's working set is contiguous.
 struct Lane {
+  static constexpr int kStride = 32;  // lanes per warp block
   double* p;
-  int64_t st;
-  __device__ __forceinline__ double& operator[](int64_t k) const { return p[k * st]; }
+  __device__ __forceinline__ double& operator[](int64_t k) const { return p[k * kStride]; }
 };
 
 // One bucket of instances that share a topology (a "model").
@@ -286,19 +286,23 @@ struct Group {
     base = lane - stage;
     mask = (S == 32) ? 0xffffffffu : (((1u << S) - 1u) << base);
   }
+  // Source lane of stage j. The lanes past the last full group of a warp
+  // (32 % S of them) form a short group; their sources are clamped to lane
+  // 31 so that every shuffle reads a lane inside the caller's mask.
+  __device__ __forceinline__ int src(int j) const { return min(base + j, 31); }
   // value of lane base+j (all lanes of the warp must call with full mask)
   __device__ __forceinline__ double from_full(double v, int j) const {
-    return __shfl_sync(0xffffffffu, v, base + j);
+    return __shfl_sync(0xffffffffu, v, src(j));
   }
   __device__ __forceinline__ double from(double v, int j) const {
-    return __shfl_sync(mask, v, base + j);
+    return __shfl_sync(mask, v, src(j));
   }
   // group sum in a fixed order: identical bits on every lane of the group
   __device__ __forceinline__ double sum(double v) const {
     if (S == 1) return v;
     double s = 0.0;
 #pragma unroll
-    for (int j = 0; j < S; ++j) s += __shfl_sync(mask, v, base + j);
+    for (int j = 0; j < S; ++j) s += __shfl_sync(mask, v, src(j));
     return s;
   }
 };

@@ -44,7 +44,7 @@ __global__ void __launch_bounds__(128) k_eval(const __grid_constant__ LaunchArgs
     c.ws[c.L.qp + d] = A.q_prev0[c.gdof(d)];
     c.ws[c.L.qc + d] = A.q_cur0[c.gdof(d)];
   }
-  c.setup();
+  c.setup(true);
   for (int d = 0; d < c.n; ++d) c.ws[c.L.xt + d] = A.q_star[c.gstage(d)];
   const double E = c.evaluate(A.tau);
   if (active) {
@@ -59,9 +59,12 @@ __global__ void __launch_bounds__(128) k_eval(const __grid_constant__ LaunchArgs
 // ------------------------------------------------------------------------
 // Persistent L-BFGS rollout: every group of S lanes integrates one instance
 // for n_steps steps. Each loop trip evaluates E, r, dE/dq at every group's
-// current trial point (convergent), then each group advances its own state
-// machine (line search, history update, convergence, next step) - the
-// iteration-level scheduling of the paper's Fig. GPU, inside a warp.
+// current trial point, then advances every group's state machine (line
+// search, history update, convergence, next step) - the iteration-level
+// scheduling of the paper's Fig. GPU, inside a warp. The whole trip is
+// convergent: every vector sweep runs once per warp with per-group
+// predicates, so groups in different phases share one pass over the
+// workspace instead of taking turns through divergent branches.
 // ------------------------------------------------------------------------
 template <int S>
 __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B) {
@@ -74,6 +77,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
   const auto& L = c.L;
   const Lane& ws = c.ws;
   const int64_t D = A.D;
+  constexpr unsigned kAll = 0xffffffffu;
 
   for (int d = 0; d < n; ++d) {
     ws[L.qp + d] = A.q_prev0[c.gdof(d)];
@@ -83,161 +87,243 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
   int worst = kConverged, iters_total = 0, evals_total = 0;
   double E = 0.0, alpha = 1.0, gd = 0.0, gamma = 1.0;
   const int max_evals = 4 * A.max_iter + kLsMax;  // evaluations per step
-  c.setup();
+  c.setup(true);
   if (!active) phase = kDone;
 
-  auto finish = [&](int st) {
-    worst = max(worst, st);
-    step_evals = 0;
-    // new state: q_prev' = stage S-2 (or q_cur when S = 1), q_cur' = stage S-1
-    for (int d = 0; d < n; ++d) {
-      const double xs = c.grp.from(ws[L.x + d], S - 1);
-      const double xp = (S == 1) ? ws[L.qc + d] : c.grp.from(ws[L.x + d], S - 2);
-      ws[L.qp + d] = xp;
-      ws[L.qc + d] = xs;
-      if (c.i == 0) {
-        if (A.traj_cur) A.traj_cur[(int64_t)step * D + c.gdof(d)] = xs;
-        if (A.traj_prev) A.traj_prev[(int64_t)step * D + c.gdof(d)] = xp;
-      }
-    }
-    if (A.q_stages_out && step == A.n_steps - 1)
-      for (int d = 0; d < n; ++d) A.q_stages_out[c.gstage(d)] = ws[L.x + d];
-    ++step;
-    if (step >= A.n_steps) {
-      phase = kDone;
-    } else {
-      c.setup();
-      phase = kFirst;
-    }
-  };
-
-  auto start_iteration = [&]() {
-    // convergence / caps at the accepted point x
-    double rr = 0.0;
-    int bad = 0;
-    for (int d = 0; d < n; ++d) {
-      rr = fma(ws[L.r + d], ws[L.r + d], rr);
-      if (!isfinite(ws[L.g + d])) bad = 1;
-    }
-    rr = c.grp.sum(rr);
-    bad = (int)c.grp.sum((double)bad);
-    if (bad || !isfinite(E) || !isfinite(rr)) { finish(kNonFinite); return; }
-    if (sqrt(rr) < A.tol) { finish(kConverged); return; }
-    if (k >= A.max_iter || step_evals >= max_evals) { finish(kMaxIter); return; }
-    // two-loop recursion with H0 = gamma * P
-    double al[kMaxHistory];
-    for (int d = 0; d < n; ++d) ws[L.d + d] = -ws[L.g + d];
-    for (int t = 0; t < nh; ++t) {
-      const int j = (head - 1 - t + 2 * m) % m;
-      const double a = ws[L.rho + j] * c.gdot(L.sh + j * n, L.d);
-      al[j] = a;
-      for (int d = 0; d < n; ++d) ws[L.d + d] = fma(-a, ws[L.yh + j * n + d], ws[L.d + d]);
-    }
-    c.precond(L.d);
-    for (int d = 0; d < n; ++d) ws[L.d + d] *= gamma;
-    for (int t = nh - 1; t >= 0; --t) {
-      const int j = (head - 1 - t + 2 * m) % m;
-      const double bta = ws[L.rho + j] * c.gdot(L.yh + j * n, L.d);
-      for (int d = 0; d < n; ++d) ws[L.d + d] = fma(al[j] - bta, ws[L.sh + j * n + d], ws[L.d + d]);
-    }
-    gd = c.gdot(L.g, L.d);
-    if (!(gd < 0.0)) {
-      nh = 0;
-      gamma = 1.0;
-      for (int d = 0; d < n; ++d) ws[L.d + d] = -ws[L.g + d];
-      c.precond(L.d);
-      gd = c.gdot(L.g, L.d);
-    }
-    alpha = 1.0;
-    trials = 0;
-    for (int d = 0; d < n; ++d) ws[L.xt + d] = ws[L.x + d] + ws[L.d + d];
-    phase = kTrial;
-  };
-
-  while (__any_sync(0xffffffffu, phase != kDone)) {
+  while (__any_sync(kAll, phase != kDone)) {
     const double* tau = A.tau ? A.tau + (int64_t)min(step, A.n_steps - 1) * D : nullptr;
     const double Et = c.evaluate(tau);
-    if (phase == kDone) continue;
-    ++evals_total;
-    ++step_evals;
-    if (phase == kFirst) {
-      for (int d = 0; d < n; ++d) {
-        ws[L.x + d] = ws[L.xt + d];
-        ws[L.g + d] = ws[L.gt + d];
-        ws[L.r + d] = ws[L.rt + d];
-      }
-      E = Et;
-      k = 0;
-      nh = 0;
-      head = 0;
-      gamma = 1.0;
-      start_iteration();
-      continue;
+    const bool live = phase != kDone;
+    if (live) {
+      ++evals_total;
+      ++step_evals;
     }
-    // line-search trial at xt = x + alpha d
-    int ok = 0;
-    {
-      double fin = 1.0;
-      for (int d = 0; d < n; ++d)
-        if (!isfinite(ws[L.gt + d])) fin = 0.0;
+    const bool first = live && phase == kFirst;
+    const bool trial = live && phase == kTrial;
+
+    // (1) line-search test at xt = x + alpha d: Armijo or approximate Wolfe
+    bool ok = false;
+    if (__any_sync(kAll, trial)) {
+      double gtd = 0.0, fin = 1.0;
+      if (trial)
+        for (int d0 = 0; d0 < n; d0 += Ctx<S>::kChunk) {
+          double gv[Ctx<S>::kChunk], dv[Ctx<S>::kChunk];
+#pragma unroll
+          for (int k = 0; k < Ctx<S>::kChunk; ++k)
+            if (d0 + k < n) {
+              gv[k] = ws[L.gt + d0 + k];
+              dv[k] = ws[L.d + d0 + k];
+            }
+#pragma unroll
+          for (int k = 0; k < Ctx<S>::kChunk; ++k)
+            if (d0 + k < n) {
+              if (!isfinite(gv[k])) fin = 0.0;
+              gtd = fma(gv[k], dv[k], gtd);
+            }
+        }
       fin = c.grp.sum(fin);
-      if (fin == (double)S && isfinite(Et)) {
-        const double gtd = c.gdot(L.gt, L.d);
+      gtd = c.grp.sum(gtd);
+      if (trial && fin == (double)S && isfinite(Et)) {
         const bool armijo = Et <= E + kLsC1 * alpha * gd;
         const bool approx = (Et <= E + kLsEps * fabs(E)) && (gtd <= (1.0 - 2.0 * kLsDelta) * fabs(gd));
         ok = armijo || approx;
       }
     }
-    if (!ok) {
-      if (step_evals >= max_evals) {
-        finish(kMaxIter);
-        continue;
-      }
-      if (++trials >= kLsMax) {
-        finish(kLsFail);
-        continue;
-      }
-      alpha *= 0.5;
-      for (int d = 0; d < n; ++d) ws[L.xt + d] = fma(alpha, ws[L.d + d], ws[L.x + d]);
-      continue;
+    int fin_st = -1;  // status of a step that ends on this trip
+    if (trial && !ok) {
+      if (step_evals >= max_evals) fin_st = kMaxIter;
+      else if (++trials >= kLsMax) fin_st = kLsFail;
+      else alpha *= 0.5;
     }
-    // accepted: curvature pair into the ring buffer
-    {
-      double sy = 0, ss = 0, yy = 0;
-      for (int d = 0; d < n; ++d) {
-        const double s_ = ws[L.xt + d] - ws[L.x + d], y_ = ws[L.gt + d] - ws[L.g + d];
-        sy = fma(s_, y_, sy);
-        ss = fma(s_, s_, ss);
-        yy = fma(y_, y_, yy);
-        ws[L.d + d] = y_;             // d is dead after acceptance: reuse for P y
+    const bool back = trial && !ok && fin_st < 0;  // next trial along the same d
+    const bool acc = first || ok;                  // xt becomes the current point
+
+    // (2) one sweep: accepted groups take (xt, gt, rt) and form the curvature
+    // pair s = xt - x, y = gt - g (s into rt, y into gt and d, all dead now);
+    // backtracking groups move xt.
+    double sy = 0.0, ss = 0.0, yy = 0.0, rr = 0.0, badg = 0.0;
+    if (__any_sync(kAll, acc || back)) {
+      if (acc) {
+        constexpr int kC = Ctx<S>::kChunk;
+        for (int d0 = 0; d0 < n; d0 += kC) {
+          double xv[kC], gv[kC], rv[kC], xo[kC], go[kC];
+#pragma unroll
+          for (int k = 0; k < kC; ++k)
+            if (d0 + k < n) {
+              xv[k] = ws[L.xt + d0 + k];
+              gv[k] = ws[L.gt + d0 + k];
+              rv[k] = ws[L.rt + d0 + k];
+              xo[k] = ok ? ws[L.x + d0 + k] : 0.0;
+              go[k] = ok ? ws[L.g + d0 + k] : 0.0;
+            }
+#pragma unroll
+          for (int k = 0; k < kC; ++k)
+            if (d0 + k < n) {
+              const int d = d0 + k;
+              if (ok) {
+                const double s_ = xv[k] - xo[k], y_ = gv[k] - go[k];
+                sy = fma(s_, y_, sy);
+                ss = fma(s_, s_, ss);
+                yy = fma(y_, y_, yy);
+                ws[L.rt + d] = s_;
+                ws[L.gt + d] = y_;
+                ws[L.d + d] = y_;
+              }
+              ws[L.x + d] = xv[k];
+              ws[L.g + d] = gv[k];
+              ws[L.r + d] = rv[k];
+              rr = fma(rv[k], rv[k], rr);
+              if (!isfinite(gv[k])) badg = 1.0;
+            }
+        }
+      } else if (back) {
+        c.vlin(L.xt, alpha, L.d, L.x);
       }
       sy = c.grp.sum(sy);
       ss = c.grp.sum(ss);
       yy = c.grp.sum(yy);
-      if (m > 0 && sy > kCurvEps * sqrt(ss) * sqrt(yy)) {
-        c.precond(L.d);
-        double yPy = 0;
-        for (int d = 0; d < n; ++d) yPy = fma(ws[L.gt + d] - ws[L.g + d], ws[L.d + d], yPy);
-        yPy = c.grp.sum(yPy);
-        for (int d = 0; d < n; ++d) {
-          ws[L.sh + head * n + d] = ws[L.xt + d] - ws[L.x + d];
-          ws[L.yh + head * n + d] = ws[L.gt + d] - ws[L.g + d];
+      rr = c.grp.sum(rr);
+      badg = c.grp.sum(badg);
+    }
+
+    // (3) curvature pair into the ring buffer: rho = 1/s^T y, gamma = s^T y / y^T P y
+    const bool pair = ok && m > 0 && sy > kCurvEps * sqrt(ss) * sqrt(yy);
+    if (__any_sync(kAll, pair)) {
+      c.precond(pair ? L.d : L.gt);  // gt is dead for every other group
+      double yPy = 0.0;
+      if (pair) {
+        constexpr int kC = Ctx<S>::kChunk;
+        for (int d0 = 0; d0 < n; d0 += kC) {
+          double yv[kC], pv[kC], sv[kC];
+#pragma unroll
+          for (int k = 0; k < kC; ++k)
+            if (d0 + k < n) {
+              yv[k] = ws[L.gt + d0 + k];
+              pv[k] = ws[L.d + d0 + k];
+              sv[k] = ws[L.rt + d0 + k];
+            }
+#pragma unroll
+          for (int k = 0; k < kC; ++k)
+            if (d0 + k < n) {
+              yPy = fma(yv[k], pv[k], yPy);
+              ws[L.sh + head * n + d0 + k] = sv[k];
+              ws[L.yh + head * n + d0 + k] = yv[k];
+            }
         }
+      }
+      yPy = c.grp.sum(yPy);
+      if (pair) {
         ws[L.rho + head] = 1.0 / sy;
         head = (head + 1) % m;
         if (nh < m) ++nh;
         gamma = sy / yPy;
       }
     }
-    for (int d = 0; d < n; ++d) {
-      ws[L.x + d] = ws[L.xt + d];
-      ws[L.g + d] = ws[L.gt + d];
-      ws[L.r + d] = ws[L.rt + d];
+
+    // (4) tests at the new current point
+    bool start = false;
+    if (acc) {
+      E = Et;
+      if (first) {
+        k = 0;
+        nh = 0;
+        head = 0;
+        gamma = 1.0;
+      } else {
+        ++k;
+        ++iters_total;
+      }
+      if (badg != 0.0 || !isfinite(E) || !isfinite(rr)) fin_st = kNonFinite;
+      else if (sqrt(rr) < A.tol) fin_st = kConverged;
+      else if (k >= A.max_iter || step_evals >= max_evals) fin_st = kMaxIter;
+      else start = true;
     }
-    E = Et;
-    ++k;
-    ++iters_total;
-    start_iteration();
+
+    // (5) steps that end: q_prev' = stage S-2 (q_cur when S = 1), q_cur' =
+    // stage S-1, trajectory, then the next step's setup for every group
+    // that goes on
+    const bool fin = fin_st >= 0;
+    if (__any_sync(kAll, fin)) {
+      if (fin) {
+        worst = max(worst, fin_st);
+        step_evals = 0;
+      }
+      for (int d = 0; d < n; ++d) {
+        const double xv = ws[L.x + d];
+        const double xs = c.grp.from(xv, S - 1);
+        const double xp = (S == 1) ? ws[L.qc + d] : c.grp.from(xv, S - 2);
+        if (fin) {
+          ws[L.qp + d] = xp;
+          ws[L.qc + d] = xs;
+          if (c.i == 0) {
+            if (A.traj_cur) A.traj_cur[(int64_t)step * D + c.gdof(d)] = xs;
+            if (A.traj_prev) A.traj_prev[(int64_t)step * D + c.gdof(d)] = xp;
+          }
+          if (A.q_stages_out && step == A.n_steps - 1) A.q_stages_out[c.gstage(d)] = xv;
+        }
+      }
+      bool next = false;
+      if (fin) {
+        ++step;
+        next = step < A.n_steps;
+        phase = next ? kFirst : kDone;
+      }
+      if (__any_sync(kAll, next)) c.setup(next);
+    }
+
+    // (6) two-loop recursion with H0 = gamma P for the groups that start an
+    // iteration; a non-descent direction falls back to -P g. Each sweep
+    // applies one update and forms the next step's dot product.
+    if (__any_sync(kAll, start)) {
+      const int nh_w = __reduce_max_sync(kAll, start ? nh : 0);
+      double gd0;
+      if (start) c.vlin(L.d, -1.0, L.g, -1);
+      auto slot = [&](int t) { return (head - 1 - t + 2 * m) % m; };
+      double al[kMaxHistory];
+      double a = 0.0;
+      if (nh_w > 0) a = ws[L.rho + slot(0)] * c.gdot(L.sh + slot(0) * n, L.d);
+      for (int t = 0; t < nh_w; ++t) {
+        const int j = slot(t);
+        al[t] = a;
+        const bool more = t + 1 < nh_w;
+        const int jn = more ? slot(t + 1) : 0;
+        const double dot = c.axpy_dot(L.d, -a, L.yh + j * n, more ? L.sh + jn * n : -1, start && t < nh);
+        if (more) a = ws[L.rho + jn] * dot;
+      }
+      c.precond(start ? L.d : L.gt);
+      if (start) c.vlin(L.d, gamma, L.d, -1);
+      if (nh_w > 0) {
+        double bta = ws[L.rho + slot(nh_w - 1)] * c.gdot(L.yh + slot(nh_w - 1) * n, L.d);
+        for (int t = nh_w - 1; t >= 0; --t) {
+          const int j = slot(t);
+          const int jn = t > 0 ? slot(t - 1) : 0;
+          const double dot = c.axpy_dot(L.d, al[t] - bta, L.sh + j * n, t > 0 ? L.yh + jn * n : L.g,
+                                        start && t < nh);
+          if (t > 0) bta = ws[L.rho + jn] * dot;
+          else gd0 = dot;
+        }
+      } else {
+        gd0 = c.gdot(L.g, L.d);
+      }
+      if (start) gd = gd0;
+      const bool reset = start && !(gd < 0.0);
+      if (__any_sync(kAll, reset)) {
+        if (reset) {
+          nh = 0;
+          gamma = 1.0;
+          c.vlin(L.d, -1.0, L.g, -1);
+        }
+        c.precond(reset ? L.d : L.gt);
+        const double gd1 = c.gdot(L.g, L.d);
+        if (reset) gd = gd1;
+      }
+      if (start) {
+        alpha = 1.0;
+        trials = 0;
+        c.vlin(L.xt, 1.0, L.d, L.x);
+        phase = kTrial;
+      }
+    }
   }
   if (active && c.i == 0) {
     if (A.status) A.status[B.inst_off + b] = worst;
@@ -306,7 +392,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
   int step = 0, phase = kFirst, k = 0, trials = 0;
   int worst = kConverged, iters_total = 0, evals_total = 0;
   double E = 0.0, lambda = -1.0, hmax = 0.0;
-  c.setup();
+  c.setup(true);
   if (!active) phase = kDone;  // warp-uniform
 
   auto gsum_bcast = [&](double v) {
@@ -334,7 +420,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     if (step >= A.n_steps) {
       phase = kDone;
     } else {
-      c.setup();
+      c.setup(true);
       phase = kFirst;
     }
   };
@@ -432,11 +518,15 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
 
 // One launch serves every bucket of the batch; each block runs the solver of
 // its bucket (L-BFGS or Newton), so an uneven batch with mixed solvers is a
-// single persistent launch.
-template <int S>
-__global__ void __launch_bounds__(128) k_rollout(const __grid_constant__ LaunchArgs A) {
+// single persistent launch. SOLVERS selects the variant: 0 every bucket
+// L-BFGS, 1 every bucket Newton, 2 mixed. The single-solver variants carry
+// only their own solver's code and registers.
+template <int S, int SOLVERS>
+__global__ void __maxnreg__(255) k_rollout(const __grid_constant__ LaunchArgs A) {
   const Bucket& B = A.bk[find_bucket(A)];
-  if (B.solver == 1) rollout_newton<S>(A, B);
+  if (SOLVERS == 0) rollout_lbfgs<S>(A, B);
+  else if (SOLVERS == 1) rollout_newton<S>(A, B);
+  else if (B.solver == 1) rollout_newton<S>(A, B);
   else rollout_lbfgs<S>(A, B);
 }
 
@@ -469,7 +559,7 @@ __global__ void __launch_bounds__(128) k_step_backward(const __grid_constant__ L
     ws[L.qp + d] = A.q_prev0[c.gdof(d)];
     ws[L.qc + d] = A.q_cur0[c.gdof(d)];
   }
-  c.setup();
+  c.setup(true);
   for (int d = 0; d < n; ++d) ws[L.xt + d] = A.q_star[c.gstage(d)];
   if (writer)
     for (int d = 0; d < n; ++d) Dn[DL.gb + c.i * n + d] = A.g_bar[c.gstage(d)];
@@ -582,7 +672,11 @@ cudaError_t PBAD_CAT(launch_backward_s, PBAD_S)(const LaunchArgs& A, int grid, c
   return cudaGetLastError();
 }
 cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
-  k_rollout<PBAD_S><<<grid, A.threads, 0, s>>>(A);
+  bool lbfgs = false, newton = false;
+  for (int k = 0; k < A.nb; ++k) (A.bk[k].solver == 1 ? newton : lbfgs) = true;
+  if (lbfgs && newton) k_rollout<PBAD_S, 2><<<grid, A.threads, 0, s>>>(A);
+  else if (newton) k_rollout<PBAD_S, 1><<<grid, A.threads, 0, s>>>(A);
+  else k_rollout<PBAD_S, 0><<<grid, A.threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 #if PBAD_S == 1

@@ -124,8 +124,7 @@ struct Ctx {
     N = B.N;
     n = B.n;
     L.make(N, n, m, Sd);
-    ws.p = B.ws + ((lane_id >> 5) * B.ws_lane) * 32 + (lane_id & 31);
-    ws.st = 32;
+    ws.p = B.ws + ((lane_id >> 5) * B.ws_lane) * Lane::kStride + (lane_id & 31);
     i = grp.stage;
   }
 
@@ -222,8 +221,10 @@ struct Ctx {
   // C_i,l = Wk[i][0] T_l(q_prev) + Wk[i][1] T_l(q_cur) for the own stage,
   // the preconditioner blocks at q_cur and the initial guess (linear
   // extrapolation through the two known nodes). q_prev/q_cur are read from
-  // the lane's workspace copies.
-  __device__ __noinline__ void setup() const {
+  // the lane's workspace copies. With commit = false the pass runs (so that a
+  // warp can run it convergently) but leaves C, the blocks and the guess of
+  // the lane untouched; T and G are scratch either way.
+  __device__ __noinline__ void setup(bool commit) const {
     double Tp[12], Tc[12], Jr[9], q3[3];
     // forward: FK at both known nodes; parents' transforms live in T (prev)
     // and G (cur) of the workspace during setup.
@@ -243,7 +244,7 @@ struct Ctx {
       double C[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) C[k] = fma(K.Wk[i][0], Tp[k], K.Wk[i][1] * Tc[k]);
-      store12(L.C + 12 * l, C);
+      if (commit) store12(L.C + 12 * l, C);
     }
     // composite world mass moments at q_cur: [Sigma_w(6) h(3) m] per link in
     // the T region (no longer needed)
@@ -334,14 +335,16 @@ struct Ctx {
           for (int k = 0; k < 9; ++k) Pj[k] = X[k];
         }
       }
-      for (int k = 0; k < nd * nd; ++k) ws[L.Pb + 9 * l + k] = Pj[k];
+      if (commit)
+        for (int k = 0; k < nd * nd; ++k) ws[L.Pb + 9 * l + k] = Pj[k];
     }
     // initial guess for the own stage
     const double sc = K.nodes[2 + i] / (0.0 - K.nodes[0]);
-    for (int d = 0; d < n; ++d) {
-      const double qc = ws[L.qc + d], qp = ws[L.qp + d];
-      ws[L.xt + d] = fma(sc, qc - qp, qc);
-    }
+    if (commit)
+      for (int d = 0; d < n; ++d) {
+        const double qc = ws[L.qc + d], qp = ws[L.qp + d];
+        ws[L.xt + d] = fma(sc, qc - qp, qc);
+      }
   }
 
   // --------------------------------------------------- residual (primal)
@@ -902,11 +905,73 @@ struct Ctx {
 
   // ------------------------------------------------- L-BFGS vector algebra
   // (group-divergent code: group-mask shuffles only)
+  // Vector sweeps over the own stage slice, kChunk DOFs at a time: a
+  // chunk's loads are issued together before any of its arithmetic, so a
+  // sweep waits for memory about n / kChunk times instead of n times. Sums
+  // accumulate in plain sequential order.
+  static constexpr int kChunk = 4;
+
+  // group sum of v[a..] . v[b..]
   __device__ double gdot(int a, int b_) const {
     double s = 0.0;
-    for (int d = 0; d < n; ++d) s = fma(ws[a + d], ws[b_ + d], s);
+    for (int d0 = 0; d0 < n; d0 += kChunk) {
+      double u[kChunk], v[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < n) {
+          u[k] = ws[a + d0 + k];
+          v[k] = ws[b_ + d0 + k];
+        }
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < n) s = fma(u[k], v[k], s);
+    }
     return grp.sum(s);
   }
+
+  // v[y..] <- ca v[a..] + v[b..] (b >= 0) or ca v[a..] (b < 0), chunked.
+  __device__ void vlin(int y, double ca, int a, int b_) const {
+    for (int d0 = 0; d0 < n; d0 += kChunk) {
+      double av[kChunk], bv[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < n) {
+          av[k] = ws[a + d0 + k];
+          bv[k] = b_ >= 0 ? ws[b_ + d0 + k] : 0.0;
+        }
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < n) ws[y + d0 + k] = b_ >= 0 ? fma(ca, av[k], bv[k]) : ca * av[k];
+    }
+  }
+
+  // v[y..] <- v[y..] + cf v[x..] when `on`, then the group sum of v[z..] .
+  // v[y..] (updated where on): one step of the two-loop recursion fused with
+  // the next step's dot product. z < 0 skips the dot product (returns 0).
+  __device__ double axpy_dot(int y, double cf, int x, int z, bool on) const {
+    double s = 0.0;
+    for (int d0 = 0; d0 < n; d0 += kChunk) {
+      double yv[kChunk], xv[kChunk], zv[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < n) {
+          yv[k] = ws[y + d0 + k];
+          xv[k] = ws[x + d0 + k];
+          zv[k] = z >= 0 ? ws[z + d0 + k] : 0.0;
+        }
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < n) {
+          if (on) {
+            yv[k] = fma(cf, xv[k], yv[k]);
+            ws[y + d0 + k] = yv[k];
+          }
+          s = fma(zv[k], yv[k], s);
+        }
+    }
+    return z >= 0 ? grp.sum(s) : 0.0;
+  }
+
   // v <- P v for the own slice of v at offset a (Kronecker: stage block Ps,
   // joint blocks Pb).
   __device__ __noinline__ void precond(int a) const {
