@@ -108,16 +108,24 @@ struct LaunchArgs {
 // ------------------------------------------------------------------------
 // per-lane context
 // ------------------------------------------------------------------------
+// The context is held by value: the hot passes below run on a private copy
+// (see primal / tangent_pass / setup / precond), so that its fields live in
+// registers instead of being reloaded from the caller's frame after every
+// workspace store (a generic store could alias it).
 template <int S>
 struct Ctx {
-  const Bucket& B;
+  Bucket B;           // copy of the bucket descriptor
   const Colloc& K;
   Group<S> grp;
   WsLayout L;
   Lane ws;
-  int b;       // instance within the bucket (always a valid index)
-  int i;       // own stage
+  int b;              // instance within the bucket (always a valid index)
+  int i;              // own stage
   int N, n;
+  double wk[2];       // K.Wk[i][*]: weights of the two known nodes for the own stage
+  double wu_row[S];   // K.Wu[i][*]
+  double wu_col[S];   // K.Wu[*][i]
+  double ps_row[S];   // K.Ps[i][*]
 
   __device__ Ctx(const Bucket& B_, const Colloc& K_, int b_, int64_t lane_id, int m, int Sd = 0)
       : B(B_), K(K_), b(b_) {
@@ -126,6 +134,14 @@ struct Ctx {
     L.make(N, n, m, Sd);
     ws.p = B.ws + ((lane_id >> 5) * B.ws_lane) * Lane::kStride + (lane_id & 31);
     i = grp.stage;
+    wk[0] = K.Wk[i][0];
+    wk[1] = K.Wk[i][1];
+#pragma unroll
+    for (int j = 0; j < S; ++j) {
+      wu_row[j] = K.Wu[i][j];
+      wu_col[j] = K.Wu[j][i];
+      ps_row[j] = K.Ps[i][j];
+    }
   }
 
   __device__ __forceinline__ double rest(int l, int k) const {
@@ -150,22 +166,6 @@ struct Ctx {
   __device__ __forceinline__ void store12(int off, const double* v) const {
 #pragma unroll
     for (int k = 0; k < 12; ++k) ws[off + k] = v[k];
-  }
-
-  // L1 prefetch hints for the next link's operands (issued one link ahead;
-  // only valid addresses are touched).
-  __device__ __forceinline__ void pf_g(const double* a) const {
-    asm volatile("prefetch.global.L1 [%0];" ::"l"(a));
-  }
-  __device__ __forceinline__ void pf_ws(int64_t k) const { pf_g(&ws[k]); }
-  __device__ __forceinline__ void prefetch_model(int l) const {
-#pragma unroll
-    for (int k = 0; k < 12; ++k) pf_g(&B.rest[((int64_t)l * 12 + k) * B.count + b]);
-#pragma unroll
-    for (int k = 0; k < 10; ++k) pf_g(&B.mm[((int64_t)l * 10 + k) * B.count + b]);
-  }
-  __device__ __forceinline__ void prefetch_ws(int off, int cnt) const {
-    for (int k = 0; k < cnt; ++k) pf_ws(off + k);
   }
 
   // T_l = T_parent * X_l * Rot(q_l). Ball joints also return Jr(q_l).
@@ -225,7 +225,11 @@ struct Ctx {
   // warp can run it convergently) but leaves C, the blocks and the guess of
   // the lane untouched; T and G are scratch either way.
   __device__ __noinline__ void setup(bool commit) const {
-    double Tp[12], Tc[12], Jr[9], q3[3];
+    const Ctx self(*this);
+    self.setup_body(commit);
+  }
+  __device__ __forceinline__ void setup_body(bool commit) const {
+    double Tp[12], Tc[12], Jr[9], q3[3] = {0.0, 0.0, 0.0};
     // forward: FK at both known nodes; parents' transforms live in T (prev)
     // and G (cur) of the workspace during setup.
     for (int l = 0; l < N; ++l) {
@@ -235,15 +239,19 @@ struct Ctx {
         load12(L.T + 12 * p, Pp);
         load12(L.G + 12 * p, Pc);
       }
-      for (int k = 0; k < nd; ++k) q3[k] = ws[L.qp + d0 + k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k < nd) q3[k] = ws[L.qp + d0 + k];
       link_fk(l, p >= 0 ? Pp : nullptr, q3, Tp, Jr);
-      for (int k = 0; k < nd; ++k) q3[k] = ws[L.qc + d0 + k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k < nd) q3[k] = ws[L.qc + d0 + k];
       link_fk(l, p >= 0 ? Pc : nullptr, q3, Tc, Jr);
       store12(L.T + 12 * l, Tp);
       store12(L.G + 12 * l, Tc);
       double C[12];
 #pragma unroll
-      for (int k = 0; k < 12; ++k) C[k] = fma(K.Wk[i][0], Tp[k], K.Wk[i][1] * Tc[k]);
+      for (int k = 0; k < 12; ++k) C[k] = fma(wk[0], Tp[k], wk[1] * Tc[k]);
       if (commit) store12(L.C + 12 * l, C);
     }
     // composite world mass moments at q_cur: [Sigma_w(6) h(3) m] per link in
@@ -283,7 +291,7 @@ struct Ctx {
     }
     // joint blocks B_j = W^T I_o W, I_o = tr(Sig_o) I - Sig_o about the joint
     for (int l = 0; l < N; ++l) {
-      double T[12], Jr[9], w[9], q[3];
+      double T[12], Jr[9], w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, q[3];
       load12(L.G + 12 * l, T);
       const int nd = ndof(l), d0 = B.dof[l];
       if (nd == 3) {
@@ -309,12 +317,16 @@ struct Ctx {
       for (int k = 0; k < 9; ++k) Io[k] = -So[k];
       Io[0] += tr; Io[4] += tr; Io[8] += tr;
       double Bj[9], Pj[9];
-      for (int a = 0; a < nd; ++a)
-        for (int bb = 0; bb < nd; ++bb) {
+#pragma unroll
+      for (int a = 0; a < 3; ++a)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb) {
           double s = 0;
+#pragma unroll
           for (int r = 0; r < 3; ++r)
+#pragma unroll
             for (int q_ = 0; q_ < 3; ++q_) s += w[3 * a + r] * Io[3 * r + q_] * w[3 * bb + q_];
-          Bj[nd * a + bb] = s;
+          Bj[3 * a + bb] = s;  // hinge: only Bj[0] is used (w[0..2] is its axis)
         }
       if (nd == 1) {
         Pj[0] = 1.0 / Bj[0];
@@ -335,8 +347,11 @@ struct Ctx {
           for (int k = 0; k < 9; ++k) Pj[k] = X[k];
         }
       }
-      if (commit)
-        for (int k = 0; k < nd * nd; ++k) ws[L.Pb + 9 * l + k] = Pj[k];
+      if (commit) {
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+          if (k < nd * nd) ws[L.Pb + 9 * l + k] = Pj[k];
+      }
     }
     // initial guess for the own stage
     const double sc = K.nodes[2 + i] / (0.0 - K.nodes[0]);
@@ -353,22 +368,21 @@ struct Ctx {
   // share of E (energy for S = 1, |r_i|^2 otherwise); the caller sums over
   // the group. Must be called convergently by the whole warp.
   __device__ __noinline__ double primal(const double* tau) const {
+    const Ctx self(*this);
+    return self.primal_body(tau);
+  }
+  __device__ __forceinline__ double primal_body(const double* tau) const {
     double Eown = 0.0;
     const double dt2 = K.dt * K.dt;
     const bool chain = B.chain;
     double Tp[12];  // parent transform (kept in registers along a chain)
-    prefetch_model(0);
-    prefetch_ws(L.C, 12);
     for (int l = 0; l < N; ++l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
-      if (l + 1 < N) {
-        prefetch_model(l + 1);
-        prefetch_ws(L.C + 12 * (l + 1), 12);
-        prefetch_ws(L.xt + B.dof[l + 1], ndof(l + 1));
-      }
-      double T[12], Jr[9], q3[3], w[9];
+      double T[12], Jr[9], q3[3] = {0.0, 0.0, 0.0}, w[9];
       if (p >= 0 && !chain) load12(L.T + 12 * p, Tp);
-      for (int k = 0; k < nd; ++k) q3[k] = ws[L.xt + d0 + k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k < nd) q3[k] = ws[L.xt + d0 + k];
       ExpCoef ec;
       link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr, nd == 3 ? &ec : nullptr);
       if (nd == 3) {  // cached for the tangent passes at this point
@@ -379,13 +393,15 @@ struct Ctx {
       }
       store12(L.T + 12 * l, T);
       link_axes(l, T, Jr, w);
-      for (int k = 0; k < 3 * nd; ++k) ws[L.axes + 9 * l + k] = w[k];
+#pragma unroll
+      for (int k = 0; k < 9; ++k)
+        if (k < 3 * nd) ws[L.axes + 9 * l + k] = w[k];
       // A = C_i + sum_j Wu[i][j] T_j (stage coupling of Eq. HOC)
       double A[12];
       load12(L.C + 12 * l, A);
 #pragma unroll
       for (int j = 0; j < S; ++j) {
-        const double wij = K.Wu[i][j];
+        const double wij = wu_row[j];
 #pragma unroll
         for (int k = 0; k < 12; ++k) A[k] = fma(wij, grp.from_full(T[k], j), A[k]);
       }
@@ -419,11 +435,6 @@ struct Ctx {
     double carry[6] = {0, 0, 0, 0, 0, 0};  // child subtree sum along a chain
     for (int l = N - 1; l >= 0; --l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
-      if (l > 0) {
-        prefetch_ws(L.acc + 6 * (l - 1), 6);
-        prefetch_ws(L.T + 12 * (l - 1), 12);
-        prefetch_ws(L.axes + 9 * (l - 1), 3 * ndof(l - 1));
-      }
       double a[6];
       for (int k = 0; k < 6; ++k) a[k] = ws[L.acc + 6 * l + k] + carry[k];
       const double o[3] = {ws[L.T + 12 * l + 3], ws[L.T + 12 * l + 7], ws[L.T + 12 * l + 11]};
@@ -464,18 +475,15 @@ struct Ctx {
   enum TangentMode { kGrad = 0, kJvp = 1, kGn = 2 };
   template <int MODE>
   __device__ __noinline__ void tangent_pass(int dir, int out, double scale) const {
+    const Ctx self(*this);
+    self.template tangent_body<MODE>(dir, out, scale);
+  }
+  template <int MODE>
+  __device__ __forceinline__ void tangent_body(int dir, int out, double scale) const {
     const bool chain = B.chain;
     double V[6] = {0, 0, 0, 0, 0, 0};  // parent twist (kept in registers along a chain)
     for (int l = 0; l < N; ++l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
-      if (l + 1 < N) {
-        prefetch_ws(L.T + 12 * (l + 1), 12);
-        prefetch_ws(L.G + 12 * (l + 1), 12);
-        prefetch_ws(L.axes + 9 * (l + 1), 3 * ndof(l + 1));
-        prefetch_ws(dir + B.dof[l + 1], ndof(l + 1));
-#pragma unroll
-        for (int k = 0; k < 10; ++k) pf_g(&B.mm[((int64_t)(l + 1) * 10 + k) * B.count + b]);
-      }
       if (!chain) {
         if (p >= 0) {
           for (int k = 0; k < 6; ++k) V[k] = ws[L.V + 6 * p + k];
@@ -517,7 +525,7 @@ struct Ctx {
       for (int k = 0; k < 12; ++k) Bs[k] = 0.0;
 #pragma unroll
       for (int j = 0; j < S; ++j) {
-        const double wgt = (MODE == kGrad) ? K.Wu[j][i] : K.Wu[i][j];
+        const double wgt = (MODE == kGrad) ? wu_col[j] : wu_row[j];
 #pragma unroll
         for (int k = 0; k < 12; ++k) Bs[k] = fma(wgt, grp.from_full(Td[k], j), Bs[k]);
       }
@@ -537,13 +545,6 @@ struct Ctx {
     double carry[6] = {0, 0, 0, 0, 0, 0};
     for (int l = N - 1; l >= 0; --l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
-      if (l > 0) {
-        prefetch_ws(L.accd + 6 * (l - 1), 6);
-        prefetch_ws(L.acc + 6 * (l - 1), 6);
-        prefetch_ws(L.V + 6 * (l - 1), 6);
-        prefetch_ws(L.T + 12 * (l - 1), 12);
-        prefetch_ws(L.axes + 9 * (l - 1), 3 * ndof(l - 1));
-      }
       double ad[6], T[12];
       for (int k = 0; k < 6; ++k) ad[k] = ws[L.accd + 6 * l + k] + carry[k];
       load12(L.T + 12 * l, T);
@@ -584,13 +585,16 @@ struct Ctx {
           for (int k = 0; k < 4; ++k) bh[k] = ws[L.ec + 4 * l + k];
           jr_tangent(th, v, bh, dJ);
         }
-        for (int k = 0; k < nd; ++k) {
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+          if (k >= nd) break;
           const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
                                ws[L.axes + 9 * l + 3 * k + 2]};
           double wd[3];
           cross(V, w, wd);
           if (nd == 3) {
             // + R dJr e_k
+#pragma unroll
             for (int r = 0; r < 3; ++r)
               wd[r] += fma(T[4 * r], dJ[k], fma(T[4 * r + 1], dJ[3 + k], T[4 * r + 2] * dJ[6 + k]));
           }
@@ -975,20 +979,30 @@ struct Ctx {
   // v <- P v for the own slice of v at offset a (Kronecker: stage block Ps,
   // joint blocks Pb).
   __device__ __noinline__ void precond(int a) const {
+    const Ctx self(*this);
+    self.precond_body(a);
+  }
+  __device__ __forceinline__ void precond_body(int a) const {
     for (int l = 0; l < N; ++l) {
       const int d0 = B.dof[l], nd = ndof(l);
-      double u[3], t[3];
-      for (int k = 0; k < nd; ++k) u[k] = ws[a + d0 + k];
-      for (int r = 0; r < nd; ++r) {
-        double s = 0.0;
-        for (int c = 0; c < nd; ++c) s = fma(ws[L.Pb + 9 * l + nd * r + c], u[c], s);
-        t[r] = s;
-      }
-      for (int k = 0; k < nd; ++k) {
+      double u[3] = {0.0, 0.0, 0.0}, t[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (k < nd) u[k] = ws[a + d0 + k];
+#pragma unroll
+      for (int r = 0; r < 3; ++r) {
         double s = 0.0;
 #pragma unroll
-        for (int j = 0; j < S; ++j) s = fma(K.Ps[i][j], grp.from(t[k], j), s);
-        ws[a + d0 + k] = s;
+        for (int c = 0; c < 3; ++c)
+          if (r < nd && c < nd) s = fma(ws[L.Pb + 9 * l + nd * r + c], u[c], s);
+        t[r] = s;
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < S; ++j) s = fma(ps_row[j], grp.from(t[k], j), s);
+        if (k < nd) ws[a + d0 + k] = s;
       }
     }
   }
