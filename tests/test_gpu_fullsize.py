@@ -1,0 +1,177 @@
+"""CUDA path vs the oracle at the workloads' full sizes, in the launch
+configuration the bench times (one launch over the whole batch, 32-thread
+blocks): sampled instances are checked against the oracle one by one, and
+properties that hold for every instance are checked on all of them."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1709_04145_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+REL_EVAL = 1e-10
+
+
+def _relerr(a, b):
+    a = np.asarray(a, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    return np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300)
+
+
+def _samples(count, k, seed):
+    rng = np.random.default_rng(seed)
+    idx = {0, count - 1} | set(rng.choice(count, size=min(k, count), replace=False).tolist())
+    return sorted(idx)
+
+
+def _guess(q_prev, q_cur, S, rng, noise):
+    """Stage configurations near the step's initial guess (linear
+    extrapolation through the known nodes), (count, S, n)."""
+    nodes, _ = O.colloc(S)
+    st = [q_cur + (nodes[2 + i] / (0.0 - nodes[0])) * (q_cur - q_prev) for i in range(S)]
+    qs = np.stack(st, axis=1)
+    return qs + rng.normal(0.0, noise, size=qs.shape)
+
+
+def _check_eval(P, batch, specs, cases, S, dt, per_bucket, seed):
+    import torch
+    dev = torch.device("cuda:0")
+    cat = lambda j: torch.tensor(np.concatenate([c[j].reshape(-1) for c in cases]), device=dev)
+    q_prev, q_cur, tau, qs = cat(0), cat(1), cat(2), cat(3)
+    E, grad, resid = P.eval_objective_grad(batch, qs, q_prev, q_cur, tau, dt, S)
+    torch.cuda.synchronize()
+    E = E.cpu().numpy()
+    assert np.isfinite(E).all()
+    grads = batch.unpack(grad.cpu().numpy(), S)
+    resids = batch.unpack(resid.cpu().numpy(), S)
+    for k, spec in enumerate(specs):
+        qp, qc, ta, q_s = cases[k]
+        for b in _samples(spec.count, per_bucket, seed + k):
+            om = O.OracleModel.from_spec(spec, b)
+            Eo, ro, go, _ = om.eval(S, dt, q_s[b], qp[b], qc[b], ta[b], True)
+            assert abs(E[batch.inst_off[k] + b] - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (spec.name, b)
+            assert _relerr(resids[k][b].reshape(-1), ro) < REL_EVAL, (spec.name, b)
+            assert _relerr(grads[k][b].reshape(-1), go) < REL_EVAL, (spec.name, b)
+
+
+def test_ball_chains_4096_eval_and_first_step():
+    """4096 ten-link ball chains, three stages, dt = 0.033: evaluation
+    parity on sampled instances; one L-BFGS step (3 iterations) on the whole
+    batch: the objective never increases on any instance, and sampled
+    instances follow the oracle's iterations."""
+    import torch
+    import paper_1709_04145_b300 as P
+    w = I.ball_chains()
+    spec, S, dt, m = w["spec"], w["stages"], w["dt"], w["history"]
+    nodes, _ = O.colloc(S)
+    q_cur = w["q0"]
+    q_prev = w["q0"] + nodes[0] * dt * w["qd0"]
+    tau = np.zeros_like(q_cur)
+    rng = np.random.default_rng(7)
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=m)
+    batch.set_threads(32)
+    qs = _guess(q_prev, q_cur, S, rng, 0.01)
+    _check_eval(P, batch, [spec], [(q_prev, q_cur, tau, qs)], S, dt, 12, 70)
+
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    max_iter = 3
+    out = P.step(batch, t(q_prev), t(q_cur), None, dt, S, P.LBFGS, m, w["tol"], max_iter)
+    qs_gpu = out["q_stages"]
+    st = out["status"].cpu().numpy()
+    assert np.isin(st, [0, 1, 2]).all()
+    x0 = t(_guess(q_prev, q_cur, S, rng, 0.0))
+    E0, _, _ = P.eval_objective_grad(batch, x0, t(q_prev), t(q_cur), None, dt, S)
+    E1, _, _ = P.eval_objective_grad(batch, qs_gpu, t(q_prev), t(q_cur), None, dt, S)
+    E0, E1 = E0.cpu().numpy(), E1.cpu().numpy()
+    assert (E1 <= E0 * (1 + 1e-11)).all()  # approximate Wolfe admits 1e-12 |E| per iteration
+    qs_h = qs_gpu.cpu().numpy().reshape(spec.count, S, spec.n_dof)
+    agree = 0
+    sample = _samples(spec.count, 10, 71)
+    for b in sample:
+        om = O.OracleModel.from_spec(spec, b)
+        q_o, st_o, _, _ = om.step(S, dt, q_prev[b], q_cur[b], tau[b], "lbfgs", m, w["tol"], max_iter)
+        if st_o == st[b] and np.max(np.abs(q_o - qs_h[b])) <= 1e-8:
+            agree += 1
+    # three line-searched iterations: a decision at the rounding level may
+    # flip on an instance, not on most
+    assert agree >= len(sample) - 2, (agree, len(sample))
+
+
+def test_uneven_batch_full_eval():
+    """1024 humanoids, 1024 chains of 50 hinge rods and 2048 chains of 5 in
+    one batch, two stages, dt = 0.05, per-step torques: evaluation parity on
+    sampled instances of every bucket."""
+    import paper_1709_04145_b300 as P
+    u = I.uneven_batch(n_steps=1)
+    S, dt = u["stages"], u["dt"]
+    nodes, _ = O.colloc(S)
+    rng = np.random.default_rng(8)
+    cases = []
+    for k, spec in enumerate(u["specs"]):
+        q0, qd0 = u["states"][k]
+        q_prev = q0 + nodes[0] * dt * qd0
+        cases.append((q_prev, q0, u["taus"][k][0], _guess(q_prev, q0, S, rng, 0.01)))
+    batch = P.Batch([P.Model.from_spec(s) for s in u["specs"]], max_stages=S, max_history=8,
+                    newton=True)
+    batch.set_threads(32)
+    _check_eval(P, batch, u["specs"], cases, S, dt, 6, 80)
+
+
+def test_humanoids_1024_step_backward():
+    """1024 humanoids, two stages, dt = 0.033: a Newton step on the whole
+    batch, then the implicit-function adjoint; sampled converged instances
+    against the oracle's dense adjoint."""
+    import torch
+    import paper_1709_04145_b300 as P
+    w = I.humanoid_adjoint(n_steps=1)
+    spec, S, dt = w["spec"], w["stages"], w["dt"]
+    nodes, _ = O.colloc(S)
+    q_cur = w["q0"]
+    q_prev = w["q0"] + nodes[0] * dt * w["qd0"]
+    tau = w["tau"][0]
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    out = P.step(batch, t(q_prev), t(q_cur), t(tau), dt, S, P.NEWTON, 8, 1e-9, 100)
+    st = out["status"].cpu().numpy()
+    assert (st == 0).mean() > 0.5
+    rng = np.random.default_rng(9)
+    gbar = rng.normal(size=S * batch.D)
+    gp, gc, gt, bst = P.step_backward(batch, t(q_prev), t(q_cur), t(tau), out["q_stages"],
+                                      t(gbar), dt, S)
+    torch.cuda.synchronize()
+    qs_h = out["q_stages"].cpu().numpy()
+    gp, gc, gt, bst = gp.cpu().numpy(), gc.cpu().numpy(), gt.cpu().numpy(), bst.cpu().numpy()
+    n = spec.n_dof
+    checked = 0
+    for b in _samples(spec.count, 12, 90):
+        if st[b] != 0:
+            continue
+        assert bst[b] == 0
+        om = O.OracleModel.from_spec(spec, b)
+        sl, ssl = slice(b * n, (b + 1) * n), slice(S * b * n, S * (b + 1) * n)
+        rp, rc, rt = om.step_adjoint(S, dt, q_prev[b], q_cur[b], tau[b], qs_h[ssl], gbar[ssl])
+        assert _relerr(gp[sl], rp) < 1e-7, b
+        assert _relerr(gc[sl], rc) < 1e-7, b
+        assert _relerr(gt[sl], rt) < 1e-7, b
+        checked += 1
+    assert checked >= 4
+
+
+@pytest.mark.parametrize("n_links", [25, 200])
+def test_scaling_chains_eval(n_links):
+    """Hinge-rod chains of 25 and 200 links, batch 256, four stages, dt =
+    0.1: evaluation parity on sampled instances."""
+    import paper_1709_04145_b300 as P
+    w = I.scaling_chains(n_links, n_steps=1)
+    spec, S, dt = w["spec"], w["stages"], w["dt"]
+    nodes, _ = O.colloc(S)
+    q_prev = w["q0"] + nodes[0] * dt * w["qd0"]
+    rng = np.random.default_rng(10)
+    case = (q_prev, w["q0"], rng.normal(0, 0.1, size=w["q0"].shape),
+            _guess(q_prev, w["q0"], S, rng, 0.01))
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8)
+    batch.set_threads(32)
+    _check_eval(P, batch, [spec], [case], S, dt, 4, 100 + n_links)
