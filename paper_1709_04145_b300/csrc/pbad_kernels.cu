@@ -73,15 +73,19 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
   const int b = active ? (int)id.inst : 0;
   const int m = A.history;
   Ctx<S> c(B, A.K, b, id.lane_id, m);
+  // c goes to the non-inlined passes; cv, a private copy used by the inline
+  // helpers only, keeps the layout and lane fields in registers across the
+  // workspace stores of the solver bookkeeping.
+  const Ctx<S> cv(c);
   const int n = c.n;
-  const auto& L = c.L;
-  const Lane& ws = c.ws;
+  const WsLayout L = c.L;
+  const Lane ws = c.ws;
   const int64_t D = A.D;
   constexpr unsigned kAll = 0xffffffffu;
 
   for (int d = 0; d < n; ++d) {
-    ws[L.qp + d] = A.q_prev0[c.gdof(d)];
-    ws[L.qc + d] = A.q_cur0[c.gdof(d)];
+    ws[L.qp + d] = A.q_prev0[cv.gdof(d)];
+    ws[L.qc + d] = A.q_cur0[cv.gdof(d)];
   }
   int step = 0, phase = kFirst, k = 0, trials = 0, nh = 0, head = 0, step_evals = 0;
   int worst = kConverged, iters_total = 0, evals_total = 0;
@@ -121,8 +125,8 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
               gtd = fma(gv[k], dv[k], gtd);
             }
         }
-      fin = c.grp.sum(fin);
-      gtd = c.grp.sum(gtd);
+      fin = cv.grp.sum(fin);
+      gtd = cv.grp.sum(gtd);
       if (trial && fin == (double)S && isfinite(Et)) {
         const bool armijo = Et <= E + kLsC1 * alpha * gd;
         const bool approx = (Et <= E + kLsEps * fabs(E)) && (gtd <= (1.0 - 2.0 * kLsDelta) * fabs(gd));
@@ -177,13 +181,13 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
             }
         }
       } else if (back) {
-        c.vlin(L.xt, alpha, L.d, L.x);
+        cv.vlin(L.xt, alpha, L.d, L.x);
       }
-      sy = c.grp.sum(sy);
-      ss = c.grp.sum(ss);
-      yy = c.grp.sum(yy);
-      rr = c.grp.sum(rr);
-      badg = c.grp.sum(badg);
+      sy = cv.grp.sum(sy);
+      ss = cv.grp.sum(ss);
+      yy = cv.grp.sum(yy);
+      rr = cv.grp.sum(rr);
+      badg = cv.grp.sum(badg);
     }
 
     // (3) curvature pair into the ring buffer: rho = 1/s^T y, gamma = s^T y / y^T P y
@@ -211,7 +215,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
             }
         }
       }
-      yPy = c.grp.sum(yPy);
+      yPy = cv.grp.sum(yPy);
       if (pair) {
         ws[L.rho + head] = 1.0 / sy;
         head = (head + 1) % m;
@@ -250,16 +254,16 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
       }
       for (int d = 0; d < n; ++d) {
         const double xv = ws[L.x + d];
-        const double xs = c.grp.from(xv, S - 1);
-        const double xp = (S == 1) ? ws[L.qc + d] : c.grp.from(xv, S - 2);
+        const double xs = cv.grp.from(xv, S - 1);
+        const double xp = (S == 1) ? ws[L.qc + d] : cv.grp.from(xv, S - 2);
         if (fin) {
           ws[L.qp + d] = xp;
           ws[L.qc + d] = xs;
-          if (c.i == 0) {
-            if (A.traj_cur) A.traj_cur[(int64_t)step * D + c.gdof(d)] = xs;
-            if (A.traj_prev) A.traj_prev[(int64_t)step * D + c.gdof(d)] = xp;
+          if (cv.i == 0) {
+            if (A.traj_cur) A.traj_cur[(int64_t)step * D + cv.gdof(d)] = xs;
+            if (A.traj_prev) A.traj_prev[(int64_t)step * D + cv.gdof(d)] = xp;
           }
-          if (A.q_stages_out && step == A.n_steps - 1) A.q_stages_out[c.gstage(d)] = xv;
+          if (A.q_stages_out && step == A.n_steps - 1) A.q_stages_out[cv.gstage(d)] = xv;
         }
       }
       bool next = false;
@@ -277,33 +281,33 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     if (__any_sync(kAll, start)) {
       const int nh_w = __reduce_max_sync(kAll, start ? nh : 0);
       double gd0;
-      if (start) c.vlin(L.d, -1.0, L.g, -1);
+      if (start) cv.vlin(L.d, -1.0, L.g, -1);
       auto slot = [&](int t) { return (head - 1 - t + 2 * m) % m; };
       double al[kMaxHistory];
       double a = 0.0;
-      if (nh_w > 0) a = ws[L.rho + slot(0)] * c.gdot(L.sh + slot(0) * n, L.d);
+      if (nh_w > 0) a = ws[L.rho + slot(0)] * cv.gdot(L.sh + slot(0) * n, L.d);
       for (int t = 0; t < nh_w; ++t) {
         const int j = slot(t);
         al[t] = a;
         const bool more = t + 1 < nh_w;
         const int jn = more ? slot(t + 1) : 0;
-        const double dot = c.axpy_dot(L.d, -a, L.yh + j * n, more ? L.sh + jn * n : -1, start && t < nh);
+        const double dot = cv.axpy_dot(L.d, -a, L.yh + j * n, more ? L.sh + jn * n : -1, start && t < nh);
         if (more) a = ws[L.rho + jn] * dot;
       }
       c.precond(start ? L.d : L.gt);
-      if (start) c.vlin(L.d, gamma, L.d, -1);
+      if (start) cv.vlin(L.d, gamma, L.d, -1);
       if (nh_w > 0) {
-        double bta = ws[L.rho + slot(nh_w - 1)] * c.gdot(L.yh + slot(nh_w - 1) * n, L.d);
+        double bta = ws[L.rho + slot(nh_w - 1)] * cv.gdot(L.yh + slot(nh_w - 1) * n, L.d);
         for (int t = nh_w - 1; t >= 0; --t) {
           const int j = slot(t);
           const int jn = t > 0 ? slot(t - 1) : 0;
-          const double dot = c.axpy_dot(L.d, al[t] - bta, L.sh + j * n, t > 0 ? L.yh + jn * n : L.g,
+          const double dot = cv.axpy_dot(L.d, al[t] - bta, L.sh + j * n, t > 0 ? L.yh + jn * n : L.g,
                                         start && t < nh);
           if (t > 0) bta = ws[L.rho + jn] * dot;
           else gd0 = dot;
         }
       } else {
-        gd0 = c.gdot(L.g, L.d);
+        gd0 = cv.gdot(L.g, L.d);
       }
       if (start) gd = gd0;
       const bool reset = start && !(gd < 0.0);
@@ -311,30 +315,30 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
         if (reset) {
           nh = 0;
           gamma = 1.0;
-          c.vlin(L.d, -1.0, L.g, -1);
+          cv.vlin(L.d, -1.0, L.g, -1);
         }
         c.precond(reset ? L.d : L.gt);
-        const double gd1 = c.gdot(L.g, L.d);
+        const double gd1 = cv.gdot(L.g, L.d);
         if (reset) gd = gd1;
       }
       if (start) {
         alpha = 1.0;
         trials = 0;
-        c.vlin(L.xt, 1.0, L.d, L.x);
+        cv.vlin(L.xt, 1.0, L.d, L.x);
         phase = kTrial;
       }
     }
   }
-  if (active && c.i == 0) {
+  if (active && cv.i == 0) {
     if (A.status) A.status[B.inst_off + b] = worst;
     if (A.iters) A.iters[B.inst_off + b] = iters_total;
     if (A.evals) A.evals[B.inst_off + b] = evals_total;
   }
   if (active) {
     for (int d = 0; d < n; ++d) {
-      if (c.i == 0) {
-        if (A.q_prev_out) A.q_prev_out[c.gdof(d)] = ws[L.qp + d];
-        if (A.q_cur_out) A.q_cur_out[c.gdof(d)] = ws[L.qc + d];
+      if (cv.i == 0) {
+        if (A.q_prev_out) A.q_prev_out[cv.gdof(d)] = ws[L.qp + d];
+        if (A.q_cur_out) A.q_cur_out[cv.gdof(d)] = ws[L.qc + d];
       }
     }
   }
