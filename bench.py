@@ -39,6 +39,13 @@ TANGENT_FLOPS = {0: 327, 1: 680}
 ENERGY_FLOPS = 54                   # Eq. EQ energy terms (one stage only)
 COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 
+# DRAM bytes (read + write) of the rollout kernel per instance-evaluation,
+# from one full ncu capture of k_rollout<3, 0> on 4096 ten-link ball chains
+# over 2 steps (profiles/k_rollout_ballchains4096_2steps_full.md): 30.31 GB
+# over 564,723 instance-evaluations. The roofline's traffic field scales it
+# by the evaluations of the timed launch. Valid for the kernel as captured.
+ROLLOUT_DRAM_BYTES_PER_EVAL = 53665.0
+
 
 def flops_per_eval(jtypes, S):
     per_stage = 0
@@ -614,7 +621,10 @@ def run_ours(args):
                          "iters_per_step": float(iters.mean() / T),
                          "evals_per_step": float(evals.mean() / T)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None,
+                     "frac": achieved / peak,
+                     "traffic": (ROLLOUT_DRAM_BYTES_PER_EVAL * float(evals.sum())
+                                 if (S, spec.n_links) == (3, 10) and spec.jtype.min() == 1 else None),
+                     "traffic_unit": "bytes per launch (DRAM read + write, scaled from an ncu capture)",
                      "peak_source": "measured FP64 FMA probe (pbad_fp64_peak) on this GPU",
                      "flops_per_launch": flops},
         "gpu_launches": args.steps,
