@@ -89,6 +89,8 @@ def parse():
     p.add_argument("--uneven-steps", type=int, default=4,
                    help="steps of the uneven three-bucket batch (0 = skip)")
     p.add_argument("--max-iter-uneven", type=int, default=100)
+    p.add_argument("--dt-sweep", action="store_true",
+                   help="add a step-size sweep of both solvers (ball and hinge chains, dt 0.001-0.128)")
     p.add_argument("--scaling-steps", type=int, default=1,
                    help="steps per rollout of the hinge-chain scaling study (0 = skip)")
     p.add_argument("--scaling-links", type=int, nargs="+", default=[25, 50, 100, 200])
@@ -423,10 +425,55 @@ def measure_uneven(P, args, dev):
                         "converged_fraction": float((st[a:b] == 0).mean()),
                         "iters_per_step": float(it[a:b].mean() / T),
                         "evals_per_step": float(evl[a:b].mean() / T)})
-    return {"value": link_steps / (ms / 1e3), "unit": UNIT, "ms": ms, "timesteps": T,
-            "launches": 1, "threads_per_block": best,
-            "autotune_ms_per_step": {str(k): v for k, v in tuned.items()},
-            "max_iter_per_step": args.max_iter_uneven, "tol": u["tol"], "buckets": buckets}
+    res = {"value": link_steps / (ms / 1e3), "unit": UNIT, "ms": ms, "timesteps": T,
+           "launches": 1, "threads_per_block": best,
+           "autotune_ms_per_step": {str(k): v for k, v in tuned.items()},
+           "max_iter_per_step": args.max_iter_uneven, "tol": u["tol"], "buckets": buckets}
+    # per-bucket solver choice from one-step probes, then the same rollout
+    from paper_1709_04145_b300.tuning import choose_solvers
+    t0 = time.perf_counter()
+    chosen, report = choose_solvers(batch, qp, qc, tau, dt, S, probe_steps=1, history=m,
+                                    tol=u["tol"], max_iter={P.LBFGS: args.max_iter_uneven,
+                                                            P.NEWTON: args.max_iter_uneven},
+                                    threads=best)
+    probe_s = time.perf_counter() - t0
+    run_c = lambda steps: P.rollout(batch, qp, qc, tau[:steps].reshape(-1).contiguous(), steps, dt,
+                                    S, chosen, m, u["tol"], args.max_iter_uneven, want_traj=False)
+    ms_c, out_c = _timed(lambda: run_c(T))
+    st_c = out_c["status"].cpu().numpy()
+    names = {P.LBFGS: "lbfgs", P.NEWTON: "newton"}
+    res["solver_choice"] = {
+        "rule": "per bucket, the solver with the least device time per converged instance-step "
+                "over a one-step probe of the bucket alone",
+        "probe_wall_s": probe_s,
+        "chosen": [names[c] for c in chosen],
+        "value": link_steps / (ms_c / 1e3), "ms": ms_c,
+        "buckets": [{"model": spec.name,
+                     "probe": {names[r.solver]: {"ms": r.ms, "converged_fraction": r.converged / r.total}
+                               for r in report[k]},
+                     "converged_fraction": float((st_c[int(batch.inst_off[k]):int(batch.inst_off[k + 1])] == 0).mean())}
+                    for k, spec in enumerate(u["specs"])]}
+    return res
+
+
+def measure_dt_sweep(P, args, dev):
+    """Step-size sweep of both solvers on two bodies: 512 ten-link ball chains
+    (three stages) and 512 five-link hinge-rod chains (two stages), two
+    steps per size from the seeded initial states, zero torques."""
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    from paper_1709_04145_b300.tuning import dt_sweep
+    dts = [0.001 * 2 ** k for k in range(8)]
+    out = {}
+    for name, spec, S in (("ball_chain10", I.ball_chain(512, 10, 2601, radius=0.15), 3),
+                          ("rod_chain5", I.rod_chain(512, 5, name="rod_chain5"), 2)):
+        q0, qd0 = I.random_state(spec, 2602)
+        model = P.Model.from_spec(spec, device=dev.index)
+        t = lambda a: torch.tensor(a.reshape(-1), device=dev)
+        out[name] = {"stages": S, "instances": spec.count,
+                     "rows": dt_sweep(model, t(q0), t(qd0), dts, S, steps=2, tol=args.tol,
+                                      max_iter=args.max_iter_uneven)}
+    return out
 
 
 def measure_scaling(P, args, dev):
@@ -645,6 +692,8 @@ def run_ours(args):
         line["uneven_batch"] = measure_uneven(P, args, dev)
     if rank == 0 and args.scaling_steps > 0:
         line["scaling_study"] = measure_scaling(P, args, dev)
+    if rank == 0 and args.dt_sweep:
+        line["dt_sweep"] = measure_dt_sweep(P, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         rate, cores, sample = cpu_oracle_rate(w, n_inst=min(os.cpu_count() or 1, 16), n_steps=1,
                                               budget_s=args.cpu_sample_seconds)

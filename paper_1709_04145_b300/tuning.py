@@ -1,0 +1,127 @@
+"""Solver choice per bucket and time-step sweeps.
+
+The paper compares L-BFGS and LM (Newton) per time step and finds the
+better one depends on the step size and the body (Section 6.1, Fig.
+OPTProf). `choose_solvers` makes that choice for each bucket of a batch
+from a short probe: it runs the bucket alone with each solver over the
+first steps of its own inputs and keeps the solver with the smaller device
+time per converged instance-step. `dt_sweep` reports, for a range of step
+sizes, what each solver achieves on a model. Both only time launches of
+the library; the decision rule itself (`pick`) is plain host logic.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import LBFGS, NEWTON, Batch, colloc, rollout
+
+
+@dataclass
+class ProbeResult:
+    """Outcome of one solver on one bucket: device milliseconds of the probe
+    launch, converged instance-steps and all instance-steps."""
+    solver: int
+    ms: float
+    converged: int
+    total: int
+    iters_per_step: float = 0.0
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def ms_per_converged(self) -> float:
+        return self.ms / self.converged if self.converged > 0 else float("inf")
+
+
+def pick(results) -> int:
+    """The solver with the smallest time per converged instance-step; if no
+    solver converges anything, the one with the most converged steps, then
+    the fastest. Ties go to L-BFGS (no dense storage)."""
+    results = list(results)
+    if not results:
+        raise ValueError("no probe results")
+    if any(r.converged > 0 for r in results):
+        return min(results, key=lambda r: (r.ms_per_converged, r.solver)).solver
+    return min(results, key=lambda r: (-r.converged, r.ms, r.solver)).solver
+
+
+def _timed(fn):
+    import torch
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    out = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1), out
+
+
+def probe(model, q_prev, q_cur, tau_seq, n_steps: int, dt: float, stages: int, solver: int,
+          history: int = 8, tol: float = 1e-8, max_iter: int = 100, threads: int = 32) -> ProbeResult:
+    """Runs one bucket alone for n_steps with one solver (after a one-step
+    warm-up launch) and counts its converged instance-steps. q_prev/q_cur:
+    DOF-packed device tensors of this bucket; tau_seq: (n_steps * D) device
+    tensor or None."""
+    batch = Batch([model], max_stages=stages, max_history=history, newton=(solver == NEWTON))
+    batch.set_threads(threads)
+    tau1 = None if tau_seq is None else tau_seq[:batch.D].contiguous()
+    rollout(batch, q_prev, q_cur, tau1, 1, dt, stages, solver, history, tol, max_iter,
+            want_traj=False)
+    converged = 0
+    qp, qc = q_prev, q_cur
+    ms = 0.0
+    iters = 0.0
+    for t in range(n_steps):
+        tau_t = None if tau_seq is None else tau_seq[t * batch.D:(t + 1) * batch.D].contiguous()
+        dms, out = _timed(lambda: rollout(batch, qp, qc, tau_t, 1, dt, stages, solver, history,
+                                          tol, max_iter, want_traj=False))
+        ms += dms
+        converged += int((out["status"] == 0).sum().item())
+        iters += float(out["iters"].float().mean().item())
+        qp, qc = out["q_prev"], out["q_cur"]
+    return ProbeResult(solver, ms, converged, model.count * n_steps, iters / n_steps)
+
+
+def choose_solvers(batch: Batch, q_prev, q_cur, tau_seq, dt: float, stages: int,
+                   probe_steps: int = 2, history: int = 8, tol: float = 1e-8,
+                   max_iter: dict | None = None, threads: int = 32):
+    """One solver per model of `batch` (LBFGS or NEWTON), chosen from probes
+    over the first `probe_steps` steps of each bucket's own inputs.
+    tau_seq: (n >= probe_steps steps, D) DOF-packed device tensor or None.
+    Returns (solvers, {model index: [ProbeResult, ...]})."""
+    max_iter = max_iter or {LBFGS: 100, NEWTON: 100}
+    solvers, report = [], {}
+    for k, m in enumerate(batch.models):
+        a, b = int(batch.dof_off[k]), int(batch.dof_off[k + 1])
+        tau_k = None
+        if tau_seq is not None:
+            tau_k = tau_seq[:probe_steps, a:b].contiguous().reshape(-1)
+        res = [probe(m, q_prev[a:b].contiguous(), q_cur[a:b].contiguous(), tau_k, probe_steps, dt,
+                     stages, sv, history, tol, max_iter[sv], threads)
+               for sv in (LBFGS, NEWTON)]
+        solvers.append(pick(res))
+        report[k] = res
+    return solvers, report
+
+
+def dt_sweep(model, q0, qd0, dts, stages: int, steps: int = 2, history: int = 8, tol: float = 1e-8,
+             max_iter: int = 100, threads: int = 32):
+    """For each step size: converged fraction, iterations per step and device
+    ms per step of each solver over `steps` steps from (q0, qd0) (device
+    tensors, DOF-packed), zero torques. Returns a list of dicts."""
+    rows = []
+    nodes, _ = colloc(stages)
+    for dt in dts:
+        q_prev = (q0 + float(nodes[0]) * dt * qd0).contiguous()
+        row = {"dt": float(dt)}
+        for name, sv in (("lbfgs", LBFGS), ("newton", NEWTON)):
+            r = probe(model, q_prev, q0, None, steps, dt, stages, sv, history, tol, max_iter,
+                      threads)
+            row[name] = {"converged_fraction": r.converged / r.total,
+                         "iters_per_step": r.iters_per_step, "ms_per_step": r.ms / steps}
+        rows.append(row)
+    return rows
+
+
+__all__ = ["ProbeResult", "pick", "probe", "choose_solvers", "dt_sweep"]
