@@ -57,6 +57,8 @@ def lib():
         L.om_legendre_roots.argtypes = [C.c_int, dp]
         L.om_colloc.restype = C.c_int
         L.om_colloc.argtypes = [C.c_int, dp, dp]
+        L.om_colloc_vel.argtypes = [C.c_int, dp]
+        L.om_model_set_drag.argtypes = [vp, C.c_double]
         L.om_mass_moment_rod.argtypes = [C.c_double, C.c_double, dp]
         L.om_mass_moment_capsule.argtypes = [C.c_double, C.c_double, C.c_double, dp]
         L.om_hmass.argtypes = [vp, dp, dp]
@@ -115,6 +117,16 @@ def colloc(S: int):
     return nodes, W
 
 
+def colloc_vel(S: int) -> np.ndarray:
+    """First-derivative weights V (S, S+2) in units of 1/dt: the stage-node
+    velocities of the collocation polynomial (S >= 2) or the backward
+    difference [0, -1, 1] of the drag potential (S = 1)."""
+    V = np.zeros((S, S + 2))
+    if lib().om_colloc_vel(S, V.ctypes.data_as(C.POINTER(C.c_double))) != 0:
+        raise ValueError("unsupported stage count")
+    return V
+
+
 def mass_moment_rod(m: float, L: float) -> np.ndarray:
     out = np.zeros(10)
     lib().om_mass_moment_rod(m, L, out.ctypes.data_as(C.POINTER(C.c_double)))
@@ -168,7 +180,7 @@ def rest_from_spec(spec, b: int) -> np.ndarray:
 class OracleModel:
     """One articulated body (one instance) in the oracle."""
 
-    def __init__(self, parent, jtype, axis, mm, rest, gravity):
+    def __init__(self, parent, jtype, axis, mm, rest, gravity, drag: float = 0.0):
         self.parent, pp = _i(parent)
         self.jtype, jp = _i(jtype)
         self.axis, ap = _d(np.asarray(axis).reshape(-1, 3))
@@ -181,11 +193,13 @@ class OracleModel:
             raise ValueError("malformed model")
         self._h = C.c_void_p(h)
         self.n_dof = lib().om_n_dof(self._h)
+        self.drag = float(drag)
+        lib().om_model_set_drag(self._h, self.drag)
 
     @classmethod
-    def from_spec(cls, spec, b: int = 0):
+    def from_spec(cls, spec, b: int = 0, drag: float = 0.0):
         return cls(spec.parent, spec.jtype, spec.axis, mass_moments_from_spec(spec, b),
-                   rest_from_spec(spec, b), spec.gravity)
+                   rest_from_spec(spec, b), spec.gravity, drag)
 
     def __del__(self):
         h = getattr(self, "_h", None)

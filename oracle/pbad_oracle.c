@@ -45,6 +45,7 @@ typedef struct {
   double *mm;   /* [N][10] */
   double *rest; /* [N][12] */
   double g[3];
+  double drag;   /* drag coefficient c of Q_drag (0 = none), see om_model_set_drag */
   int *path_len; /* number of joints from the root to l, inclusive */
   int *path;     /* [N][N]: path[l*N + k] = k-th joint on the root->l path */
 } om_model;
@@ -100,6 +101,17 @@ void *om_model_new(int n_links, const int *parent, const int *jtype,
 }
 
 int om_n_dof(void *p) { return ((om_model *)p)->n_dof; }
+
+/* Drag potential of Section 6.2 (swimmer): Q_drag = D |(P(q_{k+1}) - P(q_k))/dt|^2
+ * integrated over the body. With the mass-weighted moments M_l used here the
+ * coefficient is per unit mass, c = D / rho:
+ *   int Q_drag = c / dt^2 * tr((T_{k+1} - T_k) M (T_{k+1} - T_k)^T)
+ * (Appendix A's I-expansion of Q_drag), whose gradient is the force density
+ * -2 c rho v / dt with v = (P_{k+1} - P_k)/dt. For S >= 2 stages the same force
+ * law enters every stage residual of Eq. HOC with v the velocity of the
+ * collocation polynomial at the stage node (first-derivative weights of
+ * om_colloc_vel). */
+void om_model_set_drag(void *p, double c) { ((om_model *)p)->drag = c; }
 
 /* ------------------------------------------------------------------ */
 /* small dense helpers (4x4 row-major homogeneous, 3x3 row-major)      */
@@ -518,6 +530,56 @@ int om_colloc(int S, double *nodes, double *W) {
   return 0;
 }
 
+/* First-derivative weights V (S x (S+2), row-major, units 1/dt): velocity of
+ * the collocation polynomial at stage node i, v_i = sum_j V_ij q_j / dt. For
+ * one stage, the backward difference of the drag potential (Section 6.2):
+ * V = [0, -1, 1]. For S >= 2, V_ij = l_j'(alpha_i) of the Lagrange basis over
+ * the S+2 nodes of om_colloc (its Vandermonde inverse, recomputed here). */
+int om_colloc_vel(int S, double *Vw) {
+  if (S < 1 || S > 8) return -1;
+  int P = S + 2;
+  if (S == 1) {
+    Vw[0] = 0.0; Vw[1] = -1.0; Vw[2] = 1.0;
+    return 0;
+  }
+  double nodes[16], Wtmp[8 * 16];
+  om_colloc(S, nodes, Wtmp);
+  double V[16 * 16], C[16 * 16];
+  for (int r = 0; r < P; ++r)
+    for (int k = 0; k < P; ++k) {
+      V[r * P + k] = pow(nodes[r], k);
+      C[r * P + k] = (r == k) ? 1.0 : 0.0;
+    }
+  for (int col = 0; col < P; ++col) {
+    int piv = col;
+    for (int r = col + 1; r < P; ++r)
+      if (fabs(V[r * P + col]) > fabs(V[piv * P + col])) piv = r;
+    for (int k = 0; k < P; ++k) {
+      double t = V[col * P + k]; V[col * P + k] = V[piv * P + k]; V[piv * P + k] = t;
+      t = C[col * P + k]; C[col * P + k] = C[piv * P + k]; C[piv * P + k] = t;
+    }
+    double d = V[col * P + col];
+    for (int k = 0; k < P; ++k) { V[col * P + k] /= d; C[col * P + k] /= d; }
+    for (int r = 0; r < P; ++r) {
+      if (r == col) continue;
+      double fct = V[r * P + col];
+      for (int k = 0; k < P; ++k) {
+        V[r * P + k] -= fct * V[col * P + k];
+        C[r * P + k] -= fct * C[col * P + k];
+      }
+    }
+  }
+  for (int i = 0; i < S; ++i) {
+    double t = nodes[2 + i];
+    for (int j = 0; j < P; ++j) {
+      double s = 0;
+      for (int k = 1; k < P; ++k) s += k * C[k * P + j] * pow(t, k - 1);
+      Vw[i * P + j] = s;
+    }
+  }
+  return 0;
+}
+
 /* ------------------------------------------------------------------ */
 /* mass moments (Eq. ATOM: int rho [p;1][p;1]^T dp)                     */
 /* ------------------------------------------------------------------ */
@@ -590,9 +652,14 @@ double om_eval(void *p, int S, double dt, const double *qs,
                double *r, double *grad, double *Jr) {
   om_model *m = (om_model *)p;
   int N = m->n_links, n = m->n_dof, P = S + 2, Sn = S * n;
-  double nodes[16], W[8 * 16];
+  double nodes[16], W[8 * 16], Vw[8 * 16];
   om_colloc(S, nodes, W);
+  om_colloc_vel(S, Vw);
   double idt2 = 1.0 / (dt * dt);
+  const double cd = m->drag;
+  /* seed weights: acceleration W/dt^2 plus the drag force 2 c V/dt^2 */
+  double Wt[8 * 16];
+  for (int k = 0; k < S * P; ++k) Wt[k] = (W[k] + 2.0 * cd * Vw[k]) * idt2;
   /* transforms at every node */
   double *T = (double *)malloc(sizeof(double) * 16 * N * P);
   om_fk(p, q_prev, T);
@@ -625,17 +692,24 @@ double om_eval(void *p, int S, double dt, const double *qs,
         D[k] = T[16 * N * 2 + 16 * l + k] - 2 * T[16 * N + 16 * l + k] + T[16 * l + k];
       m4_mul(D, M, DM);
       E += 0.5 * idt2 * contract34(DM, D);
+      if (cd != 0.0) {
+        /* Q_drag: c / dt^2 tr(D' M D'^T), D' = T_{k+1} - T_k */
+        double Dv[16], DvM[16];
+        for (int k = 0; k < 16; ++k) Dv[k] = T[16 * N * 2 + 16 * l + k] - T[16 * N + 16 * l + k];
+        m4_mul(Dv, M, DvM);
+        E += cd * idt2 * contract34(DvM, Dv);
+      }
       for (int rrow = 0; rrow < 3; ++rrow)
         for (int c = 0; c < 4; ++c)
           E -= m->g[rrow] * T[16 * N * 2 + 16 * l + 4 * rrow + c] * mc4[c];
     }
     for (int i = 0; i < S; ++i) {
-      /* seed G_{i,l} = (sum_j W_ij T_l(q_j)/dt^2) M_l - g [mc; m]^T */
+      /* seed G_{i,l} = (sum_j (W_ij + 2c V_ij) T_l(q_j) / dt^2) M_l - g [mc; m]^T */
       double A[16], G[16];
       for (int k = 0; k < 16; ++k) {
         double s = 0;
-        for (int j = 0; j < P; ++j) s += W[i * P + j] * T[16 * N * j + 16 * l + k];
-        A[k] = s * idt2;
+        for (int j = 0; j < P; ++j) s += Wt[i * P + j] * T[16 * N * j + 16 * l + k];
+        A[k] = s;
       }
       m4_mul(A, M, G);
       for (int rrow = 0; rrow < 3; ++rrow)
@@ -648,9 +722,9 @@ double om_eval(void *p, int S, double dt, const double *qs,
         for (int d = 0; d < n; ++d)
           for (int e = 0; e < n; ++e) J[(i * n + d) * Sn + i * n + e] += Hblk[d * n + e];
         free(Hblk);
-        /* dependence of the seed on every unknown stage j through W_ij */
+        /* dependence of the seed on every unknown stage j through its weight */
         for (int j = 0; j < S; ++j) {
-          double wij = W[i * P + 2 + j] * idt2;
+          double wij = Wt[i * P + 2 + j];
           for (int e = 0; e < n; ++e) {
             double DM[16];
             m4_mul(dTi + 16 * n * j + 16 * e, M, DM);
@@ -691,9 +765,11 @@ void om_resid_known_jac(void *p, int S, double dt, const double *qs,
                         double *Jc) {
   om_model *m = (om_model *)p;
   int N = m->n_links, n = m->n_dof, P = S + 2, Sn = S * n;
-  double nodes[16], W[8 * 16];
+  double nodes[16], W[8 * 16], Vw[8 * 16];
   om_colloc(S, nodes, W);
+  om_colloc_vel(S, Vw);
   double idt2 = 1.0 / (dt * dt);
+  const double cd = m->drag;
   memset(Jp, 0, sizeof(double) * Sn * n);
   memset(Jc, 0, sizeof(double) * Sn * n);
   double *dTi = (double *)malloc(sizeof(double) * 16 * n * S);
@@ -706,7 +782,8 @@ void om_resid_known_jac(void *p, int S, double dt, const double *qs,
     om_link_dT(p, q_prev, l, dTp);
     om_link_dT(p, q_cur, l, dTc);
     for (int i = 0; i < S; ++i) {
-      double wp = W[i * P + 0] * idt2, wc = W[i * P + 1] * idt2;
+      double wp = (W[i * P + 0] + 2.0 * cd * Vw[i * P + 0]) * idt2;
+      double wc = (W[i * P + 1] + 2.0 * cd * Vw[i * P + 1]) * idt2;
       for (int e = 0; e < n; ++e) {
         double DMp[16], DMc[16];
         m4_mul(dTp + 16 * e, M, DMp);
@@ -1098,8 +1175,9 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
     if (rn < tol) { status = OM_CONVERGED; break; }
     if (k >= max_iter) { status = OM_MAX_ITER; break; }
     if (S == 1) {
+      /* Gauss-Newton matrix of Eq. EQ (+ Q_drag): (1 + 2 c) H_mass / dt^2 */
       om_hmass(m, x, Hm);
-      for (int i = 0; i < Sn * Sn; ++i) H[i] = Hm[i] / (dt * dt);
+      for (int i = 0; i < Sn * Sn; ++i) H[i] = (1.0 + 2.0 * m->drag) * Hm[i] / (dt * dt);
       for (int i = 0; i < Sn; ++i) gr[i] = r[i];
     } else {
       for (int a = 0; a < Sn; ++a)
