@@ -89,6 +89,8 @@ def parse():
     p.add_argument("--uneven-steps", type=int, default=4,
                    help="steps of the uneven three-bucket batch (0 = skip)")
     p.add_argument("--max-iter-uneven", type=int, default=100)
+    p.add_argument("--drag-steps", type=int, default=20,
+                   help="steps of the swimmer-like drag workload (0 = skip)")
     p.add_argument("--dt-sweep", action="store_true",
                    help="add a step-size sweep of both solvers (ball and hinge chains, dt 0.001-0.128)")
     p.add_argument("--scaling-steps", type=int, default=1,
@@ -456,6 +458,46 @@ def measure_uneven(P, args, dev):
     return res
 
 
+def measure_drag(P, args, dev):
+    """Drag potential (Section 6.2): swimmer-like chains (4096 x 4 hinge rods,
+    no gravity, c = 0.5, dt = 0.05, one stage, L-BFGS) over args.drag_steps
+    steps, and the main ball-chain batch with c = 0.5 against the same batch
+    without drag over 5 steps (the drag only changes seed weights there)."""
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    out = {}
+    w = I.swimmers(n_steps=args.drag_steps)
+    spec, S, dt, m = w["spec"], w["stages"], w["dt"], w["history"]
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index, drag=w["drag"])], max_stages=S,
+                    max_history=m)
+    qp, qc = _state_tensors(P, [(w["q0"], w["qd0"])], S, dt, dev)
+    T = w["n_steps"]
+    run = lambda: P.rollout(batch, qp, qc, None, T, dt, S, P.LBFGS, m, w["tol"], 200, want_traj=False)
+    run()
+    ms, res = _timed(run)
+    st = res["status"].cpu().numpy()
+    out["swimmers"] = {"value": spec.count * spec.n_links * T / (ms / 1e3), "unit": UNIT, "ms": ms,
+                       "instances": spec.count, "links": spec.n_links, "timesteps": T, "dt": dt,
+                       "stages": S, "drag": w["drag"], "tol": w["tol"],
+                       "converged_fraction": float((st == 0).mean()),
+                       "iters_per_step": float(res["iters"].float().mean().item() / T)}
+    wb = I.ball_chains(count=args.instances, n_links=args.links, n_steps=5)
+    spec = wb["spec"]
+    S, dt, m = wb["stages"], wb["dt"], wb["history"]
+    qp, qc = _state_tensors(P, [(wb["q0"], wb["qd0"])], S, dt, dev)
+    row = {}
+    for c in (0.0, 0.5):
+        bt = P.Batch([P.Model.from_spec(spec, device=dev.index, drag=c)], max_stages=S, max_history=m)
+        run = lambda: P.rollout(bt, qp, qc, None, 5, dt, S, P.LBFGS, m, args.tol, args.max_iter,
+                                want_traj=False)
+        run()
+        ms, res = _timed(run)
+        row[f"c={c}"] = {"ms": ms, "value": spec.count * spec.n_links * 5 / (ms / 1e3),
+                         "evals_per_step": float(res["evals"].float().mean().item() / 5)}
+    out["ball_chains_5_steps"] = row
+    return out
+
+
 def measure_dt_sweep(P, args, dev):
     """Step-size sweep of both solvers on two bodies: 512 ten-link ball chains
     (three stages) and 512 five-link hinge-rod chains (two stages), two
@@ -692,6 +734,8 @@ def run_ours(args):
         line["uneven_batch"] = measure_uneven(P, args, dev)
     if rank == 0 and args.scaling_steps > 0:
         line["scaling_study"] = measure_scaling(P, args, dev)
+    if rank == 0 and args.drag_steps > 0:
+        line["drag"] = measure_drag(P, args, dev)
     if rank == 0 and args.dt_sweep:
         line["dt_sweep"] = measure_dt_sweep(P, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

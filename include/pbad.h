@@ -114,6 +114,19 @@ PBAD_API int pbad_model_create(int32_t n_links, const int32_t* parent, const int
 PBAD_API int pbad_model_destroy(pbad_model* model);
 PBAD_API int pbad_model_info(const pbad_model* model, int32_t* n_links, int32_t* n_dof, int64_t* count);
 
+/* Drag potential of Section 6.2 (the swimmer's fluid drag) on every link of
+ * the model: Q_drag = D |(P(q_{k+1}) - P(q_k))/dt|^2 integrated over the body,
+ * with c = D / rho (per unit mass, >= 0; 0 = none). For one stage it adds
+ * c/dt^2 tr((T_{k+1} - T_k) M (T_{k+1} - T_k)^T) to Eq. EQ (Appendix A); its
+ * gradient, the force density -2 c rho v / dt, enters the residual. For
+ * S >= 2 stages the same force law enters every stage residual of Eq. HOC with
+ * v the velocity of the collocation polynomial at the stage node. Set it
+ * before creating the batches that use the model (a batch reserves the
+ * one-stage drag storage at creation; a one-stage call on a batch created
+ * before the drag was set returns PBAD_ERR_ARG). Errors: PBAD_ERR_ARG for a
+ * NULL model or a negative or non-finite c. */
+PBAD_API int pbad_model_set_drag(pbad_model* model, double c);
+
 /* Creates a batch over 1..PBAD_MAX_MODELS models (same device) and allocates
  * the solver workspace for up to max_stages stages and L-BFGS history
  * max_history; flags = PBAD_BATCH_NEWTON also reserves the dense

@@ -64,7 +64,8 @@ def fp64_peak(device: int = 0) -> float:
 class Model:
     """One topology with ``count`` instances (pbad_model)."""
 
-    def __init__(self, parent, jtype, axis, mass_moment, rest, gravity, device: int = 0):
+    def __init__(self, parent, jtype, axis, mass_moment, rest, gravity, device: int = 0,
+                 drag: float = 0.0):
         parent = np.ascontiguousarray(parent, dtype=np.int32)
         jtype = np.ascontiguousarray(jtype, dtype=np.int32)
         axis = np.ascontiguousarray(axis, dtype=np.float64).reshape(-1, 3)
@@ -86,12 +87,16 @@ class Model:
         nl, nd, cnt = C.c_int32(), C.c_int32(), C.c_int64()
         check(lib().pbad_model_info(h, C.byref(nl), C.byref(nd), C.byref(cnt)), "pbad_model_info")
         self.n_dof = nd.value
+        self.drag = float(drag)
+        if self.drag != 0.0:
+            check(lib().pbad_model_set_drag(h, self.drag), "pbad_model_set_drag")
 
     @classmethod
-    def from_spec(cls, spec: "inputs.BodySpec", device: int = 0) -> "Model":
+    def from_spec(cls, spec: "inputs.BodySpec", device: int = 0, drag: float = 0.0) -> "Model":
+        """drag: coefficient c of the drag potential (Section 6.2), per unit mass."""
         from .models import mass_moments, rest_transforms
         return cls(spec.parent, spec.jtype, spec.axis, mass_moments(spec), rest_transforms(spec),
-                   spec.gravity, device)
+                   spec.gravity, device, drag)
 
     def __del__(self):
         h = getattr(self, "_h", None)

@@ -65,6 +65,7 @@ using namespace pbad;
 struct pbad_model {
   int N = 0, n = 0, device = 0, chain = 1;
   int64_t count = 0;
+  double drag = 0.0;  // drag coefficient c of Q_drag (Section 6.2)
   std::vector<int> parent, jtype, dof;
   double g[3] = {0, 0, 0};
   int* d_topo = nullptr;     // parent[N] | jtype[N] | dof[N] | rest_eye[N]
@@ -78,6 +79,7 @@ struct pbad_batch {
   int threads = 32;  // threads per block of the solver kernels
   std::vector<pbad_model*> models;
   std::vector<int64_t> inst_off, dof_off, lanes, lane_doubles;
+  std::vector<int> tk;         // per bucket: workspace holds T(q_cur) for the one-stage drag energy
   std::vector<size_t> ws_off;  // in doubles
   int64_t n_inst = 0, D = 0;
   double* d_ws = nullptr;
@@ -170,6 +172,38 @@ int colloc_table(int S, double* nodes, double* W) {
   return 0;
 }
 
+// First derivatives of the Lagrange basis over the same nodes at the stage
+// nodes, l_j'(t) = sum_{a != j} prod_{p != j, a} (t - x_p) / prod_{p != j} (x_j - x_p);
+// one stage uses the drag potential's backward difference [0, -1, 1]
+// (Section 6.2) instead. V[i * (S+2) + j], dimensionless.
+int colloc_vel_table(int S, const double* nodes, double* V) {
+  const int P = S + 2;
+  if (S == 1) {
+    V[0] = 0.0;
+    V[1] = -1.0;
+    V[2] = 1.0;
+    return 0;
+  }
+  for (int i = 0; i < S; ++i) {
+    const double t = nodes[2 + i];
+    for (int j = 0; j < P; ++j) {
+      double den = 1.0;
+      for (int p = 0; p < P; ++p)
+        if (p != j) den *= nodes[j] - nodes[p];
+      double num = 0.0;
+      for (int a = 0; a < P; ++a) {
+        if (a == j) continue;
+        double pr = 1.0;
+        for (int p = 0; p < P; ++p)
+          if (p != j && p != a) pr *= t - nodes[p];
+        num += pr;
+      }
+      V[i * P + j] = num / den;
+    }
+  }
+  return 0;
+}
+
 // Gauss-Jordan inverse of a small dense matrix (n <= kMaxStages).
 bool small_inverse(int n, const double* A_, double* X) {
   double A[kMaxStages * kMaxStages];
@@ -210,11 +244,18 @@ int make_colloc(int S, double dt, Colloc* K) {
   K->dt = dt;
   const int P = S + 2;
   const double idt2 = 1.0 / (dt * dt);
+  double V[kMaxStages * (kMaxStages + 2)];
+  colloc_vel_table(S, nodes, V);
   for (int k = 0; k < P; ++k) K->nodes[k] = nodes[k];
   for (int i = 0; i < S; ++i) {
     K->Wk[i][0] = W[i * P + 0] * idt2;
     K->Wk[i][1] = W[i * P + 1] * idt2;
-    for (int j = 0; j < S; ++j) K->Wu[i][j] = W[i * P + 2 + j] * idt2;
+    K->Vk[i][0] = V[i * P + 0] * idt2;
+    K->Vk[i][1] = V[i * P + 1] * idt2;
+    for (int j = 0; j < S; ++j) {
+      K->Wu[i][j] = W[i * P + 2 + j] * idt2;
+      K->Vu[i][j] = V[i * P + 2 + j] * idt2;
+    }
   }
   // stage block of the L-BFGS initial inverse Hessian:
   //   S == 1: dt^2; S >= 2: (Wu^T Wu)^-1 / 2
@@ -275,6 +316,11 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.chain = m->chain;
     B.dense = bt->d_dense ? bt->d_dense + bt->dense_off[k] : nullptr;
     B.dense_stride = bt->d_dense ? bt->dense_stride[k] : 0;
+    B.drag = m->drag;
+    B.tk = bt->tk[k];
+    if (S == 1 && m->drag != 0.0 && !B.tk)
+      return fail(PBAD_ERR_ARG, "the model's drag was set after the batch was created "
+                                "(one-stage drag needs storage reserved at batch creation)");
     const bool warp_map = all_warp || B.solver == PBAD_NEWTON;
     const int64_t warps = warp_map ? m->count : (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
     blocks += (int)((warps + wpb - 1) / wpb);
@@ -440,6 +486,13 @@ int pbad_model_destroy(pbad_model* m) {
   return PBAD_OK;
 }
 
+int pbad_model_set_drag(pbad_model* m, double c) {
+  if (!m) return fail(PBAD_ERR_ARG, "null model");
+  if (!(c >= 0.0) || !std::isfinite(c)) return fail(PBAD_ERR_ARG, "drag must be finite and >= 0");
+  m->drag = c;
+  return PBAD_OK;
+}
+
 int pbad_model_info(const pbad_model* m, int32_t* n_links, int32_t* n_dof, int64_t* count) {
   if (!m) return fail(PBAD_ERR_ARG, "null model");
   if (n_links) *n_links = m->N;
@@ -504,7 +557,9 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
       bt->dense_doubles += (size_t)m->count * DL.total;
     }
     WsLayout L;
-    L.make(m->N, m->n, max_history, (flags & PBAD_BATCH_NEWTON) ? max_stages : 0);
+    const int tk = m->drag != 0.0;  // one-stage drag energy needs T(q_cur) per link
+    L.make(m->N, m->n, max_history, (flags & PBAD_BATCH_NEWTON) ? max_stages : 0, tk);
+    bt->tk.push_back(tk);
     bt->lanes.push_back(lanes);
     bt->lane_doubles.push_back(L.total);
     bt->ws_off.push_back(ws);
@@ -709,7 +764,8 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   const int64_t warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
   const int64_t blocks = (warps + 3) / 4;
   WsLayout L;
-  L.make(m->N, m->n, 0);
+  const int tk = m->drag != 0.0;
+  L.make(m->N, m->n, 0, 0, tk);
   *lanes = blocks * 4 * 32;
   *per_lane = L.total;
   A->nb = 1;
@@ -731,6 +787,8 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   B.ws_lane = L.total;
   B.block_begin = 0;
   B.chain = m->chain;
+  B.drag = m->drag;
+  B.tk = tk;
   *grid = (int)blocks;
   return PBAD_OK;
 }

@@ -46,6 +46,8 @@ struct Bucket {
   int chain;             // 1 if parent[l] == l - 1 for every link (serial chain)
   double* dense;         // per-instance dense Newton/adjoint storage (or null)
   int64_t dense_stride;  // doubles per instance in `dense`
+  double drag;           // drag coefficient c of Q_drag (Section 6.2), 0 = none
+  int tk;                // 1 if the lane workspace holds T(q_cur) for the one-stage drag energy
 };
 
 // Collocation constants of one launch (all in units of 1/dt^2 already).
@@ -56,6 +58,10 @@ struct Colloc {
   double Wk[kMaxStages][2];           // weights of the two known nodes
   double Wu[kMaxStages][kMaxStages];  // Wu[i][j]: residual stage i, unknown j
   double Ps[kMaxStages][kMaxStages];  // stage block of the L-BFGS H0
+  // velocity weights of the drag force (V / dt^2 with V the first-derivative
+  // weights; one stage: the backward difference [0, -1, 1])
+  double Vk[kMaxStages][2];
+  double Vu[kMaxStages][kMaxStages];
 };
 
 // ---------------------------------------------------------------- 3x4 math

@@ -28,8 +28,9 @@ enum Status { kConverged = 0, kMaxIter = 1, kLsFail = 2, kCholFail = 3, kNonFini
 struct WsLayout {
   int T, G, acc, axes, V, accd, C, Pb, ec, x, g, d, xt, gt, r, rt, qp, qc, sh, yh, rho;
   int u, jc;  // Jacobian-column scratch (present when Sd > 0)
+  int tk;     // T(q_cur) per link for the one-stage drag energy (present when tk_region)
   int64_t total;
-  __host__ __device__ void make(int N, int n, int m, int Sd = 0) {
+  __host__ __device__ void make(int N, int n, int m, int Sd = 0, int tk_region = 0) {
     int o = 0;
     T = o; o += 12 * N;
     G = o; o += 12 * N;
@@ -54,6 +55,7 @@ struct WsLayout {
     rho = o; o += (m > 0 ? m : 1);
     u = o; o += (Sd ? n : 0);
     jc = o; o += (Sd ? n : 0);
+    tk = o; o += (tk_region ? 12 * N : 0);
     total = o;
   }
 };
@@ -122,24 +124,27 @@ struct Ctx {
   int b;              // instance within the bucket (always a valid index)
   int i;              // own stage
   int N, n;
-  double wk[2];       // K.Wk[i][*]: weights of the two known nodes for the own stage
-  double wu_row[S];   // K.Wu[i][*]
-  double wu_col[S];   // K.Wu[*][i]
+  // seed weights of the own stage: acceleration plus the drag force,
+  // W + 2 c V (units 1/dt^2); the preconditioner keeps the drag-free block
+  double wk[2];       // known nodes: K.Wk[i][*] + 2c K.Vk[i][*]
+  double wu_row[S];   // unknown stages: K.Wu[i][*] + 2c K.Vu[i][*]
+  double wu_col[S];   // K.Wu[*][i] + 2c K.Vu[*][i]
   double ps_row[S];   // K.Ps[i][*]
 
   __device__ Ctx(const Bucket& B_, const Colloc& K_, int b_, int64_t lane_id, int m, int Sd = 0)
       : B(B_), K(K_), b(b_) {
     N = B.N;
     n = B.n;
-    L.make(N, n, m, Sd);
+    L.make(N, n, m, Sd, B.tk);
     ws.p = B.ws + ((lane_id >> 5) * B.ws_lane) * Lane::kStride + (lane_id & 31);
     i = grp.stage;
-    wk[0] = K.Wk[i][0];
-    wk[1] = K.Wk[i][1];
+    const double c2 = 2.0 * B.drag;
+    wk[0] = fma(c2, K.Vk[i][0], K.Wk[i][0]);
+    wk[1] = fma(c2, K.Vk[i][1], K.Wk[i][1]);
 #pragma unroll
     for (int j = 0; j < S; ++j) {
-      wu_row[j] = K.Wu[i][j];
-      wu_col[j] = K.Wu[j][i];
+      wu_row[j] = fma(c2, K.Vu[i][j], K.Wu[i][j]);
+      wu_col[j] = fma(c2, K.Vu[j][i], K.Wu[j][i]);
       ps_row[j] = K.Ps[i][j];
     }
   }
@@ -249,6 +254,7 @@ struct Ctx {
       link_fk(l, p >= 0 ? Pc : nullptr, q3, Tc, Jr);
       store12(L.T + 12 * l, Tp);
       store12(L.G + 12 * l, Tc);
+      if (S == 1 && commit && B.tk) store12(L.tk + 12 * l, Tc);
       double C[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) C[k] = fma(wk[0], Tp[k], wk[1] * Tc[k]);
@@ -410,14 +416,30 @@ struct Ctx {
       mul_mass(A, M, G);
       const double mc4[4] = {M.s[6], M.s[7], M.s[8], M.s[9]};
       if (S == 1) {
-        // Eq. EQ: tr(D M D^T)/(2 dt^2) with D = dt^2 A, and -g.(T [mc; m])
-        double ek = 0.0, eg = 0.0;
+        // Eq. EQ: tr(D M D^T)/(2 dt^2) with D = dt^2 A_kin, the drag potential
+        // c tr(D' M D'^T)/dt^2 with D' = dt^2 V, V = (T - T(q_cur))/dt^2, and
+        // -g.(T [mc; m]). A holds the seed's A_kin + 2c V and G = A M.
+        double ek = 0.0, eg = 0.0, ed = 0.0;
+        if (B.drag != 0.0) {
+          double Tk[12], Vd[12], VM[12];
+          load12(L.tk + 12 * l, Tk);
 #pragma unroll
-        for (int k = 0; k < 12; ++k) ek = fma(A[k], G[k], ek);
+          for (int k = 0; k < 12; ++k) Vd[k] = fma(K.Vu[0][0], T[k], K.Vk[0][1] * Tk[k]);
+          mul_mass(Vd, M, VM);
+          const double c2 = 2.0 * B.drag;
+#pragma unroll
+          for (int k = 0; k < 12; ++k) {
+            ek = fma(fma(-c2, Vd[k], A[k]), fma(-c2, VM[k], G[k]), ek);
+            ed = fma(Vd[k], VM[k], ed);
+          }
+        } else {
+#pragma unroll
+          for (int k = 0; k < 12; ++k) ek = fma(A[k], G[k], ek);
+        }
 #pragma unroll
         for (int r = 0; r < 3; ++r)
           eg = fma(B.g[r], fma(T[4 * r], mc4[0], fma(T[4 * r + 1], mc4[1], fma(T[4 * r + 2], mc4[2], T[4 * r + 3] * mc4[3]))), eg);
-        Eown += 0.5 * dt2 * ek - eg;
+        Eown += 0.5 * dt2 * ek + B.drag * dt2 * ed - eg;
       }
 #pragma unroll
       for (int r = 0; r < 3; ++r)
@@ -879,7 +901,7 @@ struct Ctx {
       for (int k = 0; k < 12; ++k) Bs[k] = 0.0;
 #pragma unroll
       for (int s = 0; s < S; ++s) {
-        const double wgt = K.Wk[s][j];
+        const double wgt = fma(2.0 * B.drag, K.Vk[s][j], K.Wk[s][j]);  // seed weight incl. drag
 #pragma unroll
         for (int k = 0; k < 12; ++k) Bs[k] = fma(wgt, grp.from_full(Td[k], s), Bs[k]);
       }

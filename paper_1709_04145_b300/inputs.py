@@ -255,6 +255,20 @@ def uneven_batch(seed_base: int = 3000, n_steps: int = 10):
                 solvers=("newton", "lbfgs", "lbfgs"), n_steps=n_steps, tol=1e-8)
 
 
+def swimmers(count: int = 4096, n_links: int = 4, seed_base: int = 6000, n_steps: int = 20,
+             drag: float = 0.5):
+    """Swimmer-like chains for the drag potential (Section 6.2): chains of
+    n_links hinge rods (L = 1, m = 1) with a fixed root, immersed (no
+    gravity: buoyancy cancels it), drag coefficient c per unit mass, dt = 0.05
+    (the paper's swimmer step), one stage (Eq. EQ), L-BFGS history 8; poses
+    U[-pi/4, pi/4], joint velocities N(0, 1)."""
+    spec = rod_chain(count, n_links, name=f"swimmer{n_links}")
+    spec.gravity = np.zeros(3)
+    q0, qd0 = random_state(spec, seed_base + 1, pose_scale=np.pi / 4, vel_sigma=1.0)
+    return dict(spec=spec, q0=q0, qd0=qd0, dt=0.05, stages=1, history=8, tol=1e-10,
+                n_steps=n_steps, drag=drag, solver="lbfgs")
+
+
 def humanoid_adjoint(count: int = 1024, seed_base: int = 4000, n_steps: int = 64):
     """Differentiation workload: humanoids, 64 steps at dt = 0.033 with two
     stages; loss = squared distance of the end effector (tip of limb 1's last
