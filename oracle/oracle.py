@@ -18,7 +18,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "pbad_oracle.c")
 _LIB = os.path.join(_HERE, "libpbad_oracle.so")
 
-HINGE, BALL = 0, 1
+HINGE, BALL, TRANSLATION = 0, 1, 2
 STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE"}
 
 

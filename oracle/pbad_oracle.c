@@ -13,7 +13,10 @@
  *   - links l = 0..N-1, parent[l] < l or -1 (world); link frame origin at its
  *     joint; T_l = T_parent(l) * X_l * Jm_l(q_l) with X_l the rest transform
  *     (3x4 row-major) and Jm_l the joint rotation (hinge: Rodrigues about a
- *     unit axis; ball: exponential map of a 3-vector).
+ *     unit axis; ball: exponential map of a 3-vector; translation: Jm =
+ *     [I | q], three prismatic coordinates along the frame axes - with a ball
+ *     joint on a child at the same origin it gives the free 6-DOF root of
+ *     Section 6.2's swimmer and spider).
  *   - mass moment M_l = int rho [p;1][p;1]^T dp over the link (4x4 symmetric),
  *     given by 10 numbers Sxx,Sxy,Sxz,Syy,Syz,Szz,mcx,mcy,mcz,m.
  *   - gravity potential Q = -rho g.P; generalised joint torques tau do work
@@ -77,7 +80,7 @@ void *om_model_new(int n_links, const int *parent, const int *jtype,
   m->path = (int *)malloc(sizeof(int) * N * N);
   int off = 0;
   for (int l = 0; l < N; ++l) {
-    if (parent[l] >= l || parent[l] < -1 || (jtype[l] != 0 && jtype[l] != 1)) {
+    if (parent[l] >= l || parent[l] < -1 || jtype[l] < 0 || jtype[l] > 2) {
       om_model_free(m);
       return NULL;
     }
@@ -306,8 +309,15 @@ void om_joint_ddrot(int type, const double *axis, const double *q, int k,
 static void joint_factor(const om_model *m, int a, const double *q, double *F) {
   double X[16], R[9], J[16];
   rest4(m->rest + 12 * a, X);
-  om_joint_rot(m->jtype[a], m->axis + 3 * a, q + m->dof_off[a], R);
-  rot4(R, 1.0, J);
+  if (m->jtype[a] == 2) {
+    /* translation: Jm = [I | q] */
+    const double *t = q + m->dof_off[a];
+    m4_eye(J);
+    J[3] = t[0]; J[7] = t[1]; J[11] = t[2];
+  } else {
+    om_joint_rot(m->jtype[a], m->axis + 3 * a, q + m->dof_off[a], R);
+    rot4(R, 1.0, J);
+  }
   m4_mul(X, J, F);
 }
 /* X_a * dJm_a/dq_k (bottom row zero). */
@@ -315,14 +325,25 @@ static void joint_factor_d(const om_model *m, int a, const double *q, int k,
                            double *F) {
   double X[16], R[9], J[16];
   rest4(m->rest + 12 * a, X);
-  om_joint_drot(m->jtype[a], m->axis + 3 * a, q + m->dof_off[a], k, R);
-  rot4(R, 0.0, J);
+  if (m->jtype[a] == 2) {
+    /* dJm/dq_k = e_k in the translation column */
+    for (int i = 0; i < 16; ++i) J[i] = 0.0;
+    J[4 * k + 3] = 1.0;
+  } else {
+    om_joint_drot(m->jtype[a], m->axis + 3 * a, q + m->dof_off[a], k, R);
+    rot4(R, 0.0, J);
+  }
   m4_mul(X, J, F);
 }
 static void joint_factor_dd(const om_model *m, int a, const double *q, int k,
                             int kk, double *F) {
   double X[16], R[9], J[16];
   rest4(m->rest + 12 * a, X);
+  if (m->jtype[a] == 2) {
+    /* Jm is affine in q: no second derivative */
+    for (int i = 0; i < 16; ++i) F[i] = 0.0;
+    return;
+  }
   om_joint_ddrot(m->jtype[a], m->axis + 3 * a, q + m->dof_off[a], k, kk, R);
   rot4(R, 0.0, J);
   m4_mul(X, J, F);

@@ -24,6 +24,7 @@ import numpy as np
 
 HINGE = 0
 BALL = 1
+TRANSLATION = 2  # three prismatic coordinates along the joint frame's axes
 ROD = 0
 CAPSULE = 1
 
@@ -36,7 +37,7 @@ class BodySpec:
 
     Attributes (N links, B = count instances):
         parent:   (N,) int32, parent[l] < l, -1 = world.
-        jtype:    (N,) int32, 0 hinge / 1 ball.
+        jtype:    (N,) int32, 0 hinge / 1 ball / 2 translation.
         axis:     (N, 3) hinge axes in the joint frame (ignored for balls).
         rest_rot: (N, 3, 3) rotation of the joint frame in the parent frame.
         attach:   (B, N, 3) joint position in the parent link frame.
@@ -69,13 +70,13 @@ class BodySpec:
 
     @property
     def n_dof(self) -> int:
-        return int(np.sum(np.where(self.jtype == BALL, 3, 1)))
+        return int(np.sum(np.where(self.jtype == HINGE, 1, 3)))
 
     def dof_slices(self):
         off = 0
         out = []
         for t in self.jtype:
-            k = 3 if t == BALL else 1
+            k = 1 if t == HINGE else 3
             out.append(slice(off, off + k))
             off += k
         return out
@@ -265,6 +266,40 @@ def swimmers(count: int = 4096, n_links: int = 4, seed_base: int = 6000, n_steps
     spec = rod_chain(count, n_links, name=f"swimmer{n_links}")
     spec.gravity = np.zeros(3)
     q0, qd0 = random_state(spec, seed_base + 1, pose_scale=np.pi / 4, vel_sigma=1.0)
+    return dict(spec=spec, q0=q0, qd0=qd0, dt=0.05, stages=1, history=8, tol=1e-10,
+                n_steps=n_steps, drag=drag, solver="lbfgs")
+
+
+def free_chain(count: int, n_links: int, length: float = 1.0, mass: float = 1.0,
+               name: str = "") -> BodySpec:
+    """Chain of n_links uniform rods whose root moves freely: a massless
+    link 0 with a translation joint at the world origin, then the first rod
+    on a ball joint at the same point (the 6-DOF rigid root of Section 6.2's
+    swimmer), then n_links - 1 rods on hinge joints (axis local +y). n_links
+    + 1 links in the model, 6 + (n_links - 1) DOFs."""
+    N = n_links + 1
+    parent = np.arange(-1, N - 1, dtype=np.int32)
+    jtype = np.array([TRANSLATION, BALL] + [HINGE] * (n_links - 1), np.int32)
+    axis = np.tile(np.array([0.0, 1.0, 0.0]), (N, 1))
+    rest_rot = np.tile(np.eye(3), (N, 1, 1))
+    L = np.full((count, N), float(length))
+    M = np.full((count, N), float(mass))
+    L[:, 0] = 0.0
+    M[:, 0] = 0.0
+    return BodySpec(parent, jtype, axis, rest_rot, _chain_attach(L), L, M, np.zeros((count, N)),
+                    np.full(N, ROD, np.int32), name=name or f"free_chain{n_links}")
+
+
+def swimmers_free(count: int = 4096, seed_base: int = 6100, n_steps: int = 20, drag: float = 0.5):
+    """Section 6.2's swimmer body: a 4-link chain with a free 6-DOF root and
+    3 hinge joints (9 DOFs), immersed (no gravity), drag c per unit mass,
+    dt = 0.05, one stage, L-BFGS history 8; root at the origin with random
+    orientation U[-pi/4, pi/4] per exp-map coordinate, hinge angles
+    U[-pi/4, pi/4], velocities N(0, 1) per coordinate."""
+    spec = free_chain(count, 4, name="swimmer_free4")
+    spec.gravity = np.zeros(3)
+    q0, qd0 = random_state(spec, seed_base + 1, pose_scale=np.pi / 4, vel_sigma=1.0)
+    q0[:, 0:3] = 0.0  # root position at the origin
     return dict(spec=spec, q0=q0, qd0=qd0, dt=0.05, stages=1, history=8, tol=1e-10,
                 n_steps=n_steps, drag=drag, solver="lbfgs")
 
