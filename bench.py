@@ -460,7 +460,8 @@ def measure_uneven(P, args, dev):
 
 def measure_drag(P, args, dev):
     """Drag potential (Section 6.2): swimmer-like chains (4096 x 4 hinge rods,
-    no gravity, c = 0.5, dt = 0.05, one stage, L-BFGS) over args.drag_steps
+    no gravity, c = 0.5, dt = 0.05, one stage, L-BFGS) and the swimmer body
+    on a free 6-DOF root (4096 x 4 links, 9 DOFs) over args.drag_steps
     steps, and the main ball-chain batch with c = 0.5 against the same batch
     without drag over 5 steps (the drag only changes seed weights there)."""
     import torch
@@ -481,6 +482,24 @@ def measure_drag(P, args, dev):
                        "stages": S, "drag": w["drag"], "tol": w["tol"],
                        "converged_fraction": float((st == 0).mean()),
                        "iters_per_step": float(res["iters"].float().mean().item() / T)}
+    # Section 6.2's swimmer body: 4 links on a free 6-DOF root (9 DOFs)
+    w = I.swimmers_free(n_steps=args.drag_steps)
+    spec, S, dt, m = w["spec"], w["stages"], w["dt"], w["history"]
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index, drag=w["drag"])], max_stages=S,
+                    max_history=m)
+    qp, qc = _state_tensors(P, [(w["q0"], w["qd0"])], S, dt, dev)
+    T = w["n_steps"]
+    run = lambda: P.rollout(batch, qp, qc, None, T, dt, S, P.LBFGS, m, w["tol"], 200, want_traj=False)
+    run()
+    ms, res = _timed(run)
+    st = res["status"].cpu().numpy()
+    bodies = spec.n_links - 1  # the root's massless carrier link is not a body
+    out["swimmers_free_root"] = {"value": spec.count * bodies * T / (ms / 1e3), "unit": UNIT,
+                                 "ms": ms, "instances": spec.count, "links": bodies,
+                                 "dofs": spec.n_dof, "timesteps": T, "dt": dt, "stages": S,
+                                 "drag": w["drag"], "tol": w["tol"],
+                                 "converged_fraction": float((st == 0).mean()),
+                                 "iters_per_step": float(res["iters"].float().mean().item() / T)}
     wb = I.ball_chains(count=args.instances, n_links=args.links, n_steps=5)
     spec = wb["spec"]
     S, dt, m = wb["stages"], wb["dt"], wb["history"]

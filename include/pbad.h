@@ -67,6 +67,10 @@ extern "C" {
 
 #define PBAD_HINGE 0
 #define PBAD_BALL 1
+/* Three prismatic coordinates along the joint frame's axes, J = [I | q]. A
+ * massless link on a translation joint carrying a body on a ball joint at
+ * the same origin is a free 6-DOF root (Section 6.2's swimmer and spider). */
+#define PBAD_TRANSLATION 2
 
 #define PBAD_LBFGS 0
 #define PBAD_NEWTON 1
@@ -100,9 +104,9 @@ PBAD_API const char* pbad_last_error(void);
 PBAD_API int pbad_colloc(int32_t stages, double* nodes, double* W);
 
 /* Creates a model (one topology, `count` instances) on CUDA device `device`.
- *   parent[n_links], joint_type[n_links] (PBAD_HINGE/PBAD_BALL),
- *   axis[n_links][3] (hinge axes in the joint frame, unit length; ignored for
- *   balls), mass_moment[count][n_links][10] = Sxx Sxy Sxz Syy Syz Szz mcx mcy
+ *   parent[n_links], joint_type[n_links] (PBAD_HINGE/PBAD_BALL/
+ *   PBAD_TRANSLATION), axis[n_links][3] (hinge axes in the joint frame, unit
+ *   length; ignored for the other types), mass_moment[count][n_links][10] = Sxx Sxy Sxz Syy Syz Szz mcx mcy
  *   mcz m of int rho [p;1][p;1]^T dp in the link frame (Eq. ATOM),
  *   rest[count][n_links][12] (3x4 row-major), gravity[3].
  * All host pointers, copied. Errors: PBAD_ERR_ARG for a malformed tree,

@@ -417,7 +417,8 @@ int pbad_model_create(int32_t n_links, const int32_t* parent, const int32_t* joi
       delete m;
       return fail(PBAD_ERR_ARG, "parent[l] must be in -1..l-1");
     }
-    if (joint_type[l] != PBAD_HINGE && joint_type[l] != PBAD_BALL) {
+    if (joint_type[l] != PBAD_HINGE && joint_type[l] != PBAD_BALL &&
+        joint_type[l] != PBAD_TRANSLATION) {
       delete m;
       return fail(PBAD_ERR_ARG, "unknown joint type");
     }

@@ -89,6 +89,29 @@ __device__ __forceinline__ double dot3(const double* a, const double* b) {
   return fma(a[0], b[0], fma(a[1], b[1], a[2] * b[2]));
 }
 
+// Joint types: 0 hinge (1 DOF), 1 ball (3, exponential map), 2 translation
+// (3 prismatic coordinates along the joint frame's axes; with a ball joint on
+// a child at the same origin it forms a free 6-DOF root).
+constexpr int kHinge = 0, kBall = 1, kTranslation = 2;
+
+// World twist (angular; linear at the world origin) of a unit rate of a DOF
+// with world axis w at origin o: rotation (w, o x w), translation (0, w).
+__device__ __forceinline__ void add_twist(int jt, const double* o, const double* w, double vk,
+                                          double* V) {
+  if (jt == kTranslation) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) V[3 + c] = fma(vk, w[c], V[3 + c]);
+  } else {
+    double ow[3];
+    cross(o, w, ow);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      V[c] = fma(vk, w[c], V[c]);
+      V[3 + c] = fma(vk, ow[c], V[3 + c]);
+    }
+  }
+}
+
 // R = c0 I + c1 [v]x + c2 v v^T (Rodrigues form shared by hinges and the
 // exponential map).
 __device__ __forceinline__ void rodrigues(const double* v, double c0, double c1, double c2, double* R) {
@@ -175,6 +198,13 @@ __device__ __forceinline__ void joint_rotation(int jt, const double* u, const do
     double s, c;
     sincos(q[0], &s, &c);
     rodrigues(u, c, s, 1.0 - c, R);
+  } else if (jt == 2) {
+    // translation joint: no rotation; its three axes are the frame's own
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+      R[k] = (k % 4 == 0) ? 1.0 : 0.0;
+      Jr[k] = R[k];
+    }
   } else {
     const double x = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
     const ExpCoef e = ec ? exp_coef<true>(x) : exp_coef<false>(x);

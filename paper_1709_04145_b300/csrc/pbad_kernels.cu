@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(128) k_link_points(const __grid_constant__ Lau
                              ws[L.axes + 9 * a + 3 * k + 2]};
         double v[3];
         cross(w, rel, v);
-        for (int r = 0; r < 3; ++r) Jp[r * n + d0 + k] = v[r];
+        for (int r = 0; r < 3; ++r) Jp[r * n + d0 + k] = B.jtype[a] == kTranslation ? w[r] : v[r];
       }
     }
   }

@@ -173,19 +173,25 @@ struct Ctx {
     for (int k = 0; k < 12; ++k) ws[off + k] = v[k];
   }
 
-  // T_l = T_parent * X_l * Rot(q_l). Ball joints also return Jr(q_l).
+  // T_l = T_parent * X_l * J(q_l), J = [Rot(q_l) | 0] or, for a translation
+  // joint, [I | q_l]. Ball joints also return Jr(q_l) (translation: I).
   __device__ __forceinline__ void link_fk(int l, const double* Tp, const double* ql, double* T,
                                           double* Jr, ExpCoef* ec = nullptr) const {
     double R[9], XJ[12];
+    const int jt = B.jtype[l];
     const double u[3] = {B.axis[3 * l], B.axis[3 * l + 1], B.axis[3 * l + 2]};
-    joint_rotation(B.jtype[l], u, ql, R, Jr, ec);
+    joint_rotation(jt, u, ql, R, Jr, ec);
     if (B.rest_eye[l]) {
-      // identity rest rotation: X_l Rot = [Rot | t_X]
+      // identity rest rotation: X_l J = [Rot | t_X] (translation: [I | t_X + q])
 #pragma unroll
       for (int r = 0; r < 3; ++r) {
 #pragma unroll
         for (int c = 0; c < 3; ++c) XJ[4 * r + c] = R[3 * r + c];
         XJ[4 * r + 3] = rest(l, 4 * r + 3);
+      }
+      if (jt == kTranslation) {  // uniform across the warp (same link on every lane)
+#pragma unroll
+        for (int r = 0; r < 3; ++r) XJ[4 * r + 3] += ql[r];
       }
     } else {
       double X[12];
@@ -197,6 +203,11 @@ struct Ctx {
         for (int c = 0; c < 3; ++c)
           XJ[4 * r + c] = fma(X[4 * r], R[c], fma(X[4 * r + 1], R[3 + c], X[4 * r + 2] * R[6 + c]));
         XJ[4 * r + 3] = X[4 * r + 3];
+      }
+      if (jt == kTranslation) {
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+          XJ[4 * r + 3] = fma(X[4 * r], ql[0], fma(X[4 * r + 1], ql[1], fma(X[4 * r + 2], ql[2], X[4 * r + 3])));
       }
     }
     if (Tp) compose(Tp, XJ, T);
@@ -299,11 +310,11 @@ struct Ctx {
     for (int l = 0; l < N; ++l) {
       double T[12], Jr[9], w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, q[3];
       load12(L.G + 12 * l, T);
-      const int nd = ndof(l), d0 = B.dof[l];
+      const int nd = ndof(l), d0 = B.dof[l], jt = B.jtype[l];
       if (nd == 3) {
         for (int k = 0; k < 3; ++k) q[k] = ws[L.qc + d0 + k];
         double R[9];
-        joint_rotation(1, nullptr, q, R, Jr);
+        joint_rotation(jt, nullptr, q, R, Jr);
       }
       link_axes(l, T, Jr, w);
       double c[10];
@@ -332,7 +343,9 @@ struct Ctx {
           for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int q_ = 0; q_ < 3; ++q_) s += w[3 * a + r] * Io[3 * r + q_] * w[3 * bb + q_];
-          Bj[3 * a + bb] = s;  // hinge: only Bj[0] is used (w[0..2] is its axis)
+          // translation: the subtree mass along orthonormal axes
+          Bj[3 * a + bb] = jt == kTranslation ? (a == bb ? c[9] : 0.0) : s;
+          // (hinge: only Bj[0] is used, w[0..2] being its axis)
         }
       if (nd == 1) {
         Pj[0] = 1.0 / Bj[0];
@@ -390,8 +403,9 @@ struct Ctx {
       for (int k = 0; k < 3; ++k)
         if (k < nd) q3[k] = ws[L.xt + d0 + k];
       ExpCoef ec;
-      link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr, nd == 3 ? &ec : nullptr);
-      if (nd == 3) {  // cached for the tangent passes at this point
+      const int jt = B.jtype[l];
+      link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr, jt == kBall ? &ec : nullptr);
+      if (jt == kBall) {  // cached for the tangent passes at this point
         ws[L.ec + 4 * l] = ec.b;
         ws[L.ec + 4 * l + 1] = ec.h;
         ws[L.ec + 4 * l + 2] = ec.db;
@@ -463,11 +477,14 @@ struct Ctx {
       double of[3];
       cross(o, a + 3, of);
       const double mo[3] = {a[0] - of[0], a[1] - of[1], a[2] - of[2]};
+      // rotation: axis . moment about the joint; translation: axis . force
+      const bool tr = B.jtype[l] == kTranslation;
+      const double load[3] = {tr ? a[3] : mo[0], tr ? a[4] : mo[1], tr ? a[5] : mo[2]};
       for (int k = 0; k < nd; ++k) {
         const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
                              ws[L.axes + 9 * l + 3 * k + 2]};
         const double tk = tau ? tau[gdof(d0 + k)] : 0.0;
-        const double rk = dot3(w, mo) - tk;
+        const double rk = dot3(w, load) - tk;
         ws[L.rt + d0 + k] = rk;
         rr = fma(rk, rk, rr);
         tq = fma(tk, ws[L.xt + d0 + k], tq);
@@ -519,13 +536,7 @@ struct Ctx {
       for (int k = 0; k < nd; ++k) {
         const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
                              ws[L.axes + 9 * l + 3 * k + 2]};
-        const double vk = ws[dir + d0 + k];
-        double ow[3];
-        cross(o, w, ow);
-        for (int c = 0; c < 3; ++c) {
-          V[c] = fma(vk, w[c], V[c]);
-          V[3 + c] = fma(vk, ow[c], V[3 + c]);
-        }
+        add_twist(B.jtype[l], o, w, ws[dir + d0 + k], V);
       }
       for (int k = 0; k < 6; ++k) ws[L.V + 6 * l + k] = V[k];
       // Tdot = [w]x T + v at the world origin
@@ -571,14 +582,17 @@ struct Ctx {
       for (int k = 0; k < 6; ++k) ad[k] = ws[L.accd + 6 * l + k] + carry[k];
       load12(L.T + 12 * l, T);
       const double o[3] = {T[3], T[7], T[11]};
+      const int jt = B.jtype[l];
       if (MODE == kGn) {
         double t3[3];
         cross(o, ad + 3, t3);
         const double mdo[3] = {ad[0] - t3[0], ad[1] - t3[1], ad[2] - t3[2]};
+        const bool tr = jt == kTranslation;
+        const double load[3] = {tr ? ad[3] : mdo[0], tr ? ad[4] : mdo[1], tr ? ad[5] : mdo[2]};
         for (int k = 0; k < nd; ++k) {
           const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
                                ws[L.axes + 9 * l + 3 * k + 2]};
-          ws[out + d0 + k] = scale * dot3(w, mdo);
+          ws[out + d0 + k] = scale * dot3(w, load);
         }
       } else {
         double a[6], V[6];
@@ -598,7 +612,7 @@ struct Ctx {
         cross(o, ad + 3, t3);
         const double mdo[3] = {ad[0] - t2[0] - t3[0], ad[1] - t2[1] - t3[1], ad[2] - t2[2] - t3[2]};
         double dJ[9];
-        if (nd == 3) {
+        if (jt == kBall) {
           double th[3], v[3], bh[4];
           for (int k = 0; k < 3; ++k) {
             th[k] = ws[L.xt + d0 + k];
@@ -614,13 +628,16 @@ struct Ctx {
                                ws[L.axes + 9 * l + 3 * k + 2]};
           double wd[3];
           cross(V, w, wd);
-          if (nd == 3) {
+          if (jt == kBall) {
             // + R dJr e_k
 #pragma unroll
             for (int r = 0; r < 3; ++r)
               wd[r] += fma(T[4 * r], dJ[k], fma(T[4 * r + 1], dJ[3 + k], T[4 * r + 2] * dJ[6 + k]));
           }
-          ws[out + d0 + k] = scale * (dot3(wd, mo) + dot3(w, mdo));
+          // rotation: d/de [w . (M - o x F)]; translation: d/de [w . F]
+          // (jt is uniform across the warp: every lane is at link l)
+          if (jt == kTranslation) ws[out + d0 + k] = scale * (dot3(wd, a + 3) + dot3(w, ad + 3));
+          else ws[out + d0 + k] = scale * (dot3(wd, mo) + dot3(w, mdo));
         }
       }
       if (chain) {
@@ -853,13 +870,7 @@ struct Ctx {
       for (int k = 0; k < nd; ++k) {
         const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
                              ws[L.axes + 9 * l + 3 * k + 2]};
-        const double vk = ws[dir + d0 + k];
-        double ow[3];
-        cross(o, w, ow);
-        for (int c = 0; c < 3; ++c) {
-          V[c] = fma(vk, w[c], V[c]);
-          V[3 + c] = fma(vk, ow[c], V[3 + c]);
-        }
+        add_twist(B.jtype[l], o, w, ws[dir + d0 + k], V);
       }
       for (int k = 0; k < 6; ++k) ws[L.V + 6 * l + k] = V[k];
       double Td[12];
@@ -919,10 +930,12 @@ struct Ctx {
       double of[3];
       cross(o, a + 3, of);
       const double mo[3] = {a[0] - of[0], a[1] - of[1], a[2] - of[2]};
+      const bool tr = B.jtype[l] == kTranslation;
+      const double load[3] = {tr ? a[3] : mo[0], tr ? a[4] : mo[1], tr ? a[5] : mo[2]};
       for (int k = 0; k < nd; ++k) {
         const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
                              ws[L.axes + 9 * l + 3 * k + 2]};
-        ws[out + d0 + k] = dot3(w, mo);
+        ws[out + d0 + k] = dot3(w, load);
       }
       if (p >= 0)
         for (int k = 0; k < 6; ++k) ws[L.acc + 6 * p + k] += a[k];
