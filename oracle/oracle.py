@@ -59,6 +59,8 @@ def lib():
         L.om_colloc.argtypes = [C.c_int, dp, dp]
         L.om_colloc_vel.argtypes = [C.c_int, dp]
         L.om_model_set_drag.argtypes = [vp, C.c_double]
+        L.om_model_set_contact.argtypes = [vp, C.c_int, ip, dp, C.c_double, C.c_double,
+                                           C.c_double]
         L.om_mass_moment_rod.argtypes = [C.c_double, C.c_double, dp]
         L.om_mass_moment_capsule.argtypes = [C.c_double, C.c_double, C.c_double, dp]
         L.om_hmass.argtypes = [vp, dp, dp]
@@ -180,7 +182,8 @@ def rest_from_spec(spec, b: int) -> np.ndarray:
 class OracleModel:
     """One articulated body (one instance) in the oracle."""
 
-    def __init__(self, parent, jtype, axis, mm, rest, gravity, drag: float = 0.0):
+    def __init__(self, parent, jtype, axis, mm, rest, gravity, drag: float = 0.0,
+                 contact=None):
         self.parent, pp = _i(parent)
         self.jtype, jp = _i(jtype)
         self.axis, ap = _d(np.asarray(axis).reshape(-1, 3))
@@ -195,11 +198,23 @@ class OracleModel:
         self.n_dof = lib().om_n_dof(self._h)
         self.drag = float(drag)
         lib().om_model_set_drag(self._h, self.drag)
+        if contact is not None:
+            self.set_contact(**contact)
+
+    def set_contact(self, link, point, z0=0.0, d1=0.0, d2=0.0):
+        """Eq. FRI penalty contact against the ground z < z0 at body points
+        point[k] (link frame) of link[k]; one stage only."""
+        lk, lp = _i(np.asarray(link).reshape(-1))
+        pt, pp = _d(np.asarray(point, dtype=np.float64).reshape(-1, 3))
+        if lib().om_model_set_contact(self._h, int(lk.shape[0]), lp, pp, float(z0), float(d1),
+                                      float(d2)) != 0:
+            raise ValueError("contact link out of range")
+        self._contact = (lk, pt)
 
     @classmethod
-    def from_spec(cls, spec, b: int = 0, drag: float = 0.0):
+    def from_spec(cls, spec, b: int = 0, drag: float = 0.0, contact=None):
         return cls(spec.parent, spec.jtype, spec.axis, mass_moments_from_spec(spec, b),
-                   rest_from_spec(spec, b), spec.gravity, drag)
+                   rest_from_spec(spec, b), spec.gravity, drag, contact)
 
     def __del__(self):
         h = getattr(self, "_h", None)

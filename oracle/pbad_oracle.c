@@ -49,6 +49,11 @@ typedef struct {
   double *rest; /* [N][12] */
   double g[3];
   double drag;   /* drag coefficient c of Q_drag (0 = none), see om_model_set_drag */
+  /* penalty contact of Eq. FRI against the ground plane z = c_z0 */
+  int n_contact;
+  int *c_link;      /* [n_contact] */
+  double *c_point;  /* [n_contact][3] in the link frame */
+  double c_z0, c_d1, c_d2;
   int *path_len; /* number of joints from the root to l, inclusive */
   int *path;     /* [N][N]: path[l*N + k] = k-th joint on the root->l path */
 } om_model;
@@ -57,6 +62,7 @@ void om_model_free(void *p) {
   om_model *m = (om_model *)p;
   if (!m) return;
   free(m->parent); free(m->jtype); free(m->dof_off); free(m->ndof);
+  free(m->c_link); free(m->c_point);
   free(m->axis); free(m->mm); free(m->rest); free(m->path_len); free(m->path);
   free(m);
 }
@@ -115,6 +121,64 @@ int om_n_dof(void *p) { return ((om_model *)p)->n_dof; }
  * collocation polynomial at the stage node (first-derivative weights of
  * om_colloc_vel). */
 void om_model_set_drag(void *p, double c) { ((om_model *)p)->drag = c; }
+
+/* Penalty frictional contact of Eq. FRI (Section 6.2, spider) against the
+ * ground: obstacle = half-space z < z0, penetration depth d(P) = max(0, z0 -
+ * P_z), tangential projection = the xy components. Over a set of body
+ * points (the integral replaced by a sum over discrete contact points):
+ *   Q_contact = sum_p D1 d(P_p)^2 + D2 d(P_p)^2 |Pi (P_p(q_{k+1}) - P_p(q_k))/dt|^2
+ * with P_p = T_l(q) [p; 1]. Added to Eq. EQ (one stage); the oracle does not
+ * define it for S >= 2. Returns -1 on a bad link index. */
+int om_model_set_contact(void *p, int n, const int *link, const double *point, double z0,
+                         double d1, double d2) {
+  om_model *m = (om_model *)p;
+  for (int k = 0; k < n; ++k)
+    if (link[k] < 0 || link[k] >= m->n_links) return -1;
+  free(m->c_link); free(m->c_point);
+  m->c_link = NULL; m->c_point = NULL;
+  m->n_contact = n;
+  if (n > 0) {
+    m->c_link = (int *)malloc(sizeof(int) * n);
+    m->c_point = (double *)malloc(sizeof(double) * 3 * n);
+    for (int k = 0; k < n; ++k) {
+      m->c_link[k] = link[k];
+      for (int c = 0; c < 3; ++c) m->c_point[3 * k + c] = point[3 * k + c];
+    }
+  }
+  m->c_z0 = z0; m->c_d1 = d1; m->c_d2 = d2;
+  return 0;
+}
+
+/* One contact point at world position P (from q_{k+1}) and Pk (from q_k):
+ * Q, f = dQ/dP, H = d2Q/dP2 and Hk = d2Q/dP dPk (3x3 row-major, rows = the
+ * components of f). Returns 0 when the point is outside the obstacle. */
+static int contact_point(const om_model *m, double dt, const double *P, const double *Pk,
+                         double *Q, double *f, double *H, double *Hk) {
+  double d = m->c_z0 - P[2];
+  if (!(d > 0.0)) return 0;
+  double D1 = m->c_d1, D2 = m->c_d2;
+  double vx = (P[0] - Pk[0]) / dt, vy = (P[1] - Pk[1]) / dt;
+  double s = vx * vx + vy * vy;
+  *Q = D1 * d * d + D2 * d * d * s;
+  f[0] = 2 * D2 * d * d * vx / dt;
+  f[1] = 2 * D2 * d * d * vy / dt;
+  f[2] = -2 * d * (D1 + D2 * s);
+  for (int k = 0; k < 9; ++k) { H[k] = 0; Hk[k] = 0; }
+  H[0] = H[4] = 2 * D2 * d * d / (dt * dt);
+  H[2] = H[6] = -4 * D2 * d * vx / dt;   /* d f_x/d P_z, d f_z/d P_x */
+  H[5] = H[7] = -4 * D2 * d * vy / dt;
+  H[8] = 2 * (D1 + D2 * s);
+  Hk[0] = Hk[4] = -2 * D2 * d * d / (dt * dt);
+  Hk[6] = 4 * D2 * d * vx / dt;          /* d f_z/d Pk_x */
+  Hk[7] = 4 * D2 * d * vy / dt;
+  return 1;
+}
+
+/* body point of link l: P = T_l [p; 1] (T row-major 4x4) */
+static void point_world(const double *T, const double *pt, double *P) {
+  for (int r = 0; r < 3; ++r)
+    P[r] = T[4 * r] * pt[0] + T[4 * r + 1] * pt[1] + T[4 * r + 2] * pt[2] + T[4 * r + 3];
+}
 
 /* ------------------------------------------------------------------ */
 /* small dense helpers (4x4 row-major homogeneous, 3x3 row-major)      */
@@ -756,6 +820,47 @@ double om_eval(void *p, int S, double dt, const double *qs,
       }
     }
   }
+  if (S == 1 && m->n_contact > 0) {
+    /* Eq. FRI contact points: energy, residual dP/dq . f and, for the
+     * Jacobian, dP/dq^T H dP/dq + d2P/dq2 . f */
+    double *dTl = (double *)malloc(sizeof(double) * 16 * n);
+    double *dP = (double *)malloc(sizeof(double) * 3 * n);
+    double *Hb = needJ ? (double *)calloc((size_t)n * n, sizeof(double)) : NULL;
+    for (int c = 0; c < m->n_contact; ++c) {
+      int l = m->c_link[c];
+      const double *pt = m->c_point + 3 * c;
+      double P[3], Pk[3], Q, f[3], H[9], Hk[9];
+      point_world(T + 16 * N * 2 + 16 * l, pt, P);
+      point_world(T + 16 * N + 16 * l, pt, Pk);
+      if (!contact_point(m, dt, P, Pk, &Q, f, H, Hk)) continue;
+      E += Q;
+      om_link_dT(p, qs, l, dTl);
+      for (int d = 0; d < n; ++d) {
+        point_world(dTl + 16 * d, pt, dP + 3 * d);  /* dP/dq_d = dT_l/dq_d [p; 1] */
+        rr[d] += dP[3 * d] * f[0] + dP[3 * d + 1] * f[1] + dP[3 * d + 2] * f[2];
+      }
+      if (needJ) {
+        for (int d = 0; d < n; ++d)
+          for (int e = 0; e < n; ++e) {
+            double s = 0;
+            for (int a = 0; a < 3; ++a)
+              for (int b = 0; b < 3; ++b) s += dP[3 * d + a] * H[3 * a + b] * dP[3 * e + b];
+            J[d * Sn + e] += s;
+          }
+        double Gc[16] = {0};
+        for (int r = 0; r < 3; ++r) {
+          Gc[4 * r] = f[r] * pt[0]; Gc[4 * r + 1] = f[r] * pt[1];
+          Gc[4 * r + 2] = f[r] * pt[2]; Gc[4 * r + 3] = f[r];
+        }
+        memset(Hb, 0, sizeof(double) * n * n);
+        link_ddT_contract(m, l, qs, Gc, Hb);
+        for (int k = 0; k < n * n; ++k) J[k] += Hb[k];
+      }
+    }
+    free(dTl);
+    free(dP);
+    free(Hb);
+  }
   if (S == 1) {
     for (int d = 0; d < n; ++d) E -= tau[d] * qs[d];
   } else {
@@ -816,7 +921,70 @@ void om_resid_known_jac(void *p, int S, double dt, const double *qs,
       }
     }
   }
+  if (S == 1 && m->n_contact > 0) {
+    /* Eq. FRI: the tangential velocity depends on q_k through P_p(q_k):
+     * dr/dq_cur += dP/dq^T (d2Q/dP dPk) dPk/dq_cur */
+    double *dP = (double *)malloc(sizeof(double) * 3 * n);
+    double *dPk = (double *)malloc(sizeof(double) * 3 * n);
+    double *Tn = (double *)malloc(sizeof(double) * 16 * N);
+    double *Tc = (double *)malloc(sizeof(double) * 16 * N);
+    om_fk(p, qs, Tn);
+    om_fk(p, q_cur, Tc);
+    for (int c = 0; c < m->n_contact; ++c) {
+      int l = m->c_link[c];
+      const double *pt = m->c_point + 3 * c;
+      double P[3], Pk[3], Q, f[3], H[9], Hk[9];
+      point_world(Tn + 16 * l, pt, P);
+      point_world(Tc + 16 * l, pt, Pk);
+      if (!contact_point(m, dt, P, Pk, &Q, f, H, Hk)) continue;
+      om_link_dT(p, qs, l, dTi);
+      om_link_dT(p, q_cur, l, dTc);
+      for (int d = 0; d < n; ++d) {
+        point_world(dTi + 16 * d, pt, dP + 3 * d);
+        point_world(dTc + 16 * d, pt, dPk + 3 * d);
+      }
+      for (int d = 0; d < n; ++d)
+        for (int e = 0; e < n; ++e) {
+          double s = 0;
+          for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) s += dP[3 * d + a] * Hk[3 * a + b] * dPk[3 * e + b];
+          Jc[d * n + e] += s;
+        }
+    }
+    free(dP); free(dPk); free(Tn); free(Tc);
+  }
   free(dTi); free(dTp); free(dTc);
+}
+
+/* H += sum over the active contact points of dP/dq^T (d2Q/dP2) dP/dq at q
+ * (one stage; q_cur gives the tangential velocity). H: n x n. */
+static void contact_gn(om_model *m, double dt, const double *q, const double *q_cur, double *H) {
+  if (m->n_contact == 0) return;
+  int N = m->n_links, n = m->n_dof;
+  double *Tn = (double *)malloc(sizeof(double) * 16 * N);
+  double *Tc = (double *)malloc(sizeof(double) * 16 * N);
+  double *dTl = (double *)malloc(sizeof(double) * 16 * n);
+  double *dP = (double *)malloc(sizeof(double) * 3 * n);
+  om_fk(m, q, Tn);
+  om_fk(m, q_cur, Tc);
+  for (int c = 0; c < m->n_contact; ++c) {
+    int l = m->c_link[c];
+    const double *pt = m->c_point + 3 * c;
+    double P[3], Pk[3], Q, f[3], Hc[9], Hk[9];
+    point_world(Tn + 16 * l, pt, P);
+    point_world(Tc + 16 * l, pt, Pk);
+    if (!contact_point(m, dt, P, Pk, &Q, f, Hc, Hk)) continue;
+    om_link_dT(m, q, l, dTl);
+    for (int d = 0; d < n; ++d) point_world(dTl + 16 * d, pt, dP + 3 * d);
+    for (int d = 0; d < n; ++d)
+      for (int e = 0; e < n; ++e) {
+        double s = 0;
+        for (int a = 0; a < 3; ++a)
+          for (int b = 0; b < 3; ++b) s += dP[3 * d + a] * Hc[3 * a + b] * dP[3 * e + b];
+        H[d * n + e] += s;
+      }
+  }
+  free(Tn); free(Tc); free(dTl); free(dP);
 }
 
 /* ------------------------------------------------------------------ */
@@ -1196,9 +1364,11 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
     if (rn < tol) { status = OM_CONVERGED; break; }
     if (k >= max_iter) { status = OM_MAX_ITER; break; }
     if (S == 1) {
-      /* Gauss-Newton matrix of Eq. EQ (+ Q_drag): (1 + 2 c) H_mass / dt^2 */
+      /* Gauss-Newton matrix of Eq. EQ (+ Q_drag): (1 + 2 c) H_mass / dt^2,
+       * plus sum_p dP/dq^T (d2Q/dP2) dP/dq of the contact points (Eq. FRI) */
       om_hmass(m, x, Hm);
       for (int i = 0; i < Sn * Sn; ++i) H[i] = (1.0 + 2.0 * m->drag) * Hm[i] / (dt * dt);
+      contact_gn(m, dt, x, qc, H);
       for (int i = 0; i < Sn; ++i) gr[i] = r[i];
     } else {
       for (int a = 0; a < Sn; ++a)
