@@ -131,6 +131,22 @@ PBAD_API int pbad_model_info(const pbad_model* model, int32_t* n_links, int32_t*
  * NULL model or a negative or non-finite c. */
 PBAD_API int pbad_model_set_drag(pbad_model* model, double c);
 
+/* Penalty frictional contact of Eq. FRI (Section 6.2, the spider) between
+ * body points of the model and the ground: obstacle = the half-space
+ * z < z0 (world), penetration depth d(P) = max(0, z0 - P_z), tangential
+ * projection = the xy components, the body integral replaced by a sum over
+ * n_points contact points (link[k], point[k][3] in that link's frame, the
+ * same for every instance):
+ *   Q = sum_k d1 d(P_k)^2 + d2 d(P_k)^2 |Pi (P_k(q_{k+1}) - P_k(q_k))/dt|^2,
+ * added to Eq. EQ. Defined for one stage only: a call with stages >= 2 on a
+ * model with contact points returns PBAD_ERR_UNSUPPORTED. n_points = 0
+ * removes the contact. Host pointers, copied to the device. Set it before
+ * creating the batches that use the model (like the drag). Errors:
+ * PBAD_ERR_ARG (NULL model, n_points < 0 or > 65536, link out of range,
+ * negative or non-finite d1/d2), PBAD_ERR_ALLOC. */
+PBAD_API int pbad_model_set_contact(pbad_model* model, int32_t n_points, const int32_t* link,
+                                    const double* point, double z0, double d1, double d2);
+
 /* Creates a batch over 1..PBAD_MAX_MODELS models (same device) and allocates
  * the solver workspace for up to max_stages stages and L-BFGS history
  * max_history; flags = PBAD_BATCH_NEWTON also reserves the dense

@@ -65,7 +65,7 @@ class Model:
     """One topology with ``count`` instances (pbad_model)."""
 
     def __init__(self, parent, jtype, axis, mass_moment, rest, gravity, device: int = 0,
-                 drag: float = 0.0):
+                 drag: float = 0.0, contact: dict | None = None):
         parent = np.ascontiguousarray(parent, dtype=np.int32)
         jtype = np.ascontiguousarray(jtype, dtype=np.int32)
         axis = np.ascontiguousarray(axis, dtype=np.float64).reshape(-1, 3)
@@ -90,13 +90,29 @@ class Model:
         self.drag = float(drag)
         if self.drag != 0.0:
             check(lib().pbad_model_set_drag(h, self.drag), "pbad_model_set_drag")
+        self.contact = None
+        if contact is not None:
+            self.set_contact(**contact)
+
+    def set_contact(self, link, point, z0: float = 0.0, d1: float = 0.0, d2: float = 0.0):
+        """Penalty contact of Eq. FRI against the ground z < z0 at body points
+        point[k] (link frame) of link[k] (one stage only; set before creating
+        batches)."""
+        lk = np.ascontiguousarray(np.asarray(link).reshape(-1), dtype=np.int32)
+        pt = np.ascontiguousarray(np.asarray(point, dtype=np.float64).reshape(-1, 3))
+        check(lib().pbad_model_set_contact(self._h, int(lk.shape[0]), _iptr(lk), _dptr(pt),
+                                           float(z0), float(d1), float(d2)),
+              "pbad_model_set_contact")
+        self.contact = dict(link=lk, point=pt, z0=z0, d1=d1, d2=d2)
 
     @classmethod
-    def from_spec(cls, spec: "inputs.BodySpec", device: int = 0, drag: float = 0.0) -> "Model":
-        """drag: coefficient c of the drag potential (Section 6.2), per unit mass."""
+    def from_spec(cls, spec: "inputs.BodySpec", device: int = 0, drag: float = 0.0,
+                  contact: dict | None = None) -> "Model":
+        """drag: coefficient c of the drag potential (Section 6.2), per unit
+        mass; contact: keyword arguments of set_contact (Eq. FRI)."""
         from .models import mass_moments, rest_transforms
         return cls(spec.parent, spec.jtype, spec.axis, mass_moments(spec), rest_transforms(spec),
-                   spec.gravity, device, drag)
+                   spec.gravity, device, drag, contact)
 
     def __del__(self):
         h = getattr(self, "_h", None)

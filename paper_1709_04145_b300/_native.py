@@ -17,7 +17,8 @@ SYMBOLS = ("pbad_version", "pbad_last_error", "pbad_colloc", "pbad_model_create"
            "pbad_model_destroy", "pbad_model_info", "pbad_batch_create", "pbad_batch_destroy",
            "pbad_batch_info", "pbad_eval_objective_grad", "pbad_step", "pbad_rollout",
            "pbad_fp64_peak", "pbad_eval_objective_grad_static", "pbad_step_backward",
-           "pbad_link_points", "pbad_batch_set_threads", "pbad_model_set_drag")
+           "pbad_link_points", "pbad_batch_set_threads", "pbad_model_set_drag",
+           "pbad_model_set_contact")
 
 
 class PBADError(RuntimeError):
@@ -55,6 +56,8 @@ def lib():
         L.pbad_fp64_peak.argtypes = [i32, C.POINTER(C.c_double)]
         L.pbad_batch_set_threads.argtypes = [vp, i32]
         L.pbad_model_set_drag.argtypes = [vp, f64]
+        L.pbad_model_set_contact.argtypes = [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
+                                             f64, f64, f64]
         L.pbad_link_points.argtypes = [vp, dp, C.POINTER(C.c_int32), dp, dp, dp, vp]
         L.pbad_step_backward.argtypes = [vp, dp, dp, dp, dp, dp, f64, i32, dp, dp, dp, ip, vp]
         L.pbad_eval_objective_grad_static.argtypes = [vp, dp, dp, dp, dp, f64, i32, dp, dp, dp, vp]

@@ -72,6 +72,11 @@ struct pbad_model {
   double* d_axis = nullptr;  // [N][3]
   double* d_mm = nullptr;    // [N][10][count]
   double* d_rest = nullptr;  // [N][12][count]
+  // penalty contact (Eq. FRI): points grouped by link
+  int n_contact = 0;
+  double c_z0 = 0.0, c_d1 = 0.0, c_d2 = 0.0;
+  int* d_coff = nullptr;     // [N + 1]
+  double* d_cpt = nullptr;   // [n_contact][3]
 };
 
 struct pbad_batch {
@@ -79,7 +84,8 @@ struct pbad_batch {
   int threads = 32;  // threads per block of the solver kernels
   std::vector<pbad_model*> models;
   std::vector<int64_t> inst_off, dof_off, lanes, lane_doubles;
-  std::vector<int> tk;         // per bucket: workspace holds T(q_cur) for the one-stage drag energy
+  std::vector<int> tk;         // per bucket: workspace holds T(q_cur) (one-stage drag / contact)
+  std::vector<int> nc;         // per bucket: contact points the workspace was laid out for
   std::vector<size_t> ws_off;  // in doubles
   int64_t n_inst = 0, D = 0;
   double* d_ws = nullptr;
@@ -318,9 +324,19 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.dense_stride = bt->d_dense ? bt->dense_stride[k] : 0;
     B.drag = m->drag;
     B.tk = bt->tk[k];
-    if (S == 1 && m->drag != 0.0 && !B.tk)
-      return fail(PBAD_ERR_ARG, "the model's drag was set after the batch was created "
-                                "(one-stage drag needs storage reserved at batch creation)");
+    if (S == 1 && (m->drag != 0.0 || m->n_contact > 0) && !B.tk)
+      return fail(PBAD_ERR_ARG, "the model's drag or contact was set after the batch was created "
+                                "(one-stage drag and contact need storage reserved at batch creation)");
+    if (m->n_contact != bt->nc[k])
+      return fail(PBAD_ERR_ARG, "the model's contact points changed after the batch was created");
+    if (m->n_contact > 0 && S != 1)
+      return fail(PBAD_ERR_UNSUPPORTED, "the penalty contact (Eq. FRI) is defined for one stage");
+    B.n_contact = m->n_contact;
+    B.c_off = m->d_coff;
+    B.c_pt = m->d_cpt;
+    B.c_z0 = m->c_z0;
+    B.c_d1 = m->c_d1;
+    B.c_d2 = m->c_d2;
     const bool warp_map = all_warp || B.solver == PBAD_NEWTON;
     const int64_t warps = warp_map ? m->count : (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
     blocks += (int)((warps + wpb - 1) / wpb);
@@ -483,7 +499,55 @@ int pbad_model_destroy(pbad_model* m) {
   cudaFree(m->d_axis);
   cudaFree(m->d_mm);
   cudaFree(m->d_rest);
+  cudaFree(m->d_coff);
+  cudaFree(m->d_cpt);
   delete m;
+  return PBAD_OK;
+}
+
+int pbad_model_set_contact(pbad_model* m, int32_t n_points, const int32_t* link,
+                           const double* point, double z0, double d1, double d2) {
+  if (!m) return fail(PBAD_ERR_ARG, "null model");
+  if (n_points < 0 || n_points > 65536) return fail(PBAD_ERR_ARG, "n_points must be in 0..65536");
+  if (n_points > 0 && (!link || !point)) return fail(PBAD_ERR_ARG, "null contact arrays");
+  if (!(d1 >= 0.0) || !(d2 >= 0.0) || !std::isfinite(d1) || !std::isfinite(d2) || !std::isfinite(z0))
+    return fail(PBAD_ERR_ARG, "d1, d2 must be finite and >= 0, z0 finite");
+  for (int k = 0; k < n_points; ++k)
+    if (link[k] < 0 || link[k] >= m->N) return fail(PBAD_ERR_ARG, "contact link out of range");
+  // group the points by link (stable)
+  std::vector<int> off(m->N + 1, 0);
+  for (int k = 0; k < n_points; ++k) off[link[k] + 1]++;
+  for (int l = 0; l < m->N; ++l) off[l + 1] += off[l];
+  std::vector<double> pts(3 * (size_t)n_points);
+  std::vector<int> fill(off.begin(), off.end() - 1);
+  for (int k = 0; k < n_points; ++k) {
+    const int at = fill[link[k]]++;
+    for (int c = 0; c < 3; ++c) pts[3 * at + c] = point[3 * k + c];
+  }
+  DeviceGuard dg(m->device);
+  if (!dg.ok) return fail(PBAD_ERR_CUDA, "cudaSetDevice failed");
+  cudaFree(m->d_coff);
+  cudaFree(m->d_cpt);
+  m->d_coff = nullptr;
+  m->d_cpt = nullptr;
+  m->n_contact = 0;
+  if (n_points > 0) {
+    if (cudaMalloc(&m->d_coff, sizeof(int) * (m->N + 1)) != cudaSuccess ||
+        cudaMalloc(&m->d_cpt, sizeof(double) * 3 * n_points) != cudaSuccess) {
+      cudaFree(m->d_coff);
+      m->d_coff = nullptr;
+      return fail(PBAD_ERR_ALLOC, "contact cudaMalloc");
+    }
+    if (cudaMemcpy(m->d_coff, off.data(), sizeof(int) * (m->N + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(m->d_cpt, pts.data(), sizeof(double) * 3 * n_points, cudaMemcpyHostToDevice) !=
+            cudaSuccess)
+      return fail(PBAD_ERR_CUDA, "contact cudaMemcpy");
+  }
+  m->n_contact = n_points;
+  m->c_z0 = z0;
+  m->c_d1 = d1;
+  m->c_d2 = d2;
   return PBAD_OK;
 }
 
@@ -558,9 +622,12 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
       bt->dense_doubles += (size_t)m->count * DL.total;
     }
     WsLayout L;
-    const int tk = m->drag != 0.0;  // one-stage drag energy needs T(q_cur) per link
-    L.make(m->N, m->n, max_history, (flags & PBAD_BATCH_NEWTON) ? max_stages : 0, tk);
+    // one-stage drag energy and contact need T(q_cur) per link
+    const int tk = m->drag != 0.0 || m->n_contact > 0;
+    L.make(m->N, m->n, max_history, (flags & PBAD_BATCH_NEWTON) ? max_stages : 0, tk,
+           m->n_contact);
     bt->tk.push_back(tk);
+    bt->nc.push_back(m->n_contact);
     bt->lanes.push_back(lanes);
     bt->lane_doubles.push_back(L.total);
     bt->ws_off.push_back(ws);
@@ -765,8 +832,10 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   const int64_t warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
   const int64_t blocks = (warps + 3) / 4;
   WsLayout L;
-  const int tk = m->drag != 0.0;
-  L.make(m->N, m->n, 0, 0, tk);
+  const int tk = m->drag != 0.0 || m->n_contact > 0;
+  if (m->n_contact > 0 && S != 1)
+    return fail(PBAD_ERR_UNSUPPORTED, "the penalty contact (Eq. FRI) is defined for one stage");
+  L.make(m->N, m->n, 0, 0, tk, m->n_contact);
   *lanes = blocks * 4 * 32;
   *per_lane = L.total;
   A->nb = 1;
@@ -790,6 +859,12 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   B.chain = m->chain;
   B.drag = m->drag;
   B.tk = tk;
+  B.n_contact = m->n_contact;
+  B.c_off = m->d_coff;
+  B.c_pt = m->d_cpt;
+  B.c_z0 = m->c_z0;
+  B.c_d1 = m->c_d1;
+  B.c_d2 = m->c_d2;
   *grid = (int)blocks;
   return PBAD_OK;
 }

@@ -47,8 +47,48 @@ struct Bucket {
   double* dense;         // per-instance dense Newton/adjoint storage (or null)
   int64_t dense_stride;  // doubles per instance in `dense`
   double drag;           // drag coefficient c of Q_drag (Section 6.2), 0 = none
-  int tk;                // 1 if the lane workspace holds T(q_cur) for the one-stage drag energy
+  int tk;                // 1 if the lane workspace holds T(q_cur) (one-stage drag / contact)
+  // penalty contact of Eq. FRI (one stage): points grouped by link,
+  // c_off[l]..c_off[l+1] index c_pt[3k..3k+2] (link frame); ground z < c_z0
+  int n_contact;
+  const int* c_off;      // [N + 1]
+  const double* c_pt;    // [n_contact][3]
+  double c_z0, c_d1, c_d2;
 };
+
+// World position of a body point p (link frame) under the 3x4 transform T.
+__device__ __forceinline__ void body_point(const double* T, const double* p, double* P) {
+#pragma unroll
+  for (int r = 0; r < 3; ++r) P[r] = fma(T[4 * r], p[0], fma(T[4 * r + 1], p[1], fma(T[4 * r + 2], p[2], T[4 * r + 3])));
+}
+
+// Penalty contact of one point (Eq. FRI against the ground z < z0): at world
+// position P (unknown step end) and Pk (its position at q_k), Q, f = dQ/dP,
+// H = d2Q/dP2 and Hk = d2Q/dP dPk (3x3 row-major, rows = components of f).
+// Returns false (and touches nothing) when the point is not in the ground.
+__device__ __forceinline__ bool ground_contact(const double* P, const double* Pk, double z0,
+                                               double D1, double D2, double dt, double* Q,
+                                               double* f, double* H, double* Hk) {
+  const double d = z0 - P[2];
+  if (!(d > 0.0)) return false;
+  const double idt = 1.0 / dt;
+  const double vx = (P[0] - Pk[0]) * idt, vy = (P[1] - Pk[1]) * idt;
+  const double s = fma(vx, vx, vy * vy);
+  const double d2 = d * d;
+  *Q = d2 * fma(D2, s, D1);
+  f[0] = 2.0 * D2 * d2 * vx * idt;
+  f[1] = 2.0 * D2 * d2 * vy * idt;
+  f[2] = -2.0 * d * fma(D2, s, D1);
+  const double hxx = 2.0 * D2 * d2 * idt * idt;
+  const double hxz = -4.0 * D2 * d * vx * idt, hyz = -4.0 * D2 * d * vy * idt;
+  H[0] = hxx; H[1] = 0.0; H[2] = hxz;
+  H[3] = 0.0; H[4] = hxx; H[5] = hyz;
+  H[6] = hxz; H[7] = hyz; H[8] = 2.0 * fma(D2, s, D1);
+  Hk[0] = -hxx; Hk[1] = 0.0; Hk[2] = 0.0;
+  Hk[3] = 0.0; Hk[4] = -hxx; Hk[5] = 0.0;
+  Hk[6] = -hxz; Hk[7] = -hyz; Hk[8] = 0.0;
+  return true;
+}
 
 // Collocation constants of one launch (all in units of 1/dt^2 already).
 struct Colloc {

@@ -28,9 +28,10 @@ enum Status { kConverged = 0, kMaxIter = 1, kLsFail = 2, kCholFail = 3, kNonFini
 struct WsLayout {
   int T, G, acc, axes, V, accd, C, Pb, ec, x, g, d, xt, gt, r, rt, qp, qc, sh, yh, rho;
   int u, jc;  // Jacobian-column scratch (present when Sd > 0)
-  int tk;     // T(q_cur) per link for the one-stage drag energy (present when tk_region)
+  int tk;     // T(q_cur) per link: one-stage drag energy and contact (present when tk_region)
+  int cg;     // 3 per contact point: adjoint load of the point at q_k (present with contact)
   int64_t total;
-  __host__ __device__ void make(int N, int n, int m, int Sd = 0, int tk_region = 0) {
+  __host__ __device__ void make(int N, int n, int m, int Sd = 0, int tk_region = 0, int nc = 0) {
     int o = 0;
     T = o; o += 12 * N;
     G = o; o += 12 * N;
@@ -56,6 +57,7 @@ struct WsLayout {
     u = o; o += (Sd ? n : 0);
     jc = o; o += (Sd ? n : 0);
     tk = o; o += (tk_region ? 12 * N : 0);
+    cg = o; o += 3 * nc;
     total = o;
   }
 };
@@ -135,7 +137,7 @@ struct Ctx {
       : B(B_), K(K_), b(b_) {
     N = B.N;
     n = B.n;
-    L.make(N, n, m, Sd, B.tk);
+    L.make(N, n, m, Sd, B.tk, B.n_contact);
     ws.p = B.ws + ((lane_id >> 5) * B.ws_lane) * Lane::kStride + (lane_id & 31);
     i = grp.stage;
     const double c2 = 2.0 * B.drag;
@@ -265,7 +267,7 @@ struct Ctx {
       link_fk(l, p >= 0 ? Pc : nullptr, q3, Tc, Jr);
       store12(L.T + 12 * l, Tp);
       store12(L.G + 12 * l, Tc);
-      if (S == 1 && commit && B.tk) store12(L.tk + 12 * l, Tc);
+      if (S == 1 && commit && B.tk) store12(L.tk + 12 * l, Tc);  // drag energy, contact
       double C[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) C[k] = fma(wk[0], Tp[k], wk[1] * Tc[k]);
@@ -459,6 +461,29 @@ struct Ctx {
       for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 4; ++c) G[4 * r + c] = fma(-B.g[r], mc4[c], G[4 * r + c]);
+      if (S == 1 && B.n_contact) {
+        // Eq. FRI contact points of this link: energy and dQ/dT = f [p; 1]^T
+        const int c0 = B.c_off[l], c1 = B.c_off[l + 1];
+        if (c1 > c0) {
+          double Tk[12];
+          load12(L.tk + 12 * l, Tk);
+          for (int c = c0; c < c1; ++c) {
+            const double pt[3] = {B.c_pt[3 * c], B.c_pt[3 * c + 1], B.c_pt[3 * c + 2]};
+            double P[3], Pk[3], Q, f[3], H[9], Hk[9];
+            body_point(T, pt, P);
+            body_point(Tk, pt, Pk);
+            if (ground_contact(P, Pk, B.c_z0, B.c_d1, B.c_d2, K.dt, &Q, f, H, Hk)) {
+              Eown += Q;
+#pragma unroll
+              for (int r = 0; r < 3; ++r) {
+#pragma unroll
+                for (int k = 0; k < 3; ++k) G[4 * r + k] = fma(f[r], pt[k], G[4 * r + k]);
+                G[4 * r + 3] += f[r];
+              }
+            }
+          }
+        }
+      }
       store12(L.G + 12 * l, G);
       double w6[6];
       wrench(G, T, w6);
@@ -565,6 +590,30 @@ struct Ctx {
       const MassMoment M = mass(l);
       double Bm[12];
       mul_mass(Bs, M, Bm);
+      if (S == 1 && B.n_contact) {
+        // contact points: d/de of f [p; 1]^T = (H Pdot) [p; 1]^T, Pdot = Tdot [p; 1]
+        const int c0 = B.c_off[l], c1 = B.c_off[l + 1];
+        if (c1 > c0) {
+          double Tk[12];
+          load12(L.tk + 12 * l, Tk);
+          for (int c = c0; c < c1; ++c) {
+            const double pt[3] = {B.c_pt[3 * c], B.c_pt[3 * c + 1], B.c_pt[3 * c + 2]};
+            double P[3], Pk[3], Pd[3], Q, f[3], H[9], Hk[9];
+            body_point(T, pt, P);
+            body_point(Tk, pt, Pk);
+            if (ground_contact(P, Pk, B.c_z0, B.c_d1, B.c_d2, K.dt, &Q, f, H, Hk)) {
+              body_point(Td, pt, Pd);
+#pragma unroll
+              for (int r = 0; r < 3; ++r) {
+                const double fd = fma(H[3 * r], Pd[0], fma(H[3 * r + 1], Pd[1], H[3 * r + 2] * Pd[2]));
+#pragma unroll
+                for (int k = 0; k < 3; ++k) Bm[4 * r + k] = fma(fd, pt[k], Bm[4 * r + k]);
+                Bm[4 * r + 3] += fd;
+              }
+            }
+          }
+        }
+      }
       double w6[6];
       if (MODE == kGn) {
         wrench(Bm, T, w6);
@@ -887,6 +936,26 @@ struct Ctx {
       Td[7] += V[4];
       Td[11] += V[5];
       store12(L.G + 12 * l, Td);
+      if (S == 1 && B.n_contact) {
+        // contact points: the load Hk^T Pdot at the point's position at q_k,
+        // for the known-node product of q_cur (T holds the step end here)
+        double Tk[12];
+        load12(L.tk + 12 * l, Tk);
+        for (int c = B.c_off[l]; c < B.c_off[l + 1]; ++c) {
+          const double pt[3] = {B.c_pt[3 * c], B.c_pt[3 * c + 1], B.c_pt[3 * c + 2]};
+          double P[3], Pk[3], Pd[3], Q, f[3], H[9], Hk[9];
+          body_point(T, pt, P);
+          body_point(Tk, pt, Pk);
+          double g[3] = {0.0, 0.0, 0.0};
+          if (ground_contact(P, Pk, B.c_z0, B.c_d1, B.c_d2, K.dt, &Q, f, H, Hk)) {
+            body_point(Td, pt, Pd);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) g[r] = fma(Hk[r], Pd[0], fma(Hk[3 + r], Pd[1], Hk[6 + r] * Pd[2]));
+          }
+#pragma unroll
+          for (int r = 0; r < 3; ++r) ws[L.cg + 3 * c + r] = g[r];
+        }
+      }
     }
   }
 
@@ -919,6 +988,19 @@ struct Ctx {
       const MassMoment M = mass(l);
       double Bm[12], w6[6];
       mul_mass(Bs, M, Bm);
+      if (S == 1 && j == 1 && B.n_contact) {
+        // contact points: their loads (from transform_tangents) act at P(q_k)
+        for (int c = B.c_off[l]; c < B.c_off[l + 1]; ++c) {
+          const double pt[3] = {B.c_pt[3 * c], B.c_pt[3 * c + 1], B.c_pt[3 * c + 2]};
+#pragma unroll
+          for (int r = 0; r < 3; ++r) {
+            const double g = ws[L.cg + 3 * c + r];
+#pragma unroll
+            for (int k = 0; k < 3; ++k) Bm[4 * r + k] = fma(g, pt[k], Bm[4 * r + k]);
+            Bm[4 * r + 3] += g;
+          }
+        }
+      }
       wrench(Bm, T, w6);
       for (int k = 0; k < 6; ++k) ws[L.acc + 6 * l + k] = w6[k];
     }
