@@ -500,6 +500,26 @@ def measure_drag(P, args, dev):
                                  "drag": w["drag"], "tol": w["tol"],
                                  "converged_fraction": float((st == 0).mean()),
                                  "iters_per_step": float(res["iters"].float().mean().item() / T)}
+    # Section 6.2's spider on the ground (free root, 4 legs, 22 DOFs, six
+    # contact points of Eq. FRI), one stage, both solvers
+    w = I.spiders(n_steps=args.drag_steps)
+    spec, S, dt, m = w["spec"], w["stages"], w["dt"], w["history"]
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index, drag=w["drag"], contact=w["contact"])],
+                    max_stages=S, max_history=m, newton=True)
+    qp, qc = _state_tensors(P, [(w["q0"], w["qd0"])], S, dt, dev)
+    T = w["n_steps"]
+    bodies = spec.n_links - 1
+    for name, sv, mi in (("lbfgs", P.LBFGS, 500), ("newton", P.NEWTON, 100)):
+        run = lambda: P.rollout(batch, qp, qc, None, T, dt, S, sv, m, w["tol"], mi, want_traj=False)
+        run()
+        ms, res = _timed(run)
+        st = res["status"].cpu().numpy()
+        out[f"spiders_contact_{name}"] = {
+            "value": spec.count * bodies * T / (ms / 1e3), "unit": UNIT, "ms": ms,
+            "instances": spec.count, "links": bodies, "dofs": spec.n_dof, "timesteps": T, "dt": dt,
+            "stages": S, "contact_points": len(w["contact"]["link"]), "tol": w["tol"],
+            "max_iter_per_step": mi, "worst_status_converged_fraction": float((st == 0).mean()),
+            "iters_per_step": float(res["iters"].float().mean().item() / T)}
     wb = I.ball_chains(count=args.instances, n_links=args.links, n_steps=5)
     spec = wb["spec"]
     S, dt, m = wb["stages"], wb["dt"], wb["history"]

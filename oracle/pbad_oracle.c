@@ -1121,6 +1121,16 @@ static void lbfgs_precond(om_model *m, int S, double dt, const double *q_cur,
     double B[9] = {0}, B2[9] = {0};
     for (int a = 0; a < k; ++a)
       for (int b = 0; b < k; ++b) B[a * k + b] = H[(o + a) * n + o + b];
+    /* thin rods on ball joints have (near) singular blocks (no inertia about
+     * the rod axis): add 1e-8 of the mean diagonal; a block with zero trace
+     * (massless subtree) becomes the identity */
+    double tr = 0;
+    for (int a = 0; a < k; ++a) tr += B[a * k + a];
+    if (tr > 0) {
+      for (int a = 0; a < k; ++a) B[a * k + a] += 1e-8 * tr / k;
+    } else {
+      for (int a = 0; a < k * k; ++a) B[a] = (a % (k + 1) == 0) ? 1.0 : 0.0;
+    }
     if (S >= 2) {
       for (int a = 0; a < k; ++a)
         for (int b = 0; b < k; ++b) {
@@ -1278,6 +1288,12 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
       for (int i = 0; i < Sn; ++i) d[i] = -g[i];
       precond_apply(m, &pc, d);
       gd = dot(g, d, Sn);
+      if (!(gd < 0)) {
+        /* -P g is not a descent direction either (P not positive definite
+         * in rounding): steepest descent */
+        for (int i = 0; i < Sn; ++i) d[i] = -g[i];
+        gd = dot(g, d, Sn);
+      }
     }
     /* backtracking line search with Armijo or approximate-Wolfe acceptance */
     double a = 1.0;

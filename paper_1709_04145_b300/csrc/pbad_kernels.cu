@@ -320,6 +320,14 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
         c.precond(reset ? L.d : L.gt);
         const double gd1 = cv.gdot(L.g, L.d);
         if (reset) gd = gd1;
+        // -P g not a descent direction either (P not positive definite in
+        // rounding): steepest descent
+        const bool sd = reset && !(gd < 0.0);
+        if (__any_sync(kAll, sd)) {
+          if (sd) cv.vlin(L.d, -1.0, L.g, -1);
+          const double gd2 = cv.gdot(L.g, L.d);
+          if (sd) gd = gd2;
+        }
       }
       if (start) {
         alpha = 1.0;

@@ -349,6 +349,20 @@ struct Ctx {
           Bj[3 * a + bb] = jt == kTranslation ? (a == bb ? c[9] : 0.0) : s;
           // (hinge: only Bj[0] is used, w[0..2] being its axis)
         }
+      {
+        // thin rods on ball joints have (near) singular blocks: add 1e-8 of
+        // the mean diagonal; a zero-trace block (massless subtree) becomes I
+        const double tr = nd == 1 ? Bj[0] : Bj[0] + Bj[4] + Bj[8];
+        if (tr > 0.0) {
+          const double lam = 1e-8 * tr / nd;
+          Bj[0] += lam;
+          Bj[4] += lam;
+          Bj[8] += lam;
+        } else {
+#pragma unroll
+          for (int k = 0; k < 9; ++k) Bj[k] = (k % 4 == 0) ? 1.0 : 0.0;
+        }
+      }
       if (nd == 1) {
         Pj[0] = 1.0 / Bj[0];
         if (S > 1) Pj[0] *= Pj[0];

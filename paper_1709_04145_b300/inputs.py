@@ -304,6 +304,60 @@ def swimmers_free(count: int = 4096, seed_base: int = 6100, n_steps: int = 20, d
                 n_steps=n_steps, drag=drag, solver="lbfgs")
 
 
+def spiders(count: int = 4096, seed_base: int = 6200, n_steps: int = 20):
+    """Section 6.2's spider body on the ground: a torso rod (L = 0.4 m,
+    m = 1 kg) on a free 6-DOF root and four legs, each an upper rod on a
+    ball hip and a lower rod on a hinge knee (L = 0.3 m, m = 0.2 kg); the
+    front pair is attached at the torso's joint, the rear pair at its tip.
+    6 + 4 x (3 + 1) = 22 DOFs (the paper counts 18 for its spider). Contact
+    points (Eq. FRI): the four feet and both torso ends against the ground
+    z < 0, D1 = 2000, D2 = 100; drag 0.05 (settling); dt = 0.02, one stage,
+    L-BFGS history 8. Initial state: torso horizontal 0.35 m above the
+    ground, legs down with every angle perturbed U[-0.2, 0.2], velocities
+    N(0, 0.3^2)."""
+    rng = np.random.default_rng(seed_base + 1)
+    # links: 0 carrier (translation), 1 torso (ball), then legs (hip ball, knee hinge) x 4
+    parent = [-1, 0]
+    jtype = [TRANSLATION, BALL]
+    attach_z = [0.0, 0.0]
+    length = [0.0, 0.4]
+    mass = [0.0, 1.0]
+    for k in range(4):
+        parent += [1, len(parent)]
+        jtype += [BALL, HINGE]
+        attach_z += [0.0 if k < 2 else -0.4, -0.3]
+        length += [0.3, 0.3]
+        mass += [0.2, 0.2]
+    N = len(parent)
+    parent = np.array(parent, np.int32)
+    jtype = np.array(jtype, np.int32)
+    axis = np.tile(np.array([0.0, 1.0, 0.0]), (N, 1))
+    rest_rot = np.tile(np.eye(3), (N, 1, 1))
+    attach = np.zeros((count, N, 3))
+    attach[:, :, 2] = np.array(attach_z)
+    # front legs splay in +-y at the torso joint, rear legs at the tip
+    for k in range(4):
+        attach[:, 2 + 2 * k, 1] = 0.1 if k % 2 == 0 else -0.1
+    L = np.tile(np.array(length), (count, 1))
+    M = np.tile(np.array(mass), (count, 1))
+    spec = BodySpec(parent, jtype, axis, rest_rot, attach, L, M, np.zeros((count, N)),
+                    np.full(N, ROD, np.int32), name="spider")
+    n = spec.n_dof
+    q0 = np.zeros((count, n))
+    sl = spec.dof_slices()
+    q0[:, sl[0]] = [0.0, 0.0, 0.35]
+    q0[:, sl[1]] = [0.0, np.pi / 2, 0.0]  # torso axis (local -z) along world -x
+    for k in range(4):
+        q0[:, sl[2 + 2 * k]] = [0.0, -np.pi / 2, 0.0]  # upper leg back to world -z
+    q0[:, 3:] += rng.uniform(-0.2, 0.2, size=(count, n - 3))
+    qd0 = rng.normal(0.0, 0.3, size=(count, n))
+    feet = [3 + 2 * k for k in range(4)]
+    contact = dict(link=feet + [1, 1], point=[[0, 0, -0.3]] * 4 + [[0, 0, 0.0], [0, 0, -0.4]],
+                   z0=0.0, d1=2000.0, d2=100.0)
+    return dict(spec=spec, q0=q0, qd0=qd0, contact=contact, drag=0.05, dt=0.02, stages=1,
+                history=8, tol=1e-8, n_steps=n_steps, solver="lbfgs")
+
+
 def humanoid_adjoint(count: int = 1024, seed_base: int = 4000, n_steps: int = 64):
     """Differentiation workload: humanoids, 64 steps at dt = 0.033 with two
     stages; loss = squared distance of the end effector (tip of limb 1's last

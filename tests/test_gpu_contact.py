@@ -128,3 +128,43 @@ def test_contact_needs_one_stage():
     q = torch.zeros(2 * batch.D, dtype=torch.float64, device="cuda:0")
     with pytest.raises(P.PBADError):
         P.eval_objective_grad(batch, q, q[:batch.D], q[:batch.D], None, 0.02, 2)
+
+
+@pytest.mark.parametrize("solver", ["lbfgs", "lm"])
+def test_spider_steps_match_oracle(solver):
+    """Section 6.2's spider body (free root, four legs, six ground contact
+    points): the first steps of both solvers against the oracle, step by
+    step from the same states; the objective never rises within a step."""
+    import torch
+    import paper_1709_04145_b300 as P
+    w = I.spiders(count=3, n_steps=4)
+    spec, dt = w["spec"], w["dt"]
+    sv = P.LBFGS if solver == "lbfgs" else P.NEWTON
+    mi = 500 if sv == P.LBFGS else 100
+    batch = P.Batch([P.Model.from_spec(spec, drag=w["drag"], contact=w["contact"])], max_stages=1,
+                    max_history=8, newton=True)
+    n = spec.n_dof
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    qc = w["q0"].copy()
+    qp = w["q0"] - dt * w["qd0"]
+    agree = 0
+    for step in range(4):
+        out = P.step(batch, t(qp), t(qc), None, dt, 1, sv, 8, w["tol"], mi)
+        qs = out["q_stages"].cpu().numpy().reshape(spec.count, n)
+        st = out["status"].cpu().numpy()
+        E0, _, _ = P.eval_objective_grad(batch, t(2 * qc - qp), t(qp), t(qc), None, dt, 1)
+        E1, _, _ = P.eval_objective_grad(batch, t(qs), t(qp), t(qc), None, dt, 1)
+        assert (E1.cpu().numpy() <= E0.cpu().numpy() * (1 + 1e-9) + 1e-12).all()
+        for b in range(spec.count):
+            om = O.OracleModel.from_spec(spec, b, drag=w["drag"], contact=w["contact"])
+            q_o, st_o, _, _ = om.step(1, dt, qp[b], qc[b], np.zeros(n), solver, 8, w["tol"], mi)
+            if st_o == st[b] == 0:
+                assert np.max(np.abs(q_o.reshape(-1) - qs[b])) <= 1e-7, (step, b)
+                agree += 1
+        # continue from the oracle's states so that every step starts equal
+        nxt = np.stack([O.OracleModel.from_spec(spec, b, drag=w["drag"], contact=w["contact"])
+                        .step(1, dt, qp[b], qc[b], np.zeros(n), solver, 8, w["tol"], mi)[0].reshape(-1)
+                        for b in range(spec.count)])
+        qp, qc = qc, nxt
+    assert agree >= 3
