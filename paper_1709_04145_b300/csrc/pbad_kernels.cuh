@@ -179,10 +179,16 @@ struct Ctx {
   // joint, [I | q_l]. Ball joints also return Jr(q_l) (translation: I).
   __device__ __forceinline__ void link_fk(int l, const double* Tp, const double* ql, double* T,
                                           double* Jr, ExpCoef* ec = nullptr) const {
-    double R[9], XJ[12];
-    const int jt = B.jtype[l];
+    double R[9];
     const double u[3] = {B.axis[3 * l], B.axis[3 * l + 1], B.axis[3 * l + 2]};
-    joint_rotation(jt, u, ql, R, Jr, ec);
+    joint_rotation(B.jtype[l], u, ql, R, Jr, ec);
+    link_fk_rot(l, Tp, ql, R, T);
+  }
+  // The same with the joint rotation R given.
+  __device__ __forceinline__ void link_fk_rot(int l, const double* Tp, const double* ql,
+                                              const double* R, double* T) const {
+    double XJ[12];
+    const int jt = B.jtype[l];
     if (B.rest_eye[l]) {
       // identity rest rotation: X_l J = [Rot | t_X] (translation: [I | t_X + q])
 #pragma unroll
@@ -411,16 +417,34 @@ struct Ctx {
     const double dt2 = K.dt * K.dt;
     const bool chain = B.chain;
     double Tp[12];  // parent transform (kept in registers along a chain)
-    for (int l = 0; l < N; ++l) {
-      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
-      double T[12], Jr[9], q3[3] = {0.0, 0.0, 0.0}, w[9];
-      if (p >= 0 && !chain) load12(L.T + 12 * p, Tp);
+    // The joint rotation of link l + 1 (exponential map, Rodrigues) is
+    // computed during link l: it does not depend on the chain, so it gives
+    // the scheduler independent work next to link l's dependent products.
+    double qn[3] = {0.0, 0.0, 0.0}, Rn[9], Jrn[9];
+    ExpCoef ecn;
+    auto joint_of = [&](int l) {
+      const int nd = ndof(l), d0 = B.dof[l], jt = B.jtype[l];
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (k < nd) q3[k] = ws[L.xt + d0 + k];
-      ExpCoef ec;
+      for (int k = 0; k < 3; ++k) qn[k] = k < nd ? ws[L.xt + d0 + k] : 0.0;
+      const double u[3] = {B.axis[3 * l], B.axis[3 * l + 1], B.axis[3 * l + 2]};
+      joint_rotation(jt, u, qn, Rn, Jrn, jt == kBall ? &ecn : nullptr);
+    };
+    joint_of(0);
+    for (int l = 0; l < N; ++l) {
+      const int p = B.parent[l], nd = ndof(l);
+      double T[12], Jr[9], R[9], q3[3], w[9];
+      const ExpCoef ec = ecn;
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        R[k] = Rn[k];
+        Jr[k] = Jrn[k];
+      }
+#pragma unroll
+      for (int k = 0; k < 3; ++k) q3[k] = qn[k];
+      if (l + 1 < N) joint_of(l + 1);
+      if (p >= 0 && !chain) load12(L.T + 12 * p, Tp);
       const int jt = B.jtype[l];
-      link_fk(l, p >= 0 ? Tp : nullptr, q3, T, Jr, jt == kBall ? &ec : nullptr);
+      link_fk_rot(l, p >= 0 ? Tp : nullptr, q3, R, T);
       if (jt == kBall) {  // cached for the tangent passes at this point
         ws[L.ec + 4 * l] = ec.b;
         ws[L.ec + 4 * l + 1] = ec.h;
