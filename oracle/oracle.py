@@ -19,6 +19,9 @@ _SRC = os.path.join(_HERE, "pbad_oracle.c")
 _LIB = os.path.join(_HERE, "libpbad_oracle.so")
 
 HINGE, BALL, TRANSLATION = 0, 1, 2
+# solver names of step/rollout: L-BFGS, Levenberg-Marquardt, and L-BFGS whose
+# two-loop recursion runs in binary32 (line search and evaluations binary64)
+SOLVERS = {"lbfgs": 0, "lm": 1, "lbfgs32": 2}
 STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE"}
 
 
@@ -79,6 +82,8 @@ def lib():
         L.om_rnea.argtypes = [vp, dp, dp, dp, dp]
         L.om_rk4.restype = C.c_int
         L.om_rk4.argtypes = [vp, dp, dp, dp, C.c_double, C.c_int]
+        L.om_lbfgs_direction.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp,
+                                         C.c_double, dp, dp, C.c_int, dp]
         _lib = L
     return _lib
 
@@ -277,9 +282,9 @@ class OracleModel:
     def step(self, S, dt, q_prev, q_cur, tau, solver="lbfgs", history=8, tol=1e-10,
              max_iter=None, precond=True):
         n = self.n_dof
-        sv = 0 if solver == "lbfgs" else 1
+        sv = SOLVERS[solver]
         if max_iter is None:
-            max_iter = 1000 if sv == 0 else 100
+            max_iter = 100 if sv == 1 else 1000
         q_prev, pp = _d(q_prev)
         q_cur, cp = _d(q_cur)
         tau, tp = _d(tau)
@@ -296,9 +301,9 @@ class OracleModel:
         """Returns dict(traj_prev, traj_cur (n_steps, n), q_prev, q_cur, status,
         iters, evals)."""
         n = self.n_dof
-        sv = 0 if solver == "lbfgs" else 1
+        sv = SOLVERS[solver]
         if max_iter is None:
-            max_iter = 1000 if sv == 0 else 100
+            max_iter = 100 if sv == 1 else 1000
         tau_seq, tsp = _d(np.asarray(tau_seq).reshape(-1, n))
         n_steps = tau_seq.shape[0]
         q_prev0, pp = _d(q_prev0)
@@ -351,6 +356,22 @@ class OracleModel:
         if rc != 0:
             raise RuntimeError("RK4 failed")
         return q, qd
+
+
+def lbfgs_direction(sh, yh, rho, gamma, P, g, head: int, nh: int, f32: bool = False):
+    """The two-loop recursion of the oracle's L-BFGS (binary64, or the
+    binary32 variant) on explicit data: ring sh, yh (m, n) with the newest
+    pair at head-1, rho (m,), H0 = gamma P with P dense (n, n). Returns d."""
+    sh, sp = _d(sh)
+    yh, yp = _d(yh)
+    rho, rp = _d(rho)
+    P, pp = _d(P)
+    g, gp = _d(g)
+    m, n = sh.shape
+    d = np.zeros(n)
+    lib().om_lbfgs_direction(n, nh, m, head, sp, yp, rp, gamma, pp, gp, int(f32),
+                             d.ctypes.data_as(C.POINTER(C.c_double)))
+    return d
 
 
 def initial_prev(q0, qd0, S: int, dt: float):

@@ -1220,6 +1220,110 @@ static double eval_point(om_model *m, int S, double dt, const double *x,
   return om_eval(m, S, dt, x, qp, qc, tau, r, g, NULL);
 }
 
+/* The L-BFGS search direction d = -H g by the two-loop recursion (Nocedal &
+ * Wright, Algorithm 7.4) over the nh newest of the mh ring slots (newest at
+ * head-1), with H0 = gamma P; P is applied in place by apply_P. sh, yh: ring
+ * of pairs, [mh][Sn]; rho[j] = 1 / s_j^T y_j; alp: mh scratch.
+ *
+ * f32dir = 1 is the mixed-precision variant: every vector operation of the
+ * recursion (the dot products, the updates, the sums) is done in binary32 on
+ * binary32 copies of -g and of the pairs; H0 is applied in binary64 to the
+ * binary32 vector and rounded back. rho and gamma enter rounded to binary32.
+ * The result is widened to binary64. */
+typedef void (*apply_fn)(void *ctx, double *v);
+
+static float dot32(const float *a, const float *b, int n) {
+  float s = 0.0f;
+  for (int i = 0; i < n; ++i) s += a[i] * b[i];
+  return s;
+}
+
+static void two_loop(int Sn, int nh, int mh, int head, const double *sh,
+                     const double *yh, const double *rho, double gamma,
+                     apply_fn apply_P, void *ctx, const double *g, int f32dir,
+                     double *d, double *alp) {
+  if (!f32dir) {
+    for (int i = 0; i < Sn; ++i) d[i] = -g[i];
+    for (int c = 0; c < nh; ++c) {
+      int j = (head - 1 - c + 2 * mh) % mh;
+      alp[j] = rho[j] * dot(sh + j * Sn, d, Sn);
+      for (int i = 0; i < Sn; ++i) d[i] -= alp[j] * yh[j * Sn + i];
+    }
+    apply_P(ctx, d);
+    for (int i = 0; i < Sn; ++i) d[i] *= gamma;
+    for (int c = nh - 1; c >= 0; --c) {
+      int j = (head - 1 - c + 2 * mh) % mh;
+      double b = rho[j] * dot(yh + j * Sn, d, Sn);
+      for (int i = 0; i < Sn; ++i) d[i] += (alp[j] - b) * sh[j * Sn + i];
+    }
+    return;
+  }
+  int nr = mh > 0 ? mh : 1;
+  float *q = (float *)malloc(sizeof(float) * Sn);
+  float *s32 = (float *)malloc(sizeof(float) * Sn * nr);
+  float *y32 = (float *)malloc(sizeof(float) * Sn * nr);
+  float *a32 = (float *)malloc(sizeof(float) * nr);
+  for (int i = 0; i < Sn * mh; ++i) {
+    s32[i] = (float)sh[i];
+    y32[i] = (float)yh[i];
+  }
+  for (int i = 0; i < Sn; ++i) q[i] = (float)(-g[i]);
+  for (int c = 0; c < nh; ++c) {
+    int j = (head - 1 - c + 2 * mh) % mh;
+    a32[j] = (float)rho[j] * dot32(s32 + j * Sn, q, Sn);
+    for (int i = 0; i < Sn; ++i) q[i] -= a32[j] * y32[j * Sn + i];
+  }
+  for (int i = 0; i < Sn; ++i) d[i] = (double)q[i];
+  apply_P(ctx, d);
+  for (int i = 0; i < Sn; ++i) q[i] = (float)(gamma * d[i]);
+  for (int c = nh - 1; c >= 0; --c) {
+    int j = (head - 1 - c + 2 * mh) % mh;
+    float b = (float)rho[j] * dot32(y32 + j * Sn, q, Sn);
+    for (int i = 0; i < Sn; ++i) q[i] += (a32[j] - b) * s32[j * Sn + i];
+  }
+  for (int i = 0; i < Sn; ++i) d[i] = (double)q[i];
+  for (int j = 0; j < mh; ++j) alp[j] = (double)a32[j];
+  free(q); free(s32); free(y32); free(a32);
+}
+
+typedef struct {
+  const om_model *m;
+  const om_precond *pc;
+} pc_ctx;
+
+static void apply_pc(void *ctx, double *v) {
+  pc_ctx *c = (pc_ctx *)ctx;
+  precond_apply(c->m, c->pc, v);
+}
+
+typedef struct {
+  int n;
+  const double *P;
+} dense_ctx;
+
+static void apply_dense(void *ctx, double *v) {
+  dense_ctx *c = (dense_ctx *)ctx;
+  double *t = (double *)malloc(sizeof(double) * c->n);
+  for (int a = 0; a < c->n; ++a) {
+    double s = 0;
+    for (int b = 0; b < c->n; ++b) s += c->P[a * c->n + b] * v[b];
+    t[a] = s;
+  }
+  memcpy(v, t, sizeof(double) * c->n);
+  free(t);
+}
+
+/* Test entry: two_loop with a dense H0 factor P (Sn x Sn, row-major). */
+void om_lbfgs_direction(int Sn, int nh, int mh, int head, const double *sh,
+                        const double *yh, const double *rho, double gamma,
+                        const double *P, const double *g, int f32dir,
+                        double *d) {
+  dense_ctx c = {Sn, P};
+  double *alp = (double *)malloc(sizeof(double) * (mh > 0 ? mh : 1));
+  two_loop(Sn, nh, mh, head, sh, yh, rho, gamma, apply_dense, &c, g, f32dir, d, alp);
+  free(alp);
+}
+
 /* One step of L-BFGS with history mh. x: in = initial guess, out = result.
  * Returns the status; *iters = accepted iterations, *evals = evaluations.
  * Besides max_iter accepted iterations, a step may use at most
@@ -1227,8 +1331,8 @@ static double eval_point(om_model *m, int S, double dt, const double *x,
  * reaching either cap gives MAX_ITER. */
 static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
                        const double *qc, const double *tau, int mh, double tol,
-                       int max_iter, int use_precond, double *x, int *iters,
-                       int *evals) {
+                       int max_iter, int use_precond, int f32dir, double *x,
+                       int *iters, int *evals) {
   int n = m->n_dof, Sn = S * n;
   double *g = (double *)malloc(sizeof(double) * Sn);
   double *r = (double *)malloc(sizeof(double) * Sn);
@@ -1266,20 +1370,8 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
     if (!isfinite(E) || !all_finite(g, Sn)) { status = OM_NONFINITE; break; }
     if (sqrt(dot(r, r, Sn)) < tol) { status = OM_CONVERGED; break; }
     if (k >= max_iter) { status = OM_MAX_ITER; break; }
-    /* two-loop recursion, H0 = gamma * diag(P) */
-    for (int i = 0; i < Sn; ++i) d[i] = -g[i];
-    for (int c = 0; c < nh; ++c) {
-      int j = (head - 1 - c + 2 * mh) % mh;
-      alp[j] = rho[j] * dot(sh + j * Sn, d, Sn);
-      for (int i = 0; i < Sn; ++i) d[i] -= alp[j] * yh[j * Sn + i];
-    }
-    precond_apply(m, &pc, d);
-    for (int i = 0; i < Sn; ++i) d[i] *= gamma;
-    for (int c = nh - 1; c >= 0; --c) {
-      int j = (head - 1 - c + 2 * mh) % mh;
-      double b = rho[j] * dot(yh + j * Sn, d, Sn);
-      for (int i = 0; i < Sn; ++i) d[i] += (alp[j] - b) * sh[j * Sn + i];
-    }
+    pc_ctx pctx = {m, &pc};
+    two_loop(Sn, nh, mh, head, sh, yh, rho, gamma, apply_pc, &pctx, g, f32dir, d, alp);
     double gd = dot(g, d, Sn);
     if (!(gd < 0)) {
       /* not a descent direction: restart from the scaled gradient */
@@ -1328,6 +1420,10 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
       for (int i = 0; i < Sn; ++i) {
         sh[head * Sn + i] = xt[i] - x[i];
         yh[head * Sn + i] = gt[i] - g[i];
+        if (f32dir) { /* the pairs are kept in binary32 */
+          sh[head * Sn + i] = (double)(float)sh[head * Sn + i];
+          yh[head * Sn + i] = (double)(float)yh[head * Sn + i];
+        }
       }
       rho[head] = 1.0 / sy;
       head = (head + 1) % mh;
@@ -1432,7 +1528,8 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
 }
 
 /* One time step: solve for the S stage configurations.
- *   solver 0 = LBFGS (history mh), 1 = LM. qs_out: S*n.
+ *   solver 0 = LBFGS (history mh), 1 = LM, 2 = LBFGS with the binary32
+ *   search direction (two_loop, f32dir). qs_out: S*n.
  * Returns the status code. */
 int om_step(void *p, int S, double dt, const double *q_prev,
             const double *q_cur, const double *tau, int solver, int mh,
@@ -1440,9 +1537,9 @@ int om_step(void *p, int S, double dt, const double *q_prev,
             int *iters, int *evals) {
   om_model *m = (om_model *)p;
   initial_guess(S, m->n_dof, q_prev, q_cur, qs_out);
-  if (solver == 0)
+  if (solver == 0 || solver == 2)
     return lbfgs_solve(m, S, dt, q_prev, q_cur, tau, mh, tol, max_iter,
-                       use_precond, qs_out, iters, evals);
+                       use_precond, solver == 2, qs_out, iters, evals);
   return lm_solve(m, S, dt, q_prev, q_cur, tau, tol, max_iter, qs_out, iters,
                   evals);
 }
