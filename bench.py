@@ -91,6 +91,9 @@ def parse():
     p.add_argument("--max-iter-uneven", type=int, default=100)
     p.add_argument("--drag-steps", type=int, default=20,
                    help="steps of the swimmer-like drag workload (0 = skip)")
+    p.add_argument("--f32-steps", type=int, default=20,
+                   help="steps of the one-stage binary32-direction L-BFGS comparisons "
+                        "(0 = skip the mixed-precision section)")
     p.add_argument("--dt-sweep", action="store_true",
                    help="add a step-size sweep of both solvers (ball and hinge chains, dt 0.001-0.128)")
     p.add_argument("--scaling-steps", type=int, default=1,
@@ -537,6 +540,56 @@ def measure_drag(P, args, dev):
     return out
 
 
+def measure_mixed_precision(P, args, dev):
+    """L-BFGS with the binary32 two-loop recursion (binary64 line search and
+    evaluations) against binary64 L-BFGS on the same batches: the main
+    ball-chain workload (all its steps), and one-stage swimmer-like chains
+    and humanoids, where L-BFGS converges, over args.f32_steps steps."""
+    import numpy as np
+    from paper_1709_04145_b300 import inputs as I
+    out = {}
+
+    def pair(name, batch, qp, qc, T, S, dt, m, tol, max_iter, units, warm=True):
+        row = {}
+        for label, sv in (("f64", P.LBFGS), ("f32_direction", P.LBFGS_F32)):
+            run = lambda: P.rollout(batch, qp, qc, None, T, dt, S, sv, m, tol, max_iter,
+                                    want_traj=False)
+            if warm:
+                run()
+            ms, res = _timed(run)
+            st = res["status"].cpu().numpy()
+            row[label] = {"ms": ms, "value": units * T / (ms / 1e3), "unit": UNIT,
+                          "iters_per_step": float(res["iters"].float().mean().item() / T),
+                          "evals_per_step": float(res["evals"].float().mean().item() / T),
+                          "status_counts": np.bincount(st, minlength=5).tolist()}
+        row["speedup"] = row["f64"]["ms"] / row["f32_direction"]["ms"]
+        row.update({"timesteps": T, "stages": S, "dt": dt, "tol": tol, "max_iter": max_iter})
+        out[name] = row
+
+    # the main workload at its full length: one run of each (the kernels are
+    # loaded and warm from the timed bench)
+    T = args.timesteps
+    wb = I.ball_chains(count=args.instances, n_links=args.links, n_steps=T)
+    spec, S, dt, m = wb["spec"], wb["stages"], wb["dt"], wb["history"]
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=S, max_history=m)
+    qp, qc = _state_tensors(P, [(wb["q0"], wb["qd0"])], S, dt, dev)
+    pair(f"ball_chains_{spec.count}x{spec.n_links}", batch, qp, qc, T, S, dt, m, args.tol,
+         args.max_iter, spec.count * spec.n_links, warm=False)
+    T = args.f32_steps
+    w = I.swimmers(n_steps=T)
+    spec, S, dt, m = w["spec"], w["stages"], w["dt"], w["history"]
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index, drag=w["drag"])], max_stages=S,
+                    max_history=m)
+    qp, qc = _state_tensors(P, [(w["q0"], w["qd0"])], S, dt, dev)
+    pair("swimmers_one_stage", batch, qp, qc, T, S, dt, m, w["tol"], 200, spec.count * spec.n_links)
+    spec = I.humanoid(1024, seed=5)
+    q0, qd0 = I.random_state(spec, 6, pose_scale=0.3, vel_sigma=0.3)
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=1, max_history=8)
+    qp, qc = _state_tensors(P, [(q0, qd0)], 1, 0.033, dev)
+    pair("humanoids_one_stage", batch, qp, qc, T, 1, 0.033, 8, 1e-8, 1000, spec.count * spec.n_links)
+    return out
+
+
 def measure_dt_sweep(P, args, dev):
     """Step-size sweep of both solvers on two bodies: 512 ten-link ball chains
     (three stages) and 512 five-link hinge-rod chains (two stages), two
@@ -775,6 +828,8 @@ def run_ours(args):
         line["scaling_study"] = measure_scaling(P, args, dev)
     if rank == 0 and args.drag_steps > 0:
         line["drag"] = measure_drag(P, args, dev)
+    if rank == 0 and args.f32_steps > 0:
+        line["mixed_precision"] = measure_mixed_precision(P, args, dev)
     if rank == 0 and args.dt_sweep:
         line["dt_sweep"] = measure_dt_sweep(P, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

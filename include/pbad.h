@@ -74,6 +74,13 @@ extern "C" {
 
 #define PBAD_LBFGS 0
 #define PBAD_NEWTON 1
+/* L-BFGS whose two-loop recursion runs in binary32 on binary32 curvature
+ * pairs (H0 = gamma P still applied in binary64); the line search, the
+ * convergence test and every evaluation of E, r and dE/dq stay binary64.
+ * The solution of a converged step is the same fixed point of the step
+ * equations; the iterates on the way differ from PBAD_LBFGS at the binary32
+ * rounding level. A mixed-precision option, not the default. */
+#define PBAD_LBFGS_F32 2
 
 /* per-instance solver status (the worst over the steps of a rollout) */
 #define PBAD_CONVERGED 0  /* |r|_2 < tol */
@@ -176,7 +183,8 @@ PBAD_API int pbad_eval_objective_grad(pbad_batch* batch, const double* q_star, c
 
 /* One time step for every instance: q_prev'/q_cur' [D] (either may be NULL),
  * q_stages_out[S*D] (NULL = skip), status/iters [instances] (NULL = skip).
- * solvers[n_models] (host, NULL = all PBAD_LBFGS); history <= max_history;
+ * solvers[n_models] (host, NULL = all PBAD_LBFGS): PBAD_LBFGS, PBAD_NEWTON or
+ * PBAD_LBFGS_F32 per model; history <= max_history;
  * tol is the bound on |r|_2 (r = dE/dq for S == 1); max_iter >= 0. */
 PBAD_API int pbad_step(pbad_batch* batch, const double* q_prev, const double* q_cur, const double* tau,
               double dt, int32_t stages, const int32_t* solvers, int32_t history, double tol,

@@ -16,10 +16,13 @@ from . import inputs
 from ._native import PBADError, check, lib
 
 __all__ = ["Model", "Batch", "colloc", "eval_objective_grad", "step", "rollout", "fp64_peak",
-           "step_backward", "PBADError", "LBFGS", "NEWTON", "STATUS", "inputs"]
+           "step_backward", "PBADError", "LBFGS", "NEWTON", "LBFGS_F32", "STATUS", "inputs"]
 
 LBFGS = 0
 NEWTON = 1
+# L-BFGS with the two-loop recursion in binary32 (line search and every
+# evaluation binary64): the mixed-precision option
+LBFGS_F32 = 2
 STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE"}
 
 

@@ -369,7 +369,8 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   if (!(tol >= 0.0)) return fail(PBAD_ERR_ARG, "tol must be >= 0");
   for (size_t k = 0; k < bt->models.size(); ++k) {
     const int sv = solvers ? solvers[k] : PBAD_LBFGS;
-    if (sv != PBAD_LBFGS && sv != PBAD_NEWTON) return fail(PBAD_ERR_ARG, "unknown solver");
+    if (sv != PBAD_LBFGS && sv != PBAD_NEWTON && sv != PBAD_LBFGS_F32)
+      return fail(PBAD_ERR_ARG, "unknown solver");
     if (sv == PBAD_NEWTON && !(bt->flags & PBAD_BATCH_NEWTON))
       return fail(PBAD_ERR_ARG, "the Newton solver needs a batch created with PBAD_BATCH_NEWTON");
   }

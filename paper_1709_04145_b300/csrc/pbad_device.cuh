@@ -381,6 +381,13 @@ struct Group {
     for (int j = 0; j < S; ++j) s += __shfl_sync(mask, v, src(j));
     return s;
   }
+  __device__ __forceinline__ float sum(float v) const {
+    if (S == 1) return v;
+    float s = 0.0f;
+#pragma unroll
+    for (int j = 0; j < S; ++j) s += __shfl_sync(mask, v, src(j));
+    return s;
+  }
 };
 
 }  // namespace pbad

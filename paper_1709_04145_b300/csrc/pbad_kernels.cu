@@ -66,12 +66,13 @@ __global__ void __launch_bounds__(128) k_eval(const __grid_constant__ LaunchArgs
 // predicates, so groups in different phases share one pass over the
 // workspace instead of taking turns through divergent branches.
 // ------------------------------------------------------------------------
-template <int S>
+template <int S, bool F32>
 __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B) {
   const LaneId<S> id(B);
   const bool active = id.real && id.inst < B.count;
   const int b = active ? (int)id.inst : 0;
   const int m = A.history;
+  constexpr bool f32 = F32;  // binary32 two-loop recursion (PBAD_LBFGS_F32)
   Ctx<S> c(B, A.K, b, id.lane_id, m);
   // c goes to the non-inlined passes; cv, a private copy used by the inline
   // helpers only, keeps the layout and lane fields in registers across the
@@ -210,9 +211,23 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
           for (int k = 0; k < kC; ++k)
             if (d0 + k < n) {
               yPy = fma(yv[k], pv[k], yPy);
-              ws[L.sh + head * n + d0 + k] = sv[k];
-              ws[L.yh + head * n + d0 + k] = yv[k];
+              if constexpr (!f32) {
+                ws[L.sh + head * n + d0 + k] = sv[k];
+                ws[L.yh + head * n + d0 + k] = yv[k];
+              }
             }
+          if constexpr (f32) {  // packed binary32 pairs (kC even: d0 / 2 is a slot)
+#pragma unroll
+            for (int k = 0; k < kC; k += 2)
+              if (d0 + k < n) {
+                const bool two = d0 + k + 1 < n;
+                const int o = (d0 + k) >> 1;
+                ws[L.sh + head * n + o] = Ctx<S>::pack32(__double2float_rn(sv[k]),
+                                                         two ? __double2float_rn(sv[k + 1]) : 0.0f);
+                ws[L.yh + head * n + o] = Ctx<S>::pack32(__double2float_rn(yv[k]),
+                                                         two ? __double2float_rn(yv[k + 1]) : 0.0f);
+              }
+          }
         }
       }
       yPy = cv.grp.sum(yPy);
@@ -276,38 +291,43 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     }
 
     // (6) two-loop recursion with H0 = gamma P for the groups that start an
-    // iteration; a non-descent direction falls back to -P g. Each sweep
-    // applies one update and forms the next step's dot product.
+    // iteration (in binary32 on binary32 pairs for PBAD_LBFGS_F32); a
+    // non-descent direction falls back to -P g, then to -g (binary64). Each
+    // sweep applies one update and forms the next step's dot product.
     if (__any_sync(kAll, start)) {
-      const int nh_w = __reduce_max_sync(kAll, start ? nh : 0);
       double gd0;
-      if (start) cv.vlin(L.d, -1.0, L.g, -1);
-      auto slot = [&](int t) { return (head - 1 - t + 2 * m) % m; };
-      double al[kMaxHistory];
-      double a = 0.0;
-      if (nh_w > 0) a = ws[L.rho + slot(0)] * cv.gdot(L.sh + slot(0) * n, L.d);
-      for (int t = 0; t < nh_w; ++t) {
-        const int j = slot(t);
-        al[t] = a;
-        const bool more = t + 1 < nh_w;
-        const int jn = more ? slot(t + 1) : 0;
-        const double dot = cv.axpy_dot(L.d, -a, L.yh + j * n, more ? L.sh + jn * n : -1, start && t < nh);
-        if (more) a = ws[L.rho + jn] * dot;
-      }
-      c.precond(start ? L.d : L.gt);
-      if (start) cv.vlin(L.d, gamma, L.d, -1);
-      if (nh_w > 0) {
-        double bta = ws[L.rho + slot(nh_w - 1)] * cv.gdot(L.yh + slot(nh_w - 1) * n, L.d);
-        for (int t = nh_w - 1; t >= 0; --t) {
-          const int j = slot(t);
-          const int jn = t > 0 ? slot(t - 1) : 0;
-          const double dot = cv.axpy_dot(L.d, al[t] - bta, L.sh + j * n, t > 0 ? L.yh + jn * n : L.g,
-                                        start && t < nh);
-          if (t > 0) bta = ws[L.rho + jn] * dot;
-          else gd0 = dot;
-        }
+      if constexpr (f32) {
+        gd0 = c.direction32(start, nh, head, gamma, m);
       } else {
-        gd0 = cv.gdot(L.g, L.d);
+        const int nh_w = __reduce_max_sync(kAll, start ? nh : 0);
+        if (start) cv.vlin(L.d, -1.0, L.g, -1);
+        auto slot = [&](int t) { return (head - 1 - t + 2 * m) % m; };
+        double al[kMaxHistory];
+        double a = 0.0;
+        if (nh_w > 0) a = ws[L.rho + slot(0)] * cv.gdot(L.sh + slot(0) * n, L.d);
+        for (int t = 0; t < nh_w; ++t) {
+          const int j = slot(t);
+          al[t] = a;
+          const bool more = t + 1 < nh_w;
+          const int jn = more ? slot(t + 1) : 0;
+          const double dot = cv.axpy_dot(L.d, -a, L.yh + j * n, more ? L.sh + jn * n : -1, start && t < nh);
+          if (more) a = ws[L.rho + jn] * dot;
+        }
+        c.precond(start ? L.d : L.gt);
+        if (start) cv.vlin(L.d, gamma, L.d, -1);
+        if (nh_w > 0) {
+          double bta = ws[L.rho + slot(nh_w - 1)] * cv.gdot(L.yh + slot(nh_w - 1) * n, L.d);
+          for (int t = nh_w - 1; t >= 0; --t) {
+            const int j = slot(t);
+            const int jn = t > 0 ? slot(t - 1) : 0;
+            const double dot = cv.axpy_dot(L.d, al[t] - bta, L.sh + j * n, t > 0 ? L.yh + jn * n : L.g,
+                                          start && t < nh);
+            if (t > 0) bta = ws[L.rho + jn] * dot;
+            else gd0 = dot;
+          }
+        } else {
+          gd0 = cv.gdot(L.g, L.d);
+        }
       }
       if (start) gd = gd0;
       const bool reset = start && !(gd < 0.0);
@@ -529,17 +549,20 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
 }
 
 // One launch serves every bucket of the batch; each block runs the solver of
-// its bucket (L-BFGS or Newton), so an uneven batch with mixed solvers is a
-// single persistent launch. SOLVERS selects the variant: 0 every bucket
-// L-BFGS, 1 every bucket Newton, 2 mixed. The single-solver variants carry
-// only their own solver's code and registers.
+// its bucket (L-BFGS, Newton or L-BFGS with the binary32 direction), so an
+// uneven batch with mixed solvers is a single persistent launch. SOLVERS
+// selects the variant: 0 every bucket L-BFGS, 1 every bucket Newton, 3 every
+// bucket binary32-direction L-BFGS, 2 mixed. The single-solver variants
+// carry only their own solver's code and registers.
 template <int S, int SOLVERS>
 __global__ void __maxnreg__(255) k_rollout(const __grid_constant__ LaunchArgs A) {
   const Bucket& B = A.bk[find_bucket(A)];
-  if (SOLVERS == 0) rollout_lbfgs<S>(A, B);
+  if (SOLVERS == 0) rollout_lbfgs<S, false>(A, B);
   else if (SOLVERS == 1) rollout_newton<S>(A, B);
+  else if (SOLVERS == 3) rollout_lbfgs<S, true>(A, B);
   else if (B.solver == 1) rollout_newton<S>(A, B);
-  else rollout_lbfgs<S>(A, B);
+  else if (B.solver == 2) rollout_lbfgs<S, true>(A, B);
+  else rollout_lbfgs<S, false>(A, B);
 }
 
 // ------------------------------------------------------------------------
@@ -684,11 +707,12 @@ cudaError_t PBAD_CAT(launch_backward_s, PBAD_S)(const LaunchArgs& A, int grid, c
   return cudaGetLastError();
 }
 cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
-  bool lbfgs = false, newton = false;
-  for (int k = 0; k < A.nb; ++k) (A.bk[k].solver == 1 ? newton : lbfgs) = true;
-  if (lbfgs && newton) k_rollout<PBAD_S, 2><<<grid, A.threads, 0, s>>>(A);
-  else if (newton) k_rollout<PBAD_S, 1><<<grid, A.threads, 0, s>>>(A);
-  else k_rollout<PBAD_S, 0><<<grid, A.threads, 0, s>>>(A);
+  int kinds = 0;  // bit per solver present
+  for (int k = 0; k < A.nb; ++k) kinds |= 1 << A.bk[k].solver;
+  if (kinds == 1) k_rollout<PBAD_S, 0><<<grid, A.threads, 0, s>>>(A);
+  else if (kinds == 2) k_rollout<PBAD_S, 1><<<grid, A.threads, 0, s>>>(A);
+  else if (kinds == 4) k_rollout<PBAD_S, 3><<<grid, A.threads, 0, s>>>(A);
+  else k_rollout<PBAD_S, 2><<<grid, A.threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 #if PBAD_S == 1

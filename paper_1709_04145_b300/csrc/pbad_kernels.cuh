@@ -1131,6 +1131,132 @@ struct Ctx {
     return z >= 0 ? grp.sum(s) : 0.0;
   }
 
+  // ------------------------- binary32 search direction (PBAD_LBFGS_F32)
+  // Binary32 vectors are packed two per workspace double: element d is the
+  // low (even d) or high (odd d) word of slot d / 2. With n odd the high
+  // word of the last slot is 0, which every update keeps at 0.
+  __device__ static __forceinline__ float lo32(double v) { return __int_as_float(__double2loint(v)); }
+  __device__ static __forceinline__ float hi32(double v) { return __int_as_float(__double2hiint(v)); }
+  __device__ static __forceinline__ double pack32(float lo, float hi) {
+    return __hiloint2double(__float_as_int(hi), __float_as_int(lo));
+  }
+  __device__ __forceinline__ int n2() const { return (n + 1) >> 1; }
+
+  // v[y..] <- v[y..] + cf v[x..] (binary32, packed) when `on`, then the
+  // binary32 group sum of v[z..] . v[y..] (z < 0: none, returns 0).
+  __device__ float axpy_dot32(int y, float cf, int x, int z, bool on) const {
+    const int h = n2();
+    float s = 0.0f;
+    for (int d0 = 0; d0 < h; d0 += kChunk) {
+      double yv[kChunk], xv[kChunk], zv[kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < h) {
+          yv[k] = ws[y + d0 + k];
+          xv[k] = ws[x + d0 + k];
+          zv[k] = z >= 0 ? ws[z + d0 + k] : 0.0;
+        }
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < h) {
+          float y0 = lo32(yv[k]), y1 = hi32(yv[k]);
+          if (on) {
+            y0 = fmaf(cf, lo32(xv[k]), y0);
+            y1 = fmaf(cf, hi32(xv[k]), y1);
+            ws[y + d0 + k] = pack32(y0, y1);
+          }
+          s = fmaf(lo32(zv[k]), y0, s);
+          s = fmaf(hi32(zv[k]), y1, s);
+        }
+    }
+    return z >= 0 ? grp.sum(s) : 0.0f;
+  }
+
+  // Packed binary32 copy of ca v[a..] (binary64), rounded to nearest.
+  __device__ void pack_scaled(int y, double ca, int a) const {
+    const int h = n2();
+    for (int d0 = 0; d0 < h; d0 += kChunk) {
+      double v[2 * kChunk];
+#pragma unroll
+      for (int k = 0; k < 2 * kChunk; ++k) v[k] = 2 * d0 + k < n ? ws[a + 2 * d0 + k] : 0.0;
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < h)
+          ws[y + d0 + k] = pack32(__double2float_rn(ca * v[2 * k]), __double2float_rn(ca * v[2 * k + 1]));
+    }
+  }
+
+  // v[y..] <- the packed binary32 vector at a, widened, where `on`; returns
+  // the binary64 group sum of v[g..] . (the widened vector), or 0 if g < 0.
+  __device__ double unpack_dot(int y, int a, int g, bool on) const {
+    const int h = n2();
+    double s = 0.0;
+    for (int d0 = 0; d0 < h; d0 += kChunk) {
+      double pv[kChunk], gv[2 * kChunk];
+#pragma unroll
+      for (int k = 0; k < kChunk; ++k)
+        if (d0 + k < h) pv[k] = ws[a + d0 + k];
+#pragma unroll
+      for (int k = 0; k < 2 * kChunk; ++k)
+        if (2 * d0 + k < n) gv[k] = g >= 0 ? ws[g + 2 * d0 + k] : 0.0;
+#pragma unroll
+      for (int k = 0; k < 2 * kChunk; ++k) {
+        const int d = 2 * d0 + k;
+        if (d < n) {
+          const double v = (double)((k & 1) ? hi32(pv[k >> 1]) : lo32(pv[k >> 1]));
+          if (on) ws[y + d] = v;
+          s = fma(gv[k], v, s);
+        }
+      }
+    }
+    return g >= 0 ? grp.sum(s) : 0.0;
+  }
+
+  // The two-loop recursion with every vector operation in binary32 on the
+  // packed pairs (ring of m, newest at head - 1) and H0 = gamma P applied in
+  // binary64 to the binary32 vector; for the groups with `start` the widened
+  // direction goes to d. The packed working vector lives in the trial
+  // gradient's region, dead at this point for every group. Returns g . d.
+  __device__ __noinline__ double direction32(bool start, int nh, int head, double gamma,
+                                             int m) const {
+    const Ctx self(*this);
+    return self.direction32_body(start, nh, head, gamma, m);
+  }
+  __device__ __forceinline__ double direction32_body(bool start, int nh, int head, double gamma,
+                                                     int m) const {
+    const int q = L.gt;
+    const int nh_w = __reduce_max_sync(0xffffffffu, start ? nh : 0);
+    if (start) pack_scaled(q, -1.0, L.g);
+    auto slot = [&](int t) { return (head - 1 - t + 2 * m) % m; };
+    float al[kMaxHistory];
+    float a = 0.0f;
+    if (nh_w > 0)
+      a = (float)ws[L.rho + slot(0)] * axpy_dot32(q, 0.0f, q, L.sh + slot(0) * n, false);
+    for (int t = 0; t < nh_w; ++t) {
+      const int j = slot(t);
+      al[t] = a;
+      const bool more = t + 1 < nh_w;
+      const int jn = more ? slot(t + 1) : 0;
+      const float dot = axpy_dot32(q, -a, L.yh + j * n, more ? L.sh + jn * n : -1, start && t < nh);
+      if (more) a = (float)ws[L.rho + jn] * dot;
+    }
+    unpack_dot(L.d, q, -1, start);
+    precond(start ? L.d : L.gt);
+    if (start) pack_scaled(q, gamma, L.d);
+    if (nh_w > 0) {
+      float bta = (float)ws[L.rho + slot(nh_w - 1)] *
+                  axpy_dot32(q, 0.0f, q, L.yh + slot(nh_w - 1) * n, false);
+      for (int t = nh_w - 1; t >= 0; --t) {
+        const int j = slot(t);
+        const int jn = t > 0 ? slot(t - 1) : 0;
+        const float dot = axpy_dot32(q, al[t] - bta, L.sh + j * n, t > 0 ? L.yh + jn * n : -1,
+                                     start && t < nh);
+        if (t > 0) bta = (float)ws[L.rho + jn] * dot;
+      }
+    }
+    return unpack_dot(L.d, q, L.g, start);
+  }
+
   // v <- P v for the own slice of v at offset a (Kronecker: stage block Ps,
   // joint blocks Pb).
   __device__ __noinline__ void precond(int a) const {

@@ -85,3 +85,20 @@ def test_product_path_fails_loudly_without_library(tmp_path, monkeypatch):
     monkeypatch.setattr(_native, "LIB_PATH", str(tmp_path / "missing.so"))
     with pytest.raises(ImportError):
         _native.lib()
+
+
+def test_header_constants_match_binding():
+    """Solver, joint-type and status codes of include/pbad.h are the ones the
+    Python binding passes."""
+    import re
+    import paper_1709_04145_b300 as P
+    from paper_1709_04145_b300 import inputs as I
+    text = open(os.path.join(ROOT, "include", "pbad.h")).read()
+    defs = {k: int(v) for k, v in re.findall(r"#define (PBAD_\w+) \(?(-?\d+)\)?", text)}
+    assert defs["PBAD_LBFGS"] == P.LBFGS
+    assert defs["PBAD_NEWTON"] == P.NEWTON
+    assert defs["PBAD_LBFGS_F32"] == P.LBFGS_F32
+    assert (defs["PBAD_HINGE"], defs["PBAD_BALL"], defs["PBAD_TRANSLATION"]) == \
+        (I.HINGE, I.BALL, I.TRANSLATION)
+    for code, name in P.STATUS.items():
+        assert defs["PBAD_" + name] == code
