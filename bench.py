@@ -41,10 +41,10 @@ COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 
 # DRAM bytes (read + write) of the rollout kernel per instance-evaluation,
 # from one full ncu capture of k_rollout<3, 0> on 4096 ten-link ball chains
-# over 2 steps (profiles/k_rollout_ballchains4096_2steps_full.md): 31.15 GB
-# over 564,724 instance-evaluations. The roofline's traffic field scales it
+# over 2 steps (profiles/k_rollout_ballchains4096_2steps_full.md): 31.21 GB
+# over 564,720 instance-evaluations. The roofline's traffic field scales it
 # by the evaluations of the timed launch. Valid for the kernel as captured.
-ROLLOUT_DRAM_BYTES_PER_EVAL = 55160.0
+ROLLOUT_DRAM_BYTES_PER_EVAL = 55266.0
 
 
 def flops_per_eval(jtypes, S):
