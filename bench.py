@@ -47,15 +47,33 @@ COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 ROLLOUT_DRAM_BYTES_PER_EVAL = 55266.0
 
 
-def flops_per_eval(jtypes, S):
+def primal_flops_per_eval(jtypes, S):
+    """Residual pass (and for one stage the energy terms) of one evaluation,
+    all S stage lanes."""
     per_stage = 0
     for jt in jtypes:
         per_stage += PRIMAL_FLOPS[jt] + COUPLING_FLOPS * S
         if S == 1:
             per_stage += ENERGY_FLOPS
-        else:
-            per_stage += TANGENT_FLOPS[jt] + COUPLING_FLOPS * S
     return per_stage * S
+
+
+def tangent_flops_per_eval(jtypes, S):
+    """Tangent pass of the Eq. EQHOC gradient (S >= 2; for one stage the
+    gradient is the residual itself)."""
+    if S == 1:
+        return 0
+    return S * sum(TANGENT_FLOPS[jt] + COUPLING_FLOPS * S for jt in jtypes)
+
+
+def rollout_flops(spec, S, m, evals, grads, iters):
+    """Algorithmic flops of a rollout from its per-instance counters: every
+    evaluation's residual pass, the tangent pass of the evaluations that
+    formed the gradient, and the L-BFGS bookkeeping per iteration."""
+    jt = spec.jtype.tolist()
+    return (float(evals.sum()) * primal_flops_per_eval(jt, S) +
+            float(grads.sum()) * tangent_flops_per_eval(jt, S) +
+            float(iters.sum()) * lbfgs_flops_per_iter(spec.n_dof, S, m))
 
 
 def lbfgs_flops_per_iter(n, S, m):
@@ -285,8 +303,7 @@ def measure_throughput_point(P, args, dev, threads):
     ms = e0.elapsed_time(e1)
     ev = out["evals"].cpu().numpy()
     it = out["iters"].cpu().numpy()
-    flops = float(ev.sum()) * flops_per_eval(spec.jtype.tolist(), S) + \
-        float(it.sum()) * lbfgs_flops_per_iter(spec.n_dof, S, m)
+    flops = rollout_flops(spec, S, m, ev, out["grads"].cpu().numpy(), it)
     return {"value": spec.count * spec.n_links * T / (ms / 1e3), "unit": UNIT, "ms": ms,
             "instances": spec.count, "timesteps": T, "achieved_tflops": flops / (ms / 1e3) / 1e12,
             "evals_per_step": float(ev.mean() / T)}
@@ -691,6 +708,7 @@ def run_ours(args):
                status=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
                iters=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
                evals=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+               grads=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
                traj_prev=None, traj_cur=None)
 
     def launch():
@@ -742,12 +760,12 @@ def run_ours(args):
     status = out["status"].cpu().numpy()
     iters = out["iters"].cpu().numpy()
     evals = out["evals"].cpu().numpy()
+    grads = out["grads"].cpu().numpy()
     link_steps = spec.count * spec.n_links * T
     value = job_throughput(link_steps, world, ms)
 
     # roofline of the rollout kernel (the only kernel of the timed region)
-    fe = flops_per_eval(spec.jtype.tolist(), S)
-    flops = float(evals.sum()) * fe + float(iters.sum()) * lbfgs_flops_per_iter(spec.n_dof, S, m)
+    flops = rollout_flops(spec, S, m, evals, grads, iters)
     achieved = flops / (ms / 1e3) / 1e12
     peak = peak_gflops / 1e3
 
@@ -800,7 +818,8 @@ def run_ours(args):
         "solver_stats": {"converged_fraction": float((status == 0).mean()),
                          "status_counts": {P.STATUS[k]: int((status == k).sum()) for k in range(5)},
                          "iters_per_step": float(iters.mean() / T),
-                         "evals_per_step": float(evals.mean() / T)},
+                         "evals_per_step": float(evals.mean() / T),
+                         "gradient_evals_per_step": float(grads.mean() / T)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
                      "traffic": (ROLLOUT_DRAM_BYTES_PER_EVAL * float(evals.sum())

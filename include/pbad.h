@@ -195,13 +195,17 @@ PBAD_API int pbad_step(pbad_batch* batch, const double* q_prev, const double* q_
  * traj_prev/traj_cur [n_steps][D] the state after each step (NULL = skip),
  * q_prev_out/q_cur_out [D] the final state (NULL = skip), status = worst
  * status over the steps, iters = total accepted iterations, evals = total
- * objective/gradient evaluations (line-search trials included); each of
- * status/iters/evals [instances] may be NULL. */
+ * objective evaluations (E and r; line-search trials included), grad_evals =
+ * the evaluations that also formed dE/dq (L-BFGS: a step's first point,
+ * accepted trials and trials the approximate-Wolfe test had to read; a trial
+ * rejected on E alone needs none) or Jr (Newton); each of
+ * status/iters/evals/grad_evals [instances] may be NULL. */
 PBAD_API int pbad_rollout(pbad_batch* batch, const double* q_prev0, const double* q_cur0,
                  const double* tau_seq, int32_t n_steps, double dt, int32_t stages,
                  const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
                  double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
-                 int32_t* status, int32_t* iters, int32_t* evals, void* stream);
+                 int32_t* status, int32_t* iters, int32_t* evals, int32_t* grad_evals,
+                 void* stream);
 
 /* Implicit-function-theorem adjoint of one converged step (no counterpart
  * in the paper, which has no adjoint; it differentiates the stage equations

@@ -230,7 +230,7 @@ def rollout(batch: Batch, q_prev0, q_cur0, tau_seq, n_steps: int, dt: float, sta
             want_traj: bool = True, out=None, stream=None):
     """n_steps steps in one persistent launch. tau_seq: (n_steps*D) or None.
     Returns dict(traj_prev, traj_cur (n_steps, D) or None, q_prev, q_cur,
-    status, iters, evals). ``out`` may supply preallocated output tensors (same keys)
+    status, iters, evals, grads). ``out`` may supply preallocated output tensors (same keys)
     so that the call allocates nothing (e.g. inside a CUDA graph)."""
     import torch
     dev = q_cur0.device
@@ -240,6 +240,7 @@ def rollout(batch: Batch, q_prev0, q_cur0, tau_seq, n_steps: int, dt: float, sta
                    status=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
                    iters=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
                    evals=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+                   grads=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
                    traj_prev=None, traj_cur=None)
         if want_traj:
             out["traj_prev"] = torch.empty((n_steps, batch.D), dtype=torch.float64, device=dev)
@@ -251,7 +252,8 @@ def rollout(batch: Batch, q_prev0, q_cur0, tau_seq, n_steps: int, dt: float, sta
                              int(max_iter), _tptr(out.get("traj_prev")),
                              _tptr(out.get("traj_cur")), _tptr(out["q_prev"]),
                              _tptr(out["q_cur"]), _tptr(out["status"]), _tptr(out["iters"]),
-                             _tptr(out.get("evals")), _stream(stream)), "pbad_rollout")
+                             _tptr(out.get("evals")), _tptr(out.get("grads")),
+                             _stream(stream)), "pbad_rollout")
     return out
 
 

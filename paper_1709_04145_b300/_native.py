@@ -52,7 +52,7 @@ def lib():
         L.pbad_step.argtypes = [vp, dp, dp, dp, f64, i32, C.POINTER(C.c_int32), i32, f64, i32,
                                 dp, dp, dp, ip, ip, vp]
         L.pbad_rollout.argtypes = [vp, dp, dp, dp, i32, f64, i32, C.POINTER(C.c_int32), i32, f64,
-                                   i32, dp, dp, dp, dp, ip, ip, ip, vp]
+                                   i32, dp, dp, dp, dp, ip, ip, ip, ip, vp]
         L.pbad_fp64_peak.argtypes = [i32, C.POINTER(C.c_double)]
         L.pbad_batch_set_threads.argtypes = [vp, i32]
         L.pbad_model_set_drag.argtypes = [vp, f64]

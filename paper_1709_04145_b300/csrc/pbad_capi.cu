@@ -358,7 +358,7 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
                  const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
                  double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
                  double* q_stages_out, int32_t* status, int32_t* iters, int32_t* evals,
-                 void* stream) {
+                 int32_t* grads, void* stream) {
   int rc = check_common(bt, stages, dt);
   if (rc != PBAD_OK) return rc;
   if (!q_prev0 || !q_cur0) return fail(PBAD_ERR_ARG, "null state");
@@ -393,6 +393,7 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   A.status = status;
   A.iters = iters;
   A.evals = evals;
+  A.grads = grads;
   cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e = launch_rollout(stages, A, grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
@@ -709,10 +710,11 @@ int pbad_rollout(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
                  const double* tau_seq, int32_t n_steps, double dt, int32_t stages,
                  const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
                  double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
-                 int32_t* status, int32_t* iters, int32_t* evals, void* stream) {
+                 int32_t* status, int32_t* iters, int32_t* evals, int32_t* grad_evals,
+                 void* stream) {
   return rollout_impl(bt, q_prev0, q_cur0, tau_seq, n_steps, dt, stages, solvers, history, tol,
                       max_iter, traj_prev, traj_cur, q_prev_out, q_cur_out, nullptr, status, iters,
-                      evals, stream);
+                      evals, grad_evals, stream);
 }
 
 int pbad_step(pbad_batch* bt, const double* q_prev, const double* q_cur, const double* tau,
@@ -721,7 +723,7 @@ int pbad_step(pbad_batch* bt, const double* q_prev, const double* q_cur, const d
               int32_t* status, int32_t* iters, void* stream) {
   return rollout_impl(bt, q_prev, q_cur, tau, 1, dt, stages, solvers, history, tol, max_iter,
                       nullptr, nullptr, q_prev_out, q_cur_out, q_stages_out, status, iters,
-                      nullptr, stream);
+                      nullptr, nullptr, stream);
 }
 
 int pbad_step_backward(pbad_batch* bt, const double* q_prev, const double* q_cur,

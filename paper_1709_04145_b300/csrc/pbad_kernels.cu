@@ -89,7 +89,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     ws[L.qc + d] = A.q_cur0[cv.gdof(d)];
   }
   int step = 0, phase = kFirst, k = 0, trials = 0, nh = 0, head = 0, step_evals = 0;
-  int worst = kConverged, iters_total = 0, evals_total = 0;
+  int worst = kConverged, iters_total = 0, evals_total = 0, grads_total = 0;
   double E = 0.0, alpha = 1.0, gd = 0.0, gamma = 1.0;
   const int max_evals = 4 * A.max_iter + kLsMax;  // evaluations per step
   c.setup(true);
@@ -97,7 +97,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
 
   while (__any_sync(kAll, phase != kDone)) {
     const double* tau = A.tau ? A.tau + (int64_t)min(step, A.n_steps - 1) * D : nullptr;
-    const double Et = c.evaluate(tau);
+    const double Et = c.evaluate_primal(tau);
     const bool live = phase != kDone;
     if (live) {
       ++evals_total;
@@ -105,12 +105,27 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     }
     const bool first = live && phase == kFirst;
     const bool trial = live && phase == kTrial;
+    // The gradient at xt is read by a step's first evaluation, by an accepted
+    // trial (the next direction) and by the approximate-Wolfe test of a trial
+    // whose energy lies within its band; a trial above both bounds is
+    // rejected on E alone. The tangent pass (S >= 2) runs on the trips where
+    // some group of the warp reads the gradient: the decisions are the same
+    // as with a gradient at every trial.
+    const bool need_g = first || (trial && isfinite(Et) &&
+                                  (Et <= E + kLsEps * fabs(E) || Et <= E + kLsC1 * alpha * gd));
+    if (need_g) ++grads_total;
+    if (S == 1) {
+      if (need_g)
+        for (int d = 0; d < n; ++d) ws[L.gt + d] = ws[L.rt + d];
+    } else if (__any_sync(kAll, need_g)) {
+      c.tangent();
+    }
 
     // (1) line-search test at xt = x + alpha d: Armijo or approximate Wolfe
     bool ok = false;
     if (__any_sync(kAll, trial)) {
       double gtd = 0.0, fin = 1.0;
-      if (trial)
+      if (trial && need_g)
         for (int d0 = 0; d0 < n; d0 += Ctx<S>::kChunk) {
           double gv[Ctx<S>::kChunk], dv[Ctx<S>::kChunk];
 #pragma unroll
@@ -361,6 +376,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     if (A.status) A.status[B.inst_off + b] = worst;
     if (A.iters) A.iters[B.inst_off + b] = iters_total;
     if (A.evals) A.evals[B.inst_off + b] = evals_total;
+    if (A.grads) A.grads[B.inst_off + b] = grads_total;
   }
   if (active) {
     for (int d = 0; d < n; ++d) {
@@ -422,7 +438,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     ws[L.qc + d] = A.q_cur0[c.gdof(d)];
   }
   int step = 0, phase = kFirst, k = 0, trials = 0;
-  int worst = kConverged, iters_total = 0, evals_total = 0;
+  int worst = kConverged, iters_total = 0, evals_total = 0, grads_total = 0;
   double E = 0.0, lambda = -1.0, hmax = 0.0;
   c.setup(true);
   if (!active) phase = kDone;  // warp-uniform
@@ -513,6 +529,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
         for (int d = 0; d < n; ++d) Dn[DL.r + c.i * n + d] = ws[L.r + d];
       __syncwarp();
       c.build_jacobian_warp(Dn, DL, id.rep, id.R, false);
+      ++grads_total;
       hmax = c.gram_warp(Dn, DL);
       if (lambda < 0.0) lambda = 1e-12 * hmax;
       trials = 0;
@@ -541,6 +558,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     if (A.status) A.status[B.inst_off + b] = worst;
     if (A.iters) A.iters[B.inst_off + b] = iters_total;
     if (A.evals) A.evals[B.inst_off + b] = evals_total;
+    if (A.grads) A.grads[B.inst_off + b] = grads_total;
     for (int d = 0; d < n; ++d) {
       if (A.q_prev_out) A.q_prev_out[c.gdof(d)] = ws[L.qp + d];
       if (A.q_cur_out) A.q_cur_out[c.gdof(d)] = ws[L.qc + d];

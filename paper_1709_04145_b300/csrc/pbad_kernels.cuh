@@ -97,6 +97,7 @@ struct LaunchArgs {
   int* status;             // [instances] or null
   int* iters;              // [instances] or null
   int* evals;              // [instances] or null (objective evaluations)
+  int* grads;              // [instances] or null (evaluations that formed dE/dq or Jr)
   // step backward (implicit-function adjoint)
   const double* g_bar;     // [S*D] dL/dq_* (stage-packed)
   double* gq_prev;         // [D]

@@ -222,3 +222,34 @@ def test_newton_status_codes():
     assert out["status"].cpu().tolist() == [4, 4]
     out = P.rollout(batch, q, q, tau, 2, 0.02, 2, P.LBFGS, 8, 1e-9, 50)
     assert out["status"].cpu().tolist() == [4, 4]
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_rollout_gradient_evaluation_counts(S):
+    """L-BFGS forms dE/dq at a step's first point, at every accepted trial and
+    where the approximate-Wolfe test reads it, and nowhere else: n_steps +
+    iterations <= gradient evaluations <= evaluations. Newton forms Jr at a
+    step's start and after every accepted iteration that does not end the
+    step. (The parity tests above check that the trajectories are the ones
+    the oracle's every-trial gradients give.)"""
+    torch = _torch()
+    P = _pbad()
+    specs = [I.ball_chain(5, 4, seed=91, radius=0.15), I.rod_chain(6, 5, name="rod5")]
+    batch = P.Batch([P.Model.from_spec(s) for s in specs], max_stages=3, max_history=8, newton=True)
+    n_steps, dt = 4, 0.02
+    states, taus, qps = _rollout_case(specs, S, dt, n_steps, 92)
+    dev = torch.device("cuda:0")
+    q_cur = torch.tensor(np.concatenate([q0.reshape(-1) for q0, _ in states]), device=dev)
+    q_prev = torch.tensor(np.concatenate([qp.reshape(-1) for qp in qps]), device=dev)
+    for sv in (P.LBFGS, P.NEWTON):
+        out = P.rollout(batch, q_prev, q_cur, None, n_steps, dt, S, sv, 8, 1e-9, 60)
+        ev = out["evals"].cpu().numpy()
+        gr = out["grads"].cpu().numpy()
+        it = out["iters"].cpu().numpy()
+        assert (gr <= ev).all()
+        if sv == P.LBFGS:
+            assert (gr >= n_steps + it).all()
+            if S >= 2:  # line searches that end in LS_FAIL reject on E alone
+                assert gr.sum() < ev.sum()
+        else:  # one build per step start and per accepted iteration, less the last
+            assert (np.abs(gr - it) <= n_steps).all()
