@@ -160,26 +160,27 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
 
     // (2) one sweep: accepted groups take (xt, gt, rt) and form the curvature
     // pair s = xt - x, y = gt - g (s into rt, y into gt and d, all dead now);
-    // backtracking groups move xt.
+    // backtracking groups move xt = x + alpha d in the same sweep.
     double sy = 0.0, ss = 0.0, yy = 0.0, rr = 0.0, badg = 0.0;
     if (__any_sync(kAll, acc || back)) {
-      if (acc) {
-        constexpr int kC = Ctx<S>::kChunk;
-        for (int d0 = 0; d0 < n; d0 += kC) {
-          double xv[kC], gv[kC], rv[kC], xo[kC], go[kC];
+      constexpr int kC = Ctx<S>::kChunk;
+      for (int d0 = 0; d0 < n; d0 += kC) {
+        double xv[kC], gv[kC], rv[kC], xo[kC], go[kC];
 #pragma unroll
-          for (int k = 0; k < kC; ++k)
-            if (d0 + k < n) {
-              xv[k] = ws[L.xt + d0 + k];
-              gv[k] = ws[L.gt + d0 + k];
-              rv[k] = ws[L.rt + d0 + k];
-              xo[k] = ok ? ws[L.x + d0 + k] : 0.0;
-              go[k] = ok ? ws[L.g + d0 + k] : 0.0;
-            }
+        for (int k = 0; k < kC; ++k)
+          if (d0 + k < n) {
+            // back: xv = d, xo = x
+            xv[k] = acc ? ws[L.xt + d0 + k] : (back ? ws[L.d + d0 + k] : 0.0);
+            gv[k] = acc ? ws[L.gt + d0 + k] : 0.0;
+            rv[k] = acc ? ws[L.rt + d0 + k] : 0.0;
+            xo[k] = (ok || back) ? ws[L.x + d0 + k] : 0.0;
+            go[k] = ok ? ws[L.g + d0 + k] : 0.0;
+          }
 #pragma unroll
-          for (int k = 0; k < kC; ++k)
-            if (d0 + k < n) {
-              const int d = d0 + k;
+        for (int k = 0; k < kC; ++k)
+          if (d0 + k < n) {
+            const int d = d0 + k;
+            if (acc) {
               if (ok) {
                 const double s_ = xv[k] - xo[k], y_ = gv[k] - go[k];
                 sy = fma(s_, y_, sy);
@@ -194,10 +195,10 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
               ws[L.r + d] = rv[k];
               rr = fma(rv[k], rv[k], rr);
               if (!isfinite(gv[k])) badg = 1.0;
+            } else if (back) {
+              ws[L.xt + d] = fma(alpha, xv[k], xo[k]);
             }
-        }
-      } else if (back) {
-        cv.vlin(L.xt, alpha, L.d, L.x);
+          }
       }
       sy = cv.grp.sum(sy);
       ss = cv.grp.sum(ss);

@@ -248,7 +248,7 @@ struct Ctx {
   // extrapolation through the two known nodes). q_prev/q_cur are read from
   // the lane's workspace copies. With commit = false the pass runs (so that a
   // warp can run it convergently) but leaves C, the blocks and the guess of
-  // the lane untouched; T and G are scratch either way.
+  // the lane untouched; T, G and the axes are scratch either way.
   __device__ __noinline__ void setup(bool commit) const {
     const Ctx self(*this);
     self.setup_body(commit);
@@ -274,6 +274,12 @@ struct Ctx {
       link_fk(l, p >= 0 ? Pc : nullptr, q3, Tc, Jr);
       store12(L.T + 12 * l, Tp);
       store12(L.G + 12 * l, Tc);
+      {  // joint axes at q_cur, for the preconditioner blocks below
+        double w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0};
+        link_axes(l, Tc, Jr, w);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) ws[L.axes + 9 * l + k] = w[k];
+      }
       if (S == 1 && commit && B.tk) store12(L.tk + 12 * l, Tc);  // drag energy, contact
       double C[12];
 #pragma unroll
@@ -317,18 +323,13 @@ struct Ctx {
     }
     // joint blocks B_j = W^T I_o W, I_o = tr(Sig_o) I - Sig_o about the joint
     for (int l = 0; l < N; ++l) {
-      double T[12], Jr[9], w[9] = {0, 0, 0, 0, 0, 0, 0, 0, 0}, q[3];
-      load12(L.G + 12 * l, T);
-      const int nd = ndof(l), d0 = B.dof[l], jt = B.jtype[l];
-      if (nd == 3) {
-        for (int k = 0; k < 3; ++k) q[k] = ws[L.qc + d0 + k];
-        double R[9];
-        joint_rotation(jt, nullptr, q, R, Jr);
-      }
-      link_axes(l, T, Jr, w);
+      double w[9];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) w[k] = ws[L.axes + 9 * l + k];
+      const int nd = ndof(l), jt = B.jtype[l];
       double c[10];
       for (int k = 0; k < 10; ++k) c[k] = ws[L.T + 12 * l + k];
-      const double o[3] = {T[3], T[7], T[11]};
+      const double o[3] = {ws[L.G + 12 * l + 3], ws[L.G + 12 * l + 7], ws[L.G + 12 * l + 11]};
       const double h[3] = {c[6], c[7], c[8]}, m = c[9];
       const int ij[6][2] = {{0, 0}, {0, 1}, {0, 2}, {1, 1}, {1, 2}, {2, 2}};
       double So[9];
@@ -342,16 +343,18 @@ struct Ctx {
       double Io[9];
       for (int k = 0; k < 9; ++k) Io[k] = -So[k];
       Io[0] += tr; Io[4] += tr; Io[8] += tr;
-      double Bj[9], Pj[9];
+      double Bj[9], Pj[9], IW[9];
+      // B = W Io W^T with the axes as the rows of W: IW = Io W^T, then W IW
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int bb = 0; bb < 3; ++bb)
+          IW[3 * r + bb] = fma(Io[3 * r], w[3 * bb], fma(Io[3 * r + 1], w[3 * bb + 1], Io[3 * r + 2] * w[3 * bb + 2]));
 #pragma unroll
       for (int a = 0; a < 3; ++a)
 #pragma unroll
         for (int bb = 0; bb < 3; ++bb) {
-          double s = 0;
-#pragma unroll
-          for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int q_ = 0; q_ < 3; ++q_) s += w[3 * a + r] * Io[3 * r + q_] * w[3 * bb + q_];
+          const double s = fma(w[3 * a], IW[bb], fma(w[3 * a + 1], IW[3 + bb], w[3 * a + 2] * IW[6 + bb]));
           // translation: the subtree mass along orthonormal axes
           Bj[3 * a + bb] = jt == kTranslation ? (a == bb ? c[9] : 0.0) : s;
           // (hinge: only Bj[0] is used, w[0..2] being its axis)
