@@ -171,6 +171,20 @@ PBAD_API int pbad_batch_info(const pbad_batch* batch, int64_t* n_instances, int6
  * the instance-to-warp mapping knob the autotuner sets. */
 PBAD_API int pbad_batch_set_threads(pbad_batch* batch, int32_t threads);
 
+/* Instance queue of pbad_step / pbad_rollout (Section 5.2's dynamic
+ * assignment of work to the GPU's cores): when the L-BFGS buckets of a
+ * launch would need more blocks than max_blocks, they get max_blocks blocks
+ * in total (each bucket a share, at least one) and a group of lanes that has
+ * finished all steps of its instance takes the bucket's next unstarted
+ * instance from a device counter, so no lane idles while instances are left.
+ * max_blocks = 0 uses the number of blocks of the rollout kernel that the
+ * GPU keeps resident (less those of Newton buckets, which keep one warp per
+ * instance); max_blocks < 0 (the default) turns the queue off: one group per
+ * instance, the hardware block scheduler starts blocks as others finish.
+ * Results per instance do not depend on it. Errors: PBAD_ERR_ARG for a null
+ * batch. */
+PBAD_API int pbad_batch_set_queue(pbad_batch* batch, int32_t max_blocks);
+
 /* Objective and gradient of one step at given stage configurations
  * (Eq. EQ / Eq. EQHOC; gradient by Algorithm DERIV in world coordinates and,
  * for S >= 2, its tangent sweep: grad = 2 Jr^T r in O(N)).

@@ -160,6 +160,12 @@ class Batch:
         check(lib().pbad_batch_set_threads(self._h, int(threads)), "pbad_batch_set_threads")
         self.threads = int(threads)
 
+    def set_queue(self, max_blocks: int):
+        """Instance queue of the L-BFGS rollouts: at most max_blocks blocks,
+        groups take the next instance when done (0 = the GPU's resident
+        blocks; < 0 = off, the default)."""
+        check(lib().pbad_batch_set_queue(self._h, int(max_blocks)), "pbad_batch_set_queue")
+
     def pack(self, per_model, stages: int = 0):
         """Concatenates per-model arrays (count, n) (or (count, S, n)) into one
         flat array (numpy or torch, whatever was given)."""

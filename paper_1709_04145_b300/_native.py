@@ -18,7 +18,7 @@ SYMBOLS = ("pbad_version", "pbad_last_error", "pbad_colloc", "pbad_model_create"
            "pbad_batch_info", "pbad_eval_objective_grad", "pbad_step", "pbad_rollout",
            "pbad_fp64_peak", "pbad_eval_objective_grad_static", "pbad_step_backward",
            "pbad_link_points", "pbad_batch_set_threads", "pbad_model_set_drag",
-           "pbad_model_set_contact")
+           "pbad_model_set_contact", "pbad_batch_set_queue")
 
 
 class PBADError(RuntimeError):
@@ -55,6 +55,7 @@ def lib():
                                    i32, dp, dp, dp, dp, ip, ip, ip, ip, vp]
         L.pbad_fp64_peak.argtypes = [i32, C.POINTER(C.c_double)]
         L.pbad_batch_set_threads.argtypes = [vp, i32]
+        L.pbad_batch_set_queue.argtypes = [vp, i32]
         L.pbad_model_set_drag.argtypes = [vp, f64]
         L.pbad_model_set_contact.argtypes = [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                              f64, f64, f64]

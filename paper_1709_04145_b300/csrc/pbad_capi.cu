@@ -1,6 +1,7 @@
 // C ABI of the PBAD library (declarations and contracts: include/pbad.h).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -13,7 +14,8 @@
 namespace pbad {
 #define PBAD_DECL(S)                                                                \
   cudaError_t launch_eval_s##S(const LaunchArgs& A, int grid, cudaStream_t s);     \
-  cudaError_t launch_rollout_s##S(const LaunchArgs& A, int grid, cudaStream_t s);
+  cudaError_t launch_rollout_s##S(const LaunchArgs& A, int grid, cudaStream_t s);  \
+  int rollout_blocks_per_sm_s##S(const LaunchArgs& A, int threads);
 #define PBAD_DECL_BWD(S) cudaError_t launch_backward_s##S(const LaunchArgs& A, int grid, cudaStream_t s);
 PBAD_DECL_BWD(1)
 PBAD_DECL_BWD(2)
@@ -47,6 +49,16 @@ cudaError_t launch_backward(int S, const LaunchArgs& A, int grid, cudaStream_t s
     case 5: return launch_backward_s5(A, grid, s);
   }
   return cudaErrorInvalidValue;
+}
+int rollout_blocks_per_sm(int S, const LaunchArgs& A, int threads) {
+  switch (S) {
+    case 1: return rollout_blocks_per_sm_s1(A, threads);
+    case 2: return rollout_blocks_per_sm_s2(A, threads);
+    case 3: return rollout_blocks_per_sm_s3(A, threads);
+    case 4: return rollout_blocks_per_sm_s4(A, threads);
+    case 5: return rollout_blocks_per_sm_s5(A, threads);
+  }
+  return 0;
 }
 cudaError_t launch_rollout(int S, const LaunchArgs& A, int grid, cudaStream_t s) {
   switch (S) {
@@ -96,6 +108,11 @@ struct pbad_batch {
   size_t dense_doubles = 0;
   std::vector<size_t> dense_off;
   std::vector<int64_t> dense_stride;
+  // instance queue of the rollouts: one counter per bucket; queue_blocks = 0
+  // caps the L-BFGS buckets at the blocks the GPU keeps resident, > 0 at that
+  // many blocks, < 0 (the default) turns the queue off
+  int* d_queue = nullptr;
+  int queue_blocks = -1;
 };
 
 namespace {
@@ -345,6 +362,57 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
   return PBAD_OK;
 }
 
+// Instance queue: when the L-BFGS buckets need more blocks than the cap, each
+// gets a share of the cap (at least one block) and its groups, once done with
+// an instance, take the next one of the bucket from its queue counter.
+// Returns whether a queue is in use.
+bool apply_queue(pbad_batch* bt, int S, LaunchArgs* A, int* grid) {
+  const int nb = A->nb;
+  for (int k = 0; k < nb; ++k) {
+    A->bk[k].queue = nullptr;
+    A->bk[k].first_dynamic = 0;
+  }
+  if (bt->queue_blocks < 0 || !bt->d_queue) return false;
+  int blocks[kMaxBuckets];
+  int64_t lb_total = 0, other = 0;
+  int n_lb = 0;
+  for (int k = 0; k < nb; ++k) {
+    blocks[k] = (k + 1 < nb ? A->bk[k + 1].block_begin : *grid) - A->bk[k].block_begin;
+    if (A->bk[k].solver == PBAD_NEWTON) {
+      other += blocks[k];
+    } else {
+      lb_total += blocks[k];
+      ++n_lb;
+    }
+  }
+  if (n_lb == 0) return false;
+  int64_t cap = bt->queue_blocks;
+  if (cap == 0) {
+    const int per_sm = rollout_blocks_per_sm(S, *A, A->threads);
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, bt->device) != cudaSuccess)
+      sms = 0;
+    if (per_sm <= 0 || sms <= 0) return false;
+    cap = (int64_t)per_sm * sms - other;
+  }
+  if (cap < n_lb) cap = n_lb;
+  if (lb_total <= cap) return false;
+  const int wpb = A->threads / 32;
+  int begin = 0;
+  for (int k = 0; k < nb; ++k) {
+    int nbk = blocks[k];
+    if (A->bk[k].solver != PBAD_NEWTON) {
+      nbk = (int)std::max<int64_t>(1, (int64_t)blocks[k] * cap / lb_total);
+      A->bk[k].queue = bt->d_queue + k;
+      A->bk[k].first_dynamic = nbk * wpb * groups_per_warp(S);
+    }
+    A->bk[k].block_begin = begin;
+    begin += nbk;
+  }
+  *grid = begin;
+  return true;
+}
+
 int check_common(pbad_batch* bt, int32_t stages, double dt) {
   if (!bt) return fail(PBAD_ERR_ARG, "null batch");
   if (stages < 1 || stages > bt->max_stages)
@@ -395,6 +463,10 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   A.evals = evals;
   A.grads = grads;
   cudaStream_t s = (cudaStream_t)stream;
+  if (apply_queue(bt, stages, &A, &grid)) {
+    const cudaError_t e = cudaMemsetAsync(bt->d_queue, 0, sizeof(int) * kMaxBuckets, s);
+    if (e != cudaSuccess) return cuda_fail(e, "queue reset");
+  }
   const cudaError_t e = launch_rollout(stages, A, grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "rollout launch");
   return PBAD_OK;
@@ -648,12 +720,19 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
     delete bt;
     return cuda_fail(e, "cudaMemset");
   }
+  e = cudaMalloc(&bt->d_queue, sizeof(int) * kMaxBuckets);
+  if (e != cudaSuccess) {
+    cudaFree(bt->d_ws);
+    delete bt;
+    return fail(PBAD_ERR_ALLOC, std::string("queue cudaMalloc: ") + cudaGetErrorString(e));
+  }
   if (bt->dense_doubles) {
     e = cudaMalloc(&bt->d_dense, sizeof(double) * bt->dense_doubles);
     if (e == cudaSuccess) e = cudaMemset(bt->d_dense, 0, sizeof(double) * bt->dense_doubles);
     if (e != cudaSuccess) {
       cudaFree(bt->d_ws);
       cudaFree(bt->d_dense);
+      cudaFree(bt->d_queue);
       delete bt;
       return fail(PBAD_ERR_ALLOC, std::string("dense cudaMalloc: ") + cudaGetErrorString(e));
     }
@@ -667,7 +746,14 @@ int pbad_batch_destroy(pbad_batch* bt) {
   DeviceGuard dg(bt->device);
   cudaFree(bt->d_ws);
   cudaFree(bt->d_dense);
+  cudaFree(bt->d_queue);
   delete bt;
+  return PBAD_OK;
+}
+
+int pbad_batch_set_queue(pbad_batch* bt, int32_t max_blocks) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  bt->queue_blocks = max_blocks;
   return PBAD_OK;
 }
 

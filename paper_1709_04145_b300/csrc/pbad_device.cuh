@@ -42,7 +42,12 @@ struct Bucket {
   double* ws;            // lane workspace
   int64_t ws_lane;       // doubles per lane in the workspace (its layout's total)
   int block_begin;       // first block of the launch that serves this bucket
-  int solver;            // 0 L-BFGS, 1 Newton
+  int solver;            // 0 L-BFGS, 1 Newton, 2 L-BFGS with the binary32 direction
+  // instance queue (L-BFGS rollouts): the launch's groups start on instances
+  // 0 .. first_dynamic - 1; a group that finishes its instance takes
+  // first_dynamic + atomicAdd(queue, 1) while that is below count
+  int* queue;            // device counter, zeroed before the launch (null = no queue)
+  int first_dynamic;
   int chain;             // 1 if parent[l] == l - 1 for every link (serial chain)
   double* dense;         // per-instance dense Newton/adjoint storage (or null)
   int64_t dense_stride;  // doubles per instance in `dense`

@@ -70,14 +70,14 @@ template <int S, bool F32>
 __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B) {
   const LaneId<S> id(B);
   const bool active = id.real && id.inst < B.count;
-  const int b = active ? (int)id.inst : 0;
+  int b = active ? (int)id.inst : 0;
   const int m = A.history;
   constexpr bool f32 = F32;  // binary32 two-loop recursion (PBAD_LBFGS_F32)
   Ctx<S> c(B, A.K, b, id.lane_id, m);
   // c goes to the non-inlined passes; cv, a private copy used by the inline
   // helpers only, keeps the layout and lane fields in registers across the
   // workspace stores of the solver bookkeeping.
-  const Ctx<S> cv(c);
+  Ctx<S> cv(c);
   const int n = c.n;
   const WsLayout L = c.L;
   const Lane ws = c.ws;
@@ -94,6 +94,40 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
   const int max_evals = 4 * A.max_iter + kLsMax;  // evaluations per step
   c.setup(true);
   if (!active) phase = kDone;
+
+  // outputs of the group's instance once its last step has ended
+  auto finish_instance = [&]() {
+    if (cv.i == 0) {
+      if (A.status) A.status[B.inst_off + b] = worst;
+      if (A.iters) A.iters[B.inst_off + b] = iters_total;
+      if (A.evals) A.evals[B.inst_off + b] = evals_total;
+      if (A.grads) A.grads[B.inst_off + b] = grads_total;
+      for (int d = 0; d < n; ++d) {
+        if (A.q_prev_out) A.q_prev_out[cv.gdof(d)] = ws[L.qp + d];
+        if (A.q_cur_out) A.q_cur_out[cv.gdof(d)] = ws[L.qc + d];
+      }
+    }
+  };
+  // the next instance of the bucket's queue (group-uniform; the group's
+  // lanes call it together): rebinds the contexts and loads its state
+  auto next_instance = [&]() -> bool {
+    if (!B.queue) return false;
+    int nb = 0;
+    if (cv.i == 0) nb = B.first_dynamic + atomicAdd(B.queue, 1);
+    nb = __shfl_sync(cv.grp.mask, nb, cv.grp.src(0));
+    if (nb >= B.count) return false;
+    b = nb;
+    c.b = nb;
+    cv.b = nb;
+    for (int d = 0; d < n; ++d) {
+      ws[L.qp + d] = A.q_prev0[cv.gdof(d)];
+      ws[L.qc + d] = A.q_cur0[cv.gdof(d)];
+    }
+    step = 0;
+    worst = kConverged;
+    iters_total = evals_total = grads_total = 0;
+    return true;
+  };
 
   while (__any_sync(kAll, phase != kDone)) {
     const double* tau = A.tau ? A.tau + (int64_t)min(step, A.n_steps - 1) * D : nullptr;
@@ -301,6 +335,10 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
       if (fin) {
         ++step;
         next = step < A.n_steps;
+        if (!next) {
+          finish_instance();
+          next = next_instance();
+        }
         phase = next ? kFirst : kDone;
       }
       if (__any_sync(kAll, next)) c.setup(next);
@@ -370,20 +408,6 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
         trials = 0;
         cv.vlin(L.xt, 1.0, L.d, L.x);
         phase = kTrial;
-      }
-    }
-  }
-  if (active && cv.i == 0) {
-    if (A.status) A.status[B.inst_off + b] = worst;
-    if (A.iters) A.iters[B.inst_off + b] = iters_total;
-    if (A.evals) A.evals[B.inst_off + b] = evals_total;
-    if (A.grads) A.grads[B.inst_off + b] = grads_total;
-  }
-  if (active) {
-    for (int d = 0; d < n; ++d) {
-      if (cv.i == 0) {
-        if (A.q_prev_out) A.q_prev_out[cv.gdof(d)] = ws[L.qp + d];
-        if (A.q_cur_out) A.q_cur_out[cv.gdof(d)] = ws[L.qc + d];
       }
     }
   }
@@ -733,6 +757,19 @@ cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cu
   else if (kinds == 4) k_rollout<PBAD_S, 3><<<grid, A.threads, 0, s>>>(A);
   else k_rollout<PBAD_S, 2><<<grid, A.threads, 0, s>>>(A);
   return cudaGetLastError();
+}
+// Blocks of the rollout kernel variant that serves these buckets that one
+// SM keeps resident at `threads` threads per block (0 on error).
+int PBAD_CAT(rollout_blocks_per_sm_s, PBAD_S)(const LaunchArgs& A, int threads) {
+  int kinds = 0;
+  for (int k = 0; k < A.nb; ++k) kinds |= 1 << A.bk[k].solver;
+  int n = 0;
+  cudaError_t e;
+  if (kinds == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 0>, threads, 0);
+  else if (kinds == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 1>, threads, 0);
+  else if (kinds == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 3>, threads, 0);
+  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 2>, threads, 0);
+  return e == cudaSuccess ? n : 0;
 }
 #if PBAD_S == 1
 cudaError_t launch_link_points(const LaunchArgs& A, int grid, cudaStream_t s) {

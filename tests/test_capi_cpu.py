@@ -102,3 +102,8 @@ def test_header_constants_match_binding():
         (I.HINGE, I.BALL, I.TRANSLATION)
     for code, name in P.STATUS.items():
         assert defs["PBAD_" + name] == code
+
+
+def test_queue_setter_rejects_null_batch():
+    from paper_1709_04145_b300._native import lib
+    assert lib().pbad_batch_set_queue(None, 0) != 0
