@@ -213,10 +213,18 @@ class ClockSampler:
 
 
 # ------------------------------------------------------------------- oracle
-def _oracle_instance(job):
-    """Runs the CPU oracle on one instance (spawned worker)."""
-    import numpy as np
+def _oracle_worker_init():
+    """Pool initializer: imports the oracle and loads its library, so that the
+    timed map runs no imports or builds."""
     sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    O.lib()
+
+
+def _oracle_instance(job):
+    """Runs the CPU oracle on one instance (spawned worker); returns its
+    compute seconds, iterations and evaluations."""
+    import numpy as np
     from oracle import oracle as O
     spec, b, qp, qc, S, dt, m, tol, max_iter, n_steps = job
     om = O.OracleModel.from_spec(spec, b)
@@ -225,29 +233,52 @@ def _oracle_instance(job):
     return time.perf_counter() - t0, res["iters"], res["evals"]
 
 
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                if line.startswith("model name"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
 def cpu_oracle_rate(w, n_inst, n_steps, budget_s):
     """Oracle link-steps/s on the host cores over a bounded sample: the first
-    instances of the workload, n_steps time steps each, one process per core
-    (spawn). Returns (rate, cores, sample description)."""
+    n_inst instances of the workload, one process per core (spawn; started,
+    imported and warmed before the timed map). n_steps = 0 picks the number
+    of time steps so that the timed map takes about budget_s seconds, from
+    the warm-up's seconds per instance-step. Returns (rate, cores, sample
+    description)."""
     import multiprocessing as mp
-    import numpy as np
     from oracle import oracle as O
     spec = w["spec"]
     S, dt = w["stages"], w["dt"]
     nodes, _ = O.colloc(S)
     qp = w["q0"] + nodes[0] * dt * w["qd0"]
-    cores = os.cpu_count() or 1
-    jobs = [(spec.select([b]), 0, qp[b], w["q0"][b], S, dt, w["history"], w["tol"], w["max_iter"],
-             n_steps) for b in range(n_inst)]
+    procs = min(os.cpu_count() or 1, n_inst)
+
+    def job(b, steps):
+        return (spec.select([b]), 0, qp[b], w["q0"][b], S, dt, w["history"], w["tol"],
+                w["max_iter"], steps)
+
     ctx = mp.get_context("spawn")
-    t0 = time.perf_counter()
-    with ctx.Pool(min(cores, n_inst)) as pool:
-        res = pool.map(_oracle_instance, jobs)
-    wall = time.perf_counter() - t0
+    with ctx.Pool(procs, initializer=_oracle_worker_init) as pool:
+        warm = pool.map(_oracle_instance, [job(b, 1) for b in range(procs)], chunksize=1)
+        per_step = max(sum(r[0] for r in warm) / len(warm), 1e-6)
+        if n_steps <= 0:
+            n_steps = int(budget_s * procs / (n_inst * per_step))
+            n_steps = max(1, min(n_steps, w["n_steps"]))
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_instance, [job(b, n_steps) for b in range(n_inst)], chunksize=1)
+        wall = time.perf_counter() - t0
     link_steps = n_inst * spec.n_links * n_steps
-    sample = (f"{n_inst} of {spec.count} instances x {n_steps} of {w['n_steps']} time steps, "
-              f"same solver settings; {wall:.1f} s wall on {min(cores, n_inst)} processes")
-    return link_steps / wall, min(cores, n_inst), sample
+    sample = (f"{n_inst} of {spec.count} instances x the first {n_steps} of {w['n_steps']} time "
+              f"steps, same solver settings; {wall:.1f} s wall on {procs} processes "
+              f"({sum(r[0] for r in res):.1f} s of oracle compute), {_cpu_model()}, "
+              f"nproc {os.cpu_count()}")
+    return link_steps / wall, procs, sample
 
 
 # --------------------------------------------------------------------- ours
@@ -853,7 +884,7 @@ def run_ours(args):
     if rank == 0 and args.dt_sweep:
         line["dt_sweep"] = measure_dt_sweep(P, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        rate, cores, sample = cpu_oracle_rate(w, n_inst=min(os.cpu_count() or 1, 16), n_steps=1,
+        rate, cores, sample = cpu_oracle_rate(w, n_inst=min(os.cpu_count() or 1, 16), n_steps=0,
                                               budget_s=args.cpu_sample_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample}
@@ -876,7 +907,8 @@ def run_reference(args):
     rates = []
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        r, cores, sample = cpu_oracle_rate(w, n_inst=n_inst, n_steps=1, budget_s=args.cpu_sample_seconds)
+        r, cores, sample = cpu_oracle_rate(w, n_inst=n_inst, n_steps=0,
+                                           budget_s=args.cpu_sample_seconds)
         rates.append(r)
     wall = time.perf_counter() - t0
     value = statistics.median(rates)
