@@ -398,6 +398,11 @@ def measure_adjoint(P, args, dev):
     kw = dict(dt=w["dt"], stages=S, solver=P.NEWTON, tol=w["tol"], max_iter=100,
               checkpoint_every=w["checkpoint_every"])
     ev = lambda: torch.cuda.Event(enable_timing=True)
+    # warm-up: the first forward and adjoint launches in a process load their
+    # kernels and the allocator's blocks (several seconds, once)
+    qw, _, _ = rollout_differentiable(batch, x0, v0, tt[:2], **kw)
+    ((points_differentiable(batch, qw, [w["ee_link"]], tip) - target) ** 2).sum().backward()
+    x0.grad = v0.grad = tt.grad = None
     torch.cuda.synchronize()
     a, b = ev(), ev()
     a.record()

@@ -76,17 +76,20 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
   Ctx<S> c(B, A.K, b, id.lane_id, m);
   // c goes to the non-inlined passes; cv, a private copy used by the inline
   // helpers only, keeps the layout and lane fields in registers across the
-  // workspace stores of the solver bookkeeping.
-  Ctx<S> cv(c);
+  // workspace stores of the solver bookkeeping. Addresses of the group's
+  // instance in the caller's arrays follow b (the queue may move it).
+  const Ctx<S> cv(c);
   const int n = c.n;
   const WsLayout L = c.L;
   const Lane ws = c.ws;
   const int64_t D = A.D;
   constexpr unsigned kAll = 0xffffffffu;
+  auto gdof = [&](int d) { return B.dof_off + (int64_t)b * n + d; };
+  auto gstage = [&](int d) { return (int64_t)S * B.dof_off + ((int64_t)b * S + cv.i) * n + d; };
 
   for (int d = 0; d < n; ++d) {
-    ws[L.qp + d] = A.q_prev0[cv.gdof(d)];
-    ws[L.qc + d] = A.q_cur0[cv.gdof(d)];
+    ws[L.qp + d] = A.q_prev0[gdof(d)];
+    ws[L.qc + d] = A.q_cur0[gdof(d)];
   }
   int step = 0, phase = kFirst, k = 0, trials = 0, nh = 0, head = 0, step_evals = 0;
   int worst = kConverged, iters_total = 0, evals_total = 0, grads_total = 0;
@@ -103,8 +106,8 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
       if (A.evals) A.evals[B.inst_off + b] = evals_total;
       if (A.grads) A.grads[B.inst_off + b] = grads_total;
       for (int d = 0; d < n; ++d) {
-        if (A.q_prev_out) A.q_prev_out[cv.gdof(d)] = ws[L.qp + d];
-        if (A.q_cur_out) A.q_cur_out[cv.gdof(d)] = ws[L.qc + d];
+        if (A.q_prev_out) A.q_prev_out[gdof(d)] = ws[L.qp + d];
+        if (A.q_cur_out) A.q_cur_out[gdof(d)] = ws[L.qc + d];
       }
     }
   };
@@ -118,10 +121,9 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     if (nb >= B.count) return false;
     b = nb;
     c.b = nb;
-    cv.b = nb;
     for (int d = 0; d < n; ++d) {
-      ws[L.qp + d] = A.q_prev0[cv.gdof(d)];
-      ws[L.qc + d] = A.q_cur0[cv.gdof(d)];
+      ws[L.qp + d] = A.q_prev0[gdof(d)];
+      ws[L.qc + d] = A.q_cur0[gdof(d)];
     }
     step = 0;
     worst = kConverged;
@@ -325,10 +327,10 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
           ws[L.qp + d] = xp;
           ws[L.qc + d] = xs;
           if (cv.i == 0) {
-            if (A.traj_cur) A.traj_cur[(int64_t)step * D + cv.gdof(d)] = xs;
-            if (A.traj_prev) A.traj_prev[(int64_t)step * D + cv.gdof(d)] = xp;
+            if (A.traj_cur) A.traj_cur[(int64_t)step * D + gdof(d)] = xs;
+            if (A.traj_prev) A.traj_prev[(int64_t)step * D + gdof(d)] = xp;
           }
-          if (A.q_stages_out && step == A.n_steps - 1) A.q_stages_out[cv.gstage(d)] = xv;
+          if (A.q_stages_out && step == A.n_steps - 1) A.q_stages_out[gstage(d)] = xv;
         }
       }
       bool next = false;
