@@ -257,6 +257,7 @@ def cpu_oracle_rate(w, n_inst, n_steps, budget_s):
     S, dt = w["stages"], w["dt"]
     nodes, _ = O.colloc(S)
     qp = w["q0"] + nodes[0] * dt * w["qd0"]
+    n_inst = min(n_inst, spec.count)
     procs = min(os.cpu_count() or 1, n_inst)
 
     def job(b, steps):
