@@ -82,6 +82,7 @@ def lib():
         L.om_rnea.argtypes = [vp, dp, dp, dp, dp]
         L.om_rk4.restype = C.c_int
         L.om_rk4.argtypes = [vp, dp, dp, dp, C.c_double, C.c_int]
+        L.om_deriv.argtypes = [vp, dp, dp, dp]
         L.om_lbfgs_direction.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp,
                                          C.c_double, dp, dp, C.c_int, dp]
         _lib = L
@@ -238,6 +239,15 @@ class OracleModel:
         out = np.zeros((self.n_dof, 4, 4))
         lib().om_link_dT(self._h, qp, l, out.ctypes.data_as(C.POINTER(C.c_double)))
         return out
+
+    def deriv(self, q, G):
+        """Algorithm DERIV (O(N)): d/dq of sum_l <G_l, T_l(q)> for fixed 3x4
+        seeds G (N, 3, 4). Returns (n,)."""
+        q, qp = _d(q)
+        G, gp = _d(np.asarray(G, dtype=np.float64).reshape(-1, 12))
+        r = np.zeros(self.n_dof)
+        lib().om_deriv(self._h, qp, gp, r.ctypes.data_as(C.POINTER(C.c_double)))
+        return r
 
     def link_ddT(self, q, l: int, d: int, e: int):
         q, qp = _d(q)

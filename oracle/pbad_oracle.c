@@ -468,6 +468,50 @@ void om_link_dT(void *p, const double *q, int l, double *dT) {
   free(F); free(pre); free(suf);
 }
 
+/* Algorithm DERIV in tree form (Section 5), the O(N) counterpart of the
+ * path derivatives above: r_d = d/dq_d sum_l <G_l, T_l(q)> for fixed 3x4
+ * seeds G_l (<A, B> = sum of entrywise products). From the leaves to the
+ * root, Y_a = G_a + sum over the children c of a of Y_c F_c^T, with F_c =
+ * X_c Jm_c(q_c) the child's local transform; for a DOF k of joint a,
+ * r = <Y_a, T_parent(a) X_a dJm_a/dq_k>. The chain rule needs no product
+ * along a root-to-link path. G: [N][12] row-major 3x4; r: [n]. */
+void om_deriv(void *p, const double *q, const double *G, double *r) {
+  om_model *m = (om_model *)p;
+  int N = m->n_links;
+  double *F = (double *)malloc(sizeof(double) * 16 * N);
+  double *T = (double *)malloc(sizeof(double) * 16 * N);
+  double *Y = (double *)malloc(sizeof(double) * 16 * N);
+  for (int a = 0; a < N; ++a) { /* parent[a] < a */
+    joint_factor(m, a, q, F + 16 * a);
+    if (m->parent[a] < 0) memcpy(T + 16 * a, F + 16 * a, sizeof(double) * 16);
+    else m4_mul(T + 16 * m->parent[a], F + 16 * a, T + 16 * a);
+    for (int i = 0; i < 12; ++i) Y[16 * a + i] = G[12 * a + i];
+    for (int i = 12; i < 16; ++i) Y[16 * a + i] = 0.0;
+  }
+  for (int a = N - 1; a >= 0; --a) { /* children before their parents */
+    int pa = m->parent[a];
+    for (int k = 0; k < m->ndof[a]; ++k) {
+      double Fd[16], PD[16];
+      joint_factor_d(m, a, q, k, Fd);
+      if (pa >= 0) m4_mul(T + 16 * pa, Fd, PD);
+      else memcpy(PD, Fd, sizeof(PD));
+      double s = 0.0;
+      for (int i = 0; i < 16; ++i) s += Y[16 * a + i] * PD[i];
+      r[m->dof_off[a] + k] = s;
+    }
+    if (pa >= 0) {
+      /* Y_parent += Y_a F_a^T */
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          double s = 0.0;
+          for (int t = 0; t < 4; ++t) s += Y[16 * a + 4 * i + t] * F[16 * a + 4 * j + t];
+          Y[16 * pa + 4 * i + j] += s;
+        }
+    }
+  }
+  free(F); free(T); free(Y);
+}
+
 /* Accumulates H[d][e] += sum over (d,e) on the root->l path of
  * (d2 T_l / dq_d dq_e) : G, with G a 3x4 (12 entries) matrix. H: [n][n]. */
 static void link_ddT_contract(const om_model *m, int l, const double *q,
