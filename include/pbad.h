@@ -178,11 +178,11 @@ PBAD_API int pbad_batch_set_threads(pbad_batch* batch, int32_t threads);
  * finished all steps of its instance takes the bucket's next unstarted
  * instance from a device counter, so no lane idles while instances are left.
  * max_blocks = 0 uses the number of blocks of the rollout kernel that the
- * GPU keeps resident (less those of Newton buckets, which keep one warp per
- * instance); max_blocks < 0 (the default) turns the queue off: one group per
- * instance, the hardware block scheduler starts blocks as others finish.
- * Results per instance do not depend on it. Errors: PBAD_ERR_ARG for a null
- * batch. */
+ * GPU keeps resident; max_blocks < 0 (the default) turns the queue off: one
+ * group per instance, the hardware block scheduler starts blocks as others
+ * finish. The queue serves launches whose buckets all use one L-BFGS solver
+ * (PBAD_LBFGS or PBAD_LBFGS_F32); other launches ignore it. Results per
+ * instance do not depend on it. Errors: PBAD_ERR_ARG for a null batch. */
 PBAD_API int pbad_batch_set_queue(pbad_batch* batch, int32_t max_blocks);
 
 /* Objective and gradient of one step at given stage configurations

@@ -373,6 +373,10 @@ bool apply_queue(pbad_batch* bt, int S, LaunchArgs* A, int* grid) {
     A->bk[k].first_dynamic = 0;
   }
   if (bt->queue_blocks < 0 || !bt->d_queue) return false;
+  // the queue variants serve launches whose buckets all use one L-BFGS kind
+  for (int k = 1; k < nb; ++k)
+    if (A->bk[k].solver != A->bk[0].solver) return false;
+  if (A->bk[0].solver == PBAD_NEWTON) return false;
   int blocks[kMaxBuckets];
   int64_t lb_total = 0, other = 0;
   int n_lb = 0;

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(128) k_eval(const __grid_constant__ LaunchArgs
 // predicates, so groups in different phases share one pass over the
 // workspace instead of taking turns through divergent branches.
 // ------------------------------------------------------------------------
-template <int S, bool F32>
+template <int S, bool F32, bool QUEUE>
 __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B) {
   const LaneId<S> id(B);
   const bool active = id.real && id.inst < B.count;
@@ -112,7 +112,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     }
   };
   // the next instance of the bucket's queue (group-uniform; the group's
-  // lanes call it together): rebinds the contexts and loads its state
+  // lanes call it together): rebinds the context and loads its state
   auto next_instance = [&]() -> bool {
     if (!B.queue) return false;
     int nb = 0;
@@ -337,9 +337,11 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
       if (fin) {
         ++step;
         next = step < A.n_steps;
-        if (!next) {
-          finish_instance();
-          next = next_instance();
+        if constexpr (QUEUE) {
+          if (!next) {
+            finish_instance();
+            next = next_instance();
+          }
         }
         phase = next ? kFirst : kDone;
       }
@@ -412,6 +414,9 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
         phase = kTrial;
       }
     }
+  }
+  if constexpr (!QUEUE) {
+    if (active) finish_instance();
   }
 }
 
@@ -597,17 +602,21 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
 // its bucket (L-BFGS, Newton or L-BFGS with the binary32 direction), so an
 // uneven batch with mixed solvers is a single persistent launch. SOLVERS
 // selects the variant: 0 every bucket L-BFGS, 1 every bucket Newton, 3 every
-// bucket binary32-direction L-BFGS, 2 mixed. The single-solver variants
-// carry only their own solver's code and registers.
+// bucket binary32-direction L-BFGS, 2 mixed; 4 and 5 are 0 and 3 with the
+// instance queue. The single-solver variants carry only their own solver's
+// code and registers (the queue's rebinding costs the others ~8% on large
+// batches, hence its own variants).
 template <int S, int SOLVERS>
 __global__ void __maxnreg__(255) k_rollout(const __grid_constant__ LaunchArgs A) {
   const Bucket& B = A.bk[find_bucket(A)];
-  if (SOLVERS == 0) rollout_lbfgs<S, false>(A, B);
+  if (SOLVERS == 0) rollout_lbfgs<S, false, false>(A, B);
   else if (SOLVERS == 1) rollout_newton<S>(A, B);
-  else if (SOLVERS == 3) rollout_lbfgs<S, true>(A, B);
+  else if (SOLVERS == 3) rollout_lbfgs<S, true, false>(A, B);
+  else if (SOLVERS == 4) rollout_lbfgs<S, false, true>(A, B);
+  else if (SOLVERS == 5) rollout_lbfgs<S, true, true>(A, B);
   else if (B.solver == 1) rollout_newton<S>(A, B);
-  else if (B.solver == 2) rollout_lbfgs<S, true>(A, B);
-  else rollout_lbfgs<S, false>(A, B);
+  else if (B.solver == 2) rollout_lbfgs<S, true, false>(A, B);
+  else rollout_lbfgs<S, false, false>(A, B);
 }
 
 // ------------------------------------------------------------------------
@@ -754,23 +763,31 @@ cudaError_t PBAD_CAT(launch_backward_s, PBAD_S)(const LaunchArgs& A, int grid, c
 cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
   int kinds = 0;  // bit per solver present
   for (int k = 0; k < A.nb; ++k) kinds |= 1 << A.bk[k].solver;
-  if (kinds == 1) k_rollout<PBAD_S, 0><<<grid, A.threads, 0, s>>>(A);
-  else if (kinds == 2) k_rollout<PBAD_S, 1><<<grid, A.threads, 0, s>>>(A);
-  else if (kinds == 4) k_rollout<PBAD_S, 3><<<grid, A.threads, 0, s>>>(A);
-  else k_rollout<PBAD_S, 2><<<grid, A.threads, 0, s>>>(A);
+  const bool queue = A.bk[0].queue != nullptr;  // set for single-kind L-BFGS launches only
+  if (kinds == 1) {
+    if (queue) k_rollout<PBAD_S, 4><<<grid, A.threads, 0, s>>>(A);
+    else k_rollout<PBAD_S, 0><<<grid, A.threads, 0, s>>>(A);
+  } else if (kinds == 2) {
+    k_rollout<PBAD_S, 1><<<grid, A.threads, 0, s>>>(A);
+  } else if (kinds == 4) {
+    if (queue) k_rollout<PBAD_S, 5><<<grid, A.threads, 0, s>>>(A);
+    else k_rollout<PBAD_S, 3><<<grid, A.threads, 0, s>>>(A);
+  } else {
+    k_rollout<PBAD_S, 2><<<grid, A.threads, 0, s>>>(A);
+  }
   return cudaGetLastError();
 }
-// Blocks of the rollout kernel variant that serves these buckets that one
-// SM keeps resident at `threads` threads per block (0 on error).
+// Blocks of the queue variant of the rollout kernel for these buckets (all
+// binary64 or all binary32-direction L-BFGS) that one SM keeps resident at
+// `threads` threads per block (0 on error or for other bucket mixes).
 int PBAD_CAT(rollout_blocks_per_sm_s, PBAD_S)(const LaunchArgs& A, int threads) {
   int kinds = 0;
   for (int k = 0; k < A.nb; ++k) kinds |= 1 << A.bk[k].solver;
   int n = 0;
   cudaError_t e;
-  if (kinds == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 0>, threads, 0);
-  else if (kinds == 2) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 1>, threads, 0);
-  else if (kinds == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 3>, threads, 0);
-  else e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 2>, threads, 0);
+  if (kinds == 1) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 4>, threads, 0);
+  else if (kinds == 4) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_rollout<PBAD_S, 5>, threads, 0);
+  else return 0;
   return e == cudaSuccess ? n : 0;
 }
 #if PBAD_S == 1

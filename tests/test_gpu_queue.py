@@ -54,18 +54,28 @@ def test_queue_bitwise_equals_static_assignment(S):
         _assert_same(got, ref)
 
 
-def test_queue_with_newton_and_binary32_buckets():
-    """Newton buckets keep one warp per instance; the L-BFGS buckets (binary64
-    and binary32 direction) share the capped blocks."""
+def test_queue_with_binary32_direction_buckets():
+    """Two buckets on the binary32-direction L-BFGS share the capped blocks."""
     import paper_1709_04145_b300 as P
-    specs = [I.humanoid(3, seed=72), I.rod_chain(90, 4, name="rod4"),
-             I.ball_chain(70, 3, seed=73, radius=0.2)]
-    batch = P.Batch([P.Model.from_spec(s) for s in specs], max_stages=2, max_history=8, newton=True)
+    specs = [I.rod_chain(90, 4, name="rod4"), I.ball_chain(70, 3, seed=73, radius=0.2)]
+    batch = P.Batch([P.Model.from_spec(s) for s in specs], max_stages=2, max_history=8)
     n_steps, dt, S = 3, 0.02, 2
     _, _, _, qp, qc, tau = _inputs(specs, S, dt, n_steps, 710)
-    solvers = [P.NEWTON, P.LBFGS, P.LBFGS_F32]
+    ref = _run(P, batch, qp, qc, tau, n_steps, dt, S, P.LBFGS_F32, -1, 100)
+    got = _run(P, batch, qp, qc, tau, n_steps, dt, S, P.LBFGS_F32, 2, 100)
+    _assert_same(got, ref)
+
+
+def test_queue_ignored_by_mixed_solver_launches():
+    """A launch with Newton and L-BFGS buckets runs without the queue."""
+    import paper_1709_04145_b300 as P
+    specs = [I.humanoid(3, seed=72), I.rod_chain(90, 4, name="rod4")]
+    batch = P.Batch([P.Model.from_spec(s) for s in specs], max_stages=2, max_history=8, newton=True)
+    n_steps, dt, S = 2, 0.02, 2
+    _, _, _, qp, qc, tau = _inputs(specs, S, dt, n_steps, 715)
+    solvers = [P.NEWTON, P.LBFGS]
     ref = _run(P, batch, qp, qc, tau, n_steps, dt, S, solvers, -1, 100)
-    got = _run(P, batch, qp, qc, tau, n_steps, dt, S, solvers, 2, 100)
+    got = _run(P, batch, qp, qc, tau, n_steps, dt, S, solvers, 1, 100)
     _assert_same(got, ref)
 
 
