@@ -232,11 +232,37 @@ __device__ __forceinline__ ExpCoef exp_coef(double x) {
   return e;
 }
 
+// x-derivatives of b and h at x, from a = sin(phi)/phi and c = cos(phi) as
+// exp_coef returns them: the same power series below x = 1, and above it
+// db = (x a - 2 (1 - c)) / (2 x^2), dh = (3 a - 2 - c) / (2 x^2) (phi s = x a).
+__device__ __forceinline__ void exp_coef_deriv(double x, double a, double c, double* db, double* dh) {
+  if (x < 1.0) {
+    const double ib[10] = {1.0 / 2, -1.0 / 24, 1.0 / 720, -1.0 / 40320, 1.0 / 3628800,
+                           -1.0 / 479001600, 1.0 / 87178291200.0, -1.0 / 20922789888000.0,
+                           1.0 / 6402373705728000.0, -1.0 / 2432902008176640000.0};
+    const double ih[10] = {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800,
+                           -1.0 / 6227020800.0, 1.0 / 1307674368000.0, -1.0 / 355687428096000.0,
+                           1.0 / 121645100408832000.0, -1.0 / 51090942171709440000.0};
+    double dB = 9 * ib[9], dH = 9 * ih[9];
+#pragma unroll
+    for (int k = 8; k >= 1; --k) {
+      dB = fma(dB, x, k * ib[k]);
+      dH = fma(dH, x, k * ih[k]);
+    }
+    *db = dB;
+    *dh = dH;
+  } else {
+    const double h2 = 0.5 / (x * x);
+    *db = (x * a - 2.0 * (1.0 - c)) * h2;
+    *dh = (3.0 * a - 2.0 - c) * h2;
+  }
+}
+
 // Joint rotation (and, for balls, the right Jacobian Jr) of one joint.
 //   hinge: R = Rot(u, q), world axis w = R_link u
 //   ball:  R = exp([theta]x), world axes w_k = R_link Jr(theta) e_k
-// ec (optional) receives the exponential-map coefficients with their
-// derivatives, for the tangent passes at the same configuration.
+// ec (optional) receives the exponential-map coefficients (c, a, b, h), for
+// the tangent passes at the same configuration.
 __device__ __forceinline__ void joint_rotation(int jt, const double* u, const double* q, double* R,
                                                double* Jr, ExpCoef* ec = nullptr) {
   if (jt == 0) {
@@ -252,7 +278,7 @@ __device__ __forceinline__ void joint_rotation(int jt, const double* u, const do
     }
   } else {
     const double x = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
-    const ExpCoef e = ec ? exp_coef<true>(x) : exp_coef<false>(x);
+    const ExpCoef e = exp_coef<false>(x);
     if (ec) *ec = e;
     rodrigues(q, e.c, e.a, e.b, R);
     // Jr = (1 - h x) I - b [theta]x + h theta theta^T
@@ -260,36 +286,30 @@ __device__ __forceinline__ void joint_rotation(int jt, const double* u, const do
   }
 }
 
-// Derivative of Jr along v: -2 (theta.v) b' K - b [v]x + 2 (theta.v) h' K^2 + h ([v]x K + K [v]x)
-// with K = [theta]x and K^2 = theta theta^T - x I.
-// (b, h, db, dh) of the exponential map at th, as cached by the residual pass.
-__device__ __forceinline__ void jr_tangent(const double* th, const double* v, const double* bh,
-                                           double* dJ) {
+// dJr^T u, the derivative of Jr along v contracted with u, without forming
+// dJr = -2 (theta.v) b' K - b [v]x + 2 (theta.v) h' K^2 + h ([v]x K + K [v]x)
+// (K = [theta]x, K^2 = theta theta^T - x I, [v]x K + K [v]x = v theta^T +
+// theta v^T - 2 (v.theta) I): the transposes act on u as K^T u = u x theta,
+// [v]x^T u = u x v, and the symmetric parts directly. cab = (c, a, b, h) of
+// the exponential map at th, as cached by the residual pass.
+__device__ __forceinline__ void jr_tangent_dot(const double* th, const double* v, const double* cab,
+                                               const double* u, double* z) {
   const double x = fma(th[0], th[0], fma(th[1], th[1], th[2] * th[2]));
-  ExpCoef e;
-  e.b = bh[0];
-  e.h = bh[1];
-  e.db = bh[2];
-  e.dh = bh[3];
-  const double tv = dot3(th, v);
-  const double cb = -2.0 * tv * e.db, ch = 2.0 * tv * e.dh;
-  // [v]x K + K [v]x = v th^T + th v^T - 2 (v.th) I
-  double K[9], K2[9], VK[9], Vx[9];
-  K[0] = 0; K[1] = -th[2]; K[2] = th[1];
-  K[3] = th[2]; K[4] = 0; K[5] = -th[0];
-  K[6] = -th[1]; K[7] = th[0]; K[8] = 0;
-  Vx[0] = 0; Vx[1] = -v[2]; Vx[2] = v[1];
-  Vx[3] = v[2]; Vx[4] = 0; Vx[5] = -v[0];
-  Vx[6] = -v[1]; Vx[7] = v[0]; Vx[8] = 0;
+  double db, dh;
+  exp_coef_deriv(x, cab[1], cab[0], &db, &dh);
+  const double b = cab[2], h = cab[3];
+  const double tv = dot3(th, v), tu = dot3(th, u), vu = dot3(v, u);
+  const double cb = -2.0 * tv * db, ch = 2.0 * tv * dh;
+  double ut[3], uv[3];
+  cross(u, th, ut);
+  cross(u, v, uv);
+  // ch (theta tu - x u) + h (v tu + theta vu - 2 tv u)
+  const double cu = -fma(ch, x, 2.0 * h * tv);
+  const double ct = fma(ch, tu, h * vu);
+  const double cv = h * tu;
 #pragma unroll
   for (int r = 0; r < 3; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      K2[3 * r + c] = th[r] * th[c] - (r == c ? x : 0.0);
-      VK[3 * r + c] = v[r] * th[c] + th[r] * v[c] - (r == c ? 2.0 * tv : 0.0);
-    }
-#pragma unroll
-  for (int k = 0; k < 9; ++k) dJ[k] = fma(cb, K[k], fma(-e.b, Vx[k], fma(ch, K2[k], e.h * VK[k])));
+    z[r] = fma(cb, ut[r], fma(-b, uv[r], fma(ct, th[r], fma(cv, v[r], cu * u[r]))));
 }
 
 // Mass moment M (4x4 symmetric) of link l for instance b.

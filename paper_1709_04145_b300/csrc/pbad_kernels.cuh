@@ -450,10 +450,10 @@ struct Ctx {
       const int jt = B.jtype[l];
       link_fk_rot(l, p >= 0 ? Tp : nullptr, q3, R, T);
       if (jt == kBall) {  // cached for the tangent passes at this point
-        ws[L.ec + 4 * l] = ec.b;
-        ws[L.ec + 4 * l + 1] = ec.h;
-        ws[L.ec + 4 * l + 2] = ec.db;
-        ws[L.ec + 4 * l + 3] = ec.dh;
+        ws[L.ec + 4 * l] = ec.c;
+        ws[L.ec + 4 * l + 1] = ec.a;
+        ws[L.ec + 4 * l + 2] = ec.b;
+        ws[L.ec + 4 * l + 3] = ec.h;
       }
       store12(L.T + 12 * l, T);
       link_axes(l, T, Jr, w);
@@ -702,15 +702,19 @@ struct Ctx {
         cross(od, a + 3, t2);
         cross(o, ad + 3, t3);
         const double mdo[3] = {ad[0] - t2[0] - t3[0], ad[1] - t2[1] - t3[1], ad[2] - t2[2] - t3[2]};
-        double dJ[9];
+        // ball: d/de of w_k = R Jr e_k adds R dJr e_k, whose contraction
+        // with mo is (dJr^T R^T mo)_k
+        double zb[3] = {0.0, 0.0, 0.0};
         if (jt == kBall) {
-          double th[3], v[3], bh[4];
+          double th[3], v[3], cab[4], u[3];
           for (int k = 0; k < 3; ++k) {
             th[k] = ws[L.xt + d0 + k];
             v[k] = ws[dir + d0 + k];
           }
-          for (int k = 0; k < 4; ++k) bh[k] = ws[L.ec + 4 * l + k];
-          jr_tangent(th, v, bh, dJ);
+          for (int k = 0; k < 4; ++k) cab[k] = ws[L.ec + 4 * l + k];
+#pragma unroll
+          for (int c = 0; c < 3; ++c) u[c] = fma(T[c], mo[0], fma(T[4 + c], mo[1], T[8 + c] * mo[2]));
+          jr_tangent_dot(th, v, cab, u, zb);
         }
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
@@ -719,16 +723,10 @@ struct Ctx {
                                ws[L.axes + 9 * l + 3 * k + 2]};
           double wd[3];
           cross(V, w, wd);
-          if (jt == kBall) {
-            // + R dJr e_k
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-              wd[r] += fma(T[4 * r], dJ[k], fma(T[4 * r + 1], dJ[3 + k], T[4 * r + 2] * dJ[6 + k]));
-          }
           // rotation: d/de [w . (M - o x F)]; translation: d/de [w . F]
           // (jt is uniform across the warp: every lane is at link l)
           if (jt == kTranslation) ws[out + d0 + k] = scale * (dot3(wd, a + 3) + dot3(w, ad + 3));
-          else ws[out + d0 + k] = scale * (dot3(wd, mo) + dot3(w, mdo));
+          else ws[out + d0 + k] = scale * (dot3(wd, mo) + zb[k] + dot3(w, mdo));
         }
       }
       if (chain) {
