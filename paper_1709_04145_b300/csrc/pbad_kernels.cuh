@@ -568,6 +568,26 @@ struct Ctx {
     return (S == 1) ? (Eown - tq) : rr;
   }
 
+  // V += the twist of joint l's DOFs along the direction at offset dir (own
+  // stage slice); o is the joint origin. Three DOFs are summed into one axis
+  // rate first (one cross product instead of three).
+  __device__ __forceinline__ void add_joint_twist(int l, int nd, int d0, const double* o, int dir,
+                                                  double* V) const {
+    if (nd == 1) {
+      const double w[3] = {ws[L.axes + 9 * l], ws[L.axes + 9 * l + 1], ws[L.axes + 9 * l + 2]};
+      add_twist(B.jtype[l], o, w, ws[dir + d0], V);
+    } else {
+      double wj[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        const double vk = ws[dir + d0 + k];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) wj[c] = fma(vk, ws[L.axes + 9 * l + 3 * k + c], wj[c]);
+      }
+      add_twist(B.jtype[l], o, wj, 1.0, V);
+    }
+  }
+
   // ------------------------------------------------------- tangent passes
   // d/de of the residual pass of the own stage along a direction v (own
   // stage slice at workspace offset `dir`), with the seeds perturbed by
@@ -600,11 +620,7 @@ struct Ctx {
       double T[12];
       load12(L.T + 12 * l, T);
       const double o[3] = {T[3], T[7], T[11]};
-      for (int k = 0; k < nd; ++k) {
-        const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
-                             ws[L.axes + 9 * l + 3 * k + 2]};
-        add_twist(B.jtype[l], o, w, ws[dir + d0 + k], V);
-      }
+      add_joint_twist(l, nd, d0, o, dir, V);
       for (int k = 0; k < 6; ++k) ws[L.V + 6 * l + k] = V[k];
       // Tdot = [w]x T + v at the world origin
       double Td[12];
@@ -716,17 +732,20 @@ struct Ctx {
           for (int c = 0; c < 3; ++c) u[c] = fma(T[c], mo[0], fma(T[4 + c], mo[1], T[8 + c] * mo[2]));
           jr_tangent_dot(th, v, cab, u, zb);
         }
+        // rotation: d/de [w . (M - o x F)] = (V x w) . mo + w . mdo = w . (mo x V
+        // + mdo); translation: d/de [w . F] = w . (F x V + Fd)
+        // (jt is uniform across the warp: every lane is at link l)
+        const bool tr = jt == kTranslation;
+        double qv[3];
+        cross(tr ? a + 3 : mo, V, qv);
+#pragma unroll
+        for (int r = 0; r < 3; ++r) qv[r] += tr ? ad[3 + r] : mdo[r];
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
           if (k >= nd) break;
           const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
                                ws[L.axes + 9 * l + 3 * k + 2]};
-          double wd[3];
-          cross(V, w, wd);
-          // rotation: d/de [w . (M - o x F)]; translation: d/de [w . F]
-          // (jt is uniform across the warp: every lane is at link l)
-          if (jt == kTranslation) ws[out + d0 + k] = scale * (dot3(wd, a + 3) + dot3(w, ad + 3));
-          else ws[out + d0 + k] = scale * (dot3(wd, mo) + zb[k] + dot3(w, mdo));
+          ws[out + d0 + k] = scale * (dot3(w, qv) + zb[k]);
         }
       }
       if (chain) {
@@ -956,11 +975,7 @@ struct Ctx {
       double T[12];
       load12(L.T + 12 * l, T);
       const double o[3] = {T[3], T[7], T[11]};
-      for (int k = 0; k < nd; ++k) {
-        const double w[3] = {ws[L.axes + 9 * l + 3 * k], ws[L.axes + 9 * l + 3 * k + 1],
-                             ws[L.axes + 9 * l + 3 * k + 2]};
-        add_twist(B.jtype[l], o, w, ws[dir + d0 + k], V);
-      }
+      add_joint_twist(l, nd, d0, o, dir, V);
       for (int k = 0; k < 6; ++k) ws[L.V + 6 * l + k] = V[k];
       double Td[12];
 #pragma unroll
