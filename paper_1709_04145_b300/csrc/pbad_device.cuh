@@ -174,7 +174,7 @@ __device__ __forceinline__ void rodrigues(const double* v, double c0, double c1,
 // Scalar functions of x = |theta|^2 for the exponential map:
 //   b(x) = (1 - cos phi)/x, h(x) = (phi - sin phi)/phi^3 and their x-derivatives,
 //   plus cos phi and a = sin(phi)/phi. Power series below x = 1 (terms
-//   through x^9; the remainder is below 2e-20), closed forms above.
+//   through x^8; the remainders are below 1e-17), closed forms above.
 struct ExpCoef {
   double c, a, b, h, db, dh;
 };
@@ -184,7 +184,7 @@ __device__ __forceinline__ ExpCoef exp_coef(double x) {
   e.db = 0.0;
   e.dh = 0.0;
   if (x < 1.0) {
-    // Horner in x; terms through x^9
+    // Horner in x; terms through x^8 (the tables run to x^9)
     // a = sum (-1)^k x^k/(2k+1)!, b = sum (-1)^k x^k/(2k+2)!, h = sum (-1)^k x^k/(2k+3)!
     const double ia[10] = {1.0, -1.0 / 6, 1.0 / 120, -1.0 / 5040, 1.0 / 362880, -1.0 / 39916800,
                            1.0 / 6227020800.0, -1.0 / 1307674368000.0, 1.0 / 355687428096000.0,
@@ -195,16 +195,16 @@ __device__ __forceinline__ ExpCoef exp_coef(double x) {
     const double ih[10] = {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800,
                            -1.0 / 6227020800.0, 1.0 / 1307674368000.0, -1.0 / 355687428096000.0,
                            1.0 / 121645100408832000.0, -1.0 / 51090942171709440000.0};
-    double A = ia[9], B = ib[9], H = ih[9], dB = 9 * ib[9], dH = 9 * ih[9];
+    double A = ia[8], B = ib[8], H = ih[8], dB = 8 * ib[8], dH = 8 * ih[8];
 #pragma unroll
-    for (int k = 8; k >= 0; --k) {
+    for (int k = 7; k >= 0; --k) {
       A = fma(A, x, ia[k]);
       B = fma(B, x, ib[k]);
       H = fma(H, x, ih[k]);
     }
     if (DERIV) {
 #pragma unroll
-      for (int k = 8; k >= 1; --k) {
+      for (int k = 7; k >= 1; --k) {
         dB = fma(dB, x, k * ib[k]);
         dH = fma(dH, x, k * ih[k]);
       }
@@ -243,9 +243,9 @@ __device__ __forceinline__ void exp_coef_deriv(double x, double a, double c, dou
     const double ih[10] = {1.0 / 6, -1.0 / 120, 1.0 / 5040, -1.0 / 362880, 1.0 / 39916800,
                            -1.0 / 6227020800.0, 1.0 / 1307674368000.0, -1.0 / 355687428096000.0,
                            1.0 / 121645100408832000.0, -1.0 / 51090942171709440000.0};
-    double dB = 9 * ib[9], dH = 9 * ih[9];
+    double dB = 8 * ib[8], dH = 8 * ih[8];  // terms through x^7 (remainder below 1e-17)
 #pragma unroll
-    for (int k = 8; k >= 1; --k) {
+    for (int k = 7; k >= 1; --k) {
       dB = fma(dB, x, k * ib[k]);
       dH = fma(dH, x, k * ih[k]);
     }
@@ -274,15 +274,15 @@ __device__ __forceinline__ void joint_rotation(int jt, const double* u, const do
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
       R[k] = (k % 4 == 0) ? 1.0 : 0.0;
-      Jr[k] = R[k];
+      if (Jr) Jr[k] = R[k];
     }
   } else {
     const double x = fma(q[0], q[0], fma(q[1], q[1], q[2] * q[2]));
     const ExpCoef e = exp_coef<false>(x);
     if (ec) *ec = e;
     rodrigues(q, e.c, e.a, e.b, R);
-    // Jr = (1 - h x) I - b [theta]x + h theta theta^T
-    rodrigues(q, fma(-e.h, x, 1.0), -e.b, e.h, Jr);
+    // Jr = (1 - h x) I - b [theta]x + h theta theta^T (null: not wanted)
+    if (Jr) rodrigues(q, fma(-e.h, x, 1.0), -e.b, e.h, Jr);
   }
 }
 

@@ -267,7 +267,7 @@ struct Ctx {
 #pragma unroll
       for (int k = 0; k < 3; ++k)
         if (k < nd) q3[k] = ws[L.qp + d0 + k];
-      link_fk(l, p >= 0 ? Pp : nullptr, q3, Tp, Jr);
+      link_fk(l, p >= 0 ? Pp : nullptr, q3, Tp, nullptr);  // no Jr at q_prev
 #pragma unroll
       for (int k = 0; k < 3; ++k)
         if (k < nd) q3[k] = ws[L.qc + d0 + k];
@@ -284,6 +284,12 @@ struct Ctx {
       double C[12];
 #pragma unroll
       for (int k = 0; k < 12; ++k) C[k] = fma(wk[0], Tp[k], wk[1] * Tc[k]);
+      if (S > 1) {
+        // gravity folded into the seed: (A - g e4^T) M = A M - g [m c; m]^T,
+        // since e4^T M is M's last row
+#pragma unroll
+        for (int r = 0; r < 3; ++r) C[4 * r + 3] -= B.g[r];
+      }
       if (commit) store12(L.C + 12 * l, C);
     }
     // composite world mass moments at q_cur: [Sigma_w(6) h(3) m] per link in
@@ -499,10 +505,12 @@ struct Ctx {
           eg = fma(B.g[r], fma(T[4 * r], mc4[0], fma(T[4 * r + 1], mc4[1], fma(T[4 * r + 2], mc4[2], T[4 * r + 3] * mc4[3]))), eg);
         Eown += 0.5 * dt2 * ek + B.drag * dt2 * ed - eg;
       }
+      if (S == 1) {  // S > 1: gravity is folded into C (setup)
 #pragma unroll
-      for (int r = 0; r < 3; ++r)
+        for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) G[4 * r + c] = fma(-B.g[r], mc4[c], G[4 * r + c]);
+          for (int c = 0; c < 4; ++c) G[4 * r + c] = fma(-B.g[r], mc4[c], G[4 * r + c]);
+      }
       if (S == 1 && B.n_contact) {
         // Eq. FRI contact points of this link: energy and dQ/dT = f [p; 1]^T
         const int c0 = B.c_off[l], c1 = B.c_off[l + 1];
