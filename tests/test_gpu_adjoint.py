@@ -154,3 +154,50 @@ def test_rollout_gradient_matches_oracle_dense_adjoint():
         assert _relerr(x0.grad[sl].cpu().numpy(), a_prev + a_cur) < 1e-6
         assert _relerr(v0.grad[sl].cpu().numpy(), nodes[0] * dt * a_prev) < 1e-6
         assert _relerr(tt.grad[:, sl].cpu().numpy(), g_tau) < 1e-6
+
+
+@pytest.mark.parametrize("S", [1, 2])
+def test_step_backward_large_ball_rotations(S):
+    """Newton step and its adjoint with ball joints turned 1-2.6 rad (the
+    closed-form branch of the exponential map and of its derivatives in
+    the Jacobian columns), against the oracle's dense adjoint."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    dev = torch.device("cuda:0")
+    spec = I.ball_chain(6, 3, seed=43, radius=0.15)
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    dt = 0.01
+    nodes, _ = O.colloc(S)
+    rng = np.random.default_rng(6)
+    B, n = spec.count, spec.n_dof
+    v = rng.normal(size=(B, n // 3, 3))
+    v /= np.linalg.norm(v, axis=-1, keepdims=True)
+    q0 = (v * rng.uniform(1.0, 2.6, size=(B, n // 3, 1))).reshape(B, n)
+    qd0 = rng.normal(0, 0.3, size=(B, n))
+    qp = q0 + nodes[0] * dt * qd0
+    tau = rng.normal(0, 0.1, B * n)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    out = P.step(batch, t(qp), t(q0), t(tau), dt, S, P.NEWTON, 8, 1e-9, 100)
+    st = out["status"].cpu().numpy()
+    assert (st == 0).sum() >= B - 1
+    qs = out["q_stages"]
+    gbar = rng.normal(size=S * batch.D)
+    gp, gc, gt, bst = P.step_backward(batch, t(qp), t(q0), t(tau), qs, t(gbar), dt, S)
+    torch.cuda.synchronize()
+    qs_h = qs.cpu().numpy()
+    gp, gc, gt, bst = gp.cpu().numpy(), gc.cpu().numpy(), gt.cpu().numpy(), bst.cpu().numpy()
+    qp_f, q0_f = qp.reshape(-1), q0.reshape(-1)
+    checked = 0
+    for b in range(B):
+        if st[b] != 0:
+            continue
+        assert bst[b] == 0
+        om = O.OracleModel.from_spec(spec, b)
+        sl, ssl = slice(b * n, (b + 1) * n), slice(S * b * n, S * (b + 1) * n)
+        rp, rc, rt = om.step_adjoint(S, dt, qp_f[sl], q0_f[sl], tau[sl], qs_h[ssl], gbar[ssl])
+        assert _relerr(gp[sl], rp) < 1e-7, b
+        assert _relerr(gc[sl], rc) < 1e-7, b
+        assert _relerr(gt[sl], rt) < 1e-7, b
+        checked += 1
+    assert checked >= B - 1

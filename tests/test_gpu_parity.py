@@ -253,3 +253,42 @@ def test_rollout_gradient_evaluation_counts(S):
                 assert gr.sum() < ev.sum()
         else:  # one build per step start and per accepted iteration, less the last
             assert (np.abs(gr - it) <= n_steps).all()
+
+
+def _large_rotations(B, n, S, rng):
+    """Ball-joint exp-map vectors with |theta| in [1, 2.6]: the closed-form
+    branch of the exponential map's coefficients (|theta|^2 >= 1)."""
+    def draw(shape):
+        v = rng.normal(size=shape + (3,))
+        v /= np.linalg.norm(v, axis=-1, keepdims=True)
+        return (v * rng.uniform(1.0, 2.6, size=shape + (1,))).reshape(shape[:-1] + (n,))
+    q_cur = draw((B, n // 3))
+    q_prev = q_cur + rng.normal(0, 0.02, size=(B, n))
+    qs = q_cur[:, None, :] + rng.normal(0, 0.03, size=(B, S, n))
+    return q_prev, q_cur, qs
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_eval_large_ball_rotations(S):
+    """E, r and dE/dq at rotations of 1-2.6 rad per ball joint (the series
+    covers |theta| < 1 on the GPU), against the oracle's own exp map."""
+    torch = _torch()
+    P = _pbad()
+    spec = I.ball_chain(9, 4, seed=13, radius=0.12)
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8)
+    rng = np.random.default_rng(14)
+    B, n, dt = spec.count, spec.n_dof, 0.02
+    q_prev, q_cur, qs = _large_rotations(B, n, S, rng)
+    tau = rng.normal(0, 0.3, size=(B, n))
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    E, grad, resid = P.eval_objective_grad(batch, t(qs), t(q_prev), t(q_cur), t(tau), dt, S)
+    torch.cuda.synchronize()
+    E, grad, resid = E.cpu().numpy(), grad.cpu().numpy(), resid.cpu().numpy()
+    for b in range(B):
+        om = O.OracleModel.from_spec(spec, b)
+        Eo, ro, go, _ = om.eval(S, dt, qs[b].reshape(-1), q_prev[b], q_cur[b], tau[b], True)
+        sl = slice(b * S * n, (b + 1) * S * n)
+        assert abs(E[b] - Eo) <= REL_EVAL * max(abs(Eo), 1.0), b
+        assert _relerr(resid[sl], ro) < REL_EVAL, b
+        assert _relerr(grad[sl], go) < REL_EVAL, b
