@@ -76,6 +76,9 @@ using namespace pbad;
 
 struct pbad_model {
   int N = 0, n = 0, device = 0, chain = 1;
+  // 1 if every link's mass moment has Sxy = Sxz = Syz = mcx = mcy = 0 (a body
+  // symmetric about its frame's z axis: rods, capsules)
+  int axial = 1;
   int64_t count = 0;
   double drag = 0.0;  // drag coefficient c of Q_drag (Section 6.2)
   std::vector<int> parent, jtype, dof;
@@ -337,6 +340,7 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.block_begin = blocks;
     B.solver = solvers ? solvers[k] : PBAD_LBFGS;
     B.chain = m->chain;
+    B.axial = m->axial;
     B.dense = bt->d_dense ? bt->d_dense + bt->dense_off[k] : nullptr;
     B.dense_stride = bt->d_dense ? bt->dense_stride[k] : 0;
     B.drag = m->drag;
@@ -546,8 +550,11 @@ int pbad_model_create(int32_t n_links, const int32_t* parent, const int32_t* joi
   std::vector<double> mm((size_t)n_links * 10 * count), rs((size_t)n_links * 12 * count);
   for (int64_t b = 0; b < count; ++b)
     for (int l = 0; l < n_links; ++l) {
-      for (int k = 0; k < 10; ++k)
-        mm[((size_t)l * 10 + k) * count + b] = mass_moment[((size_t)b * n_links + l) * 10 + k];
+      for (int k = 0; k < 10; ++k) {
+        const double v = mass_moment[((size_t)b * n_links + l) * 10 + k];
+        mm[((size_t)l * 10 + k) * count + b] = v;
+        if ((k == 1 || k == 2 || k == 4 || k == 6 || k == 7) && v != 0.0) m->axial = 0;
+      }
       for (int k = 0; k < 12; ++k)
         rs[((size_t)l * 12 + k) * count + b] = rest[((size_t)b * n_links + l) * 12 + k];
     }
@@ -950,6 +957,7 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   B.ws_lane = L.total;
   B.block_begin = 0;
   B.chain = m->chain;
+  B.axial = m->axial;
   B.drag = m->drag;
   B.tk = tk;
   B.n_contact = m->n_contact;

@@ -49,6 +49,7 @@ struct Bucket {
   int* queue;            // device counter, zeroed before the launch (null = no queue)
   int first_dynamic;
   int chain;             // 1 if parent[l] == l - 1 for every link (serial chain)
+  int axial;             // 1 if every mass moment has Sxy = Sxz = Syz = mcx = mcy = 0
   double* dense;         // per-instance dense Newton/adjoint storage (or null)
   int64_t dense_stride;  // doubles per instance in `dense`
   double drag;           // drag coefficient c of Q_drag (Section 6.2), 0 = none
@@ -332,6 +333,21 @@ __device__ __forceinline__ void mul_mass(const double* A, const MassMoment& M, d
     Y[4 * r + 1] = fma(a0, s[1], fma(a1, s[3], fma(a2, s[4], a3 * s[7])));
     Y[4 * r + 2] = fma(a0, s[2], fma(a1, s[4], fma(a2, s[5], a3 * s[8])));
     Y[4 * r + 3] = fma(a0, s[6], fma(a1, s[7], fma(a2, s[8], a3 * s[9])));
+  }
+}
+
+// The same product for a mass moment with Sxy = Sxz = Syz = mcx = mcy = 0
+// (symmetric about the frame's z axis): the terms of mul_mass that remain, in
+// its order, so the results are bitwise equal.
+__device__ __forceinline__ void mul_mass_axial(const double* A, const MassMoment& M, double* Y) {
+  const double* s = M.s;
+#pragma unroll
+  for (int r = 0; r < 3; ++r) {
+    const double a0 = A[4 * r], a1 = A[4 * r + 1], a2 = A[4 * r + 2], a3 = A[4 * r + 3];
+    Y[4 * r + 0] = a0 * s[0];
+    Y[4 * r + 1] = a1 * s[3];
+    Y[4 * r + 2] = fma(a2, s[5], a3 * s[8]);
+    Y[4 * r + 3] = fma(a2, s[8], a3 * s[9]);
   }
 }
 

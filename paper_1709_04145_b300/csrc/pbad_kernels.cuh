@@ -477,7 +477,8 @@ struct Ctx {
       }
       const MassMoment M = mass(l);
       double G[12];
-      mul_mass(A, M, G);
+      if (B.axial) mul_mass_axial(A, M, G);
+      else mul_mass(A, M, G);
       const double mc4[4] = {M.s[6], M.s[7], M.s[8], M.s[9]};
       if (S == 1) {
         // Eq. EQ: tr(D M D^T)/(2 dt^2) with D = dt^2 A_kin, the drag potential
@@ -655,7 +656,8 @@ struct Ctx {
       }
       const MassMoment M = mass(l);
       double Bm[12];
-      mul_mass(Bs, M, Bm);
+      if (B.axial) mul_mass_axial(Bs, M, Bm);
+      else mul_mass(Bs, M, Bm);
       if (S == 1 && B.n_contact) {
         // contact points: d/de of f [p; 1]^T = (H Pdot) [p; 1]^T, Pdot = Tdot [p; 1]
         const int c0 = B.c_off[l], c1 = B.c_off[l + 1];
@@ -1050,7 +1052,8 @@ struct Ctx {
       }
       const MassMoment M = mass(l);
       double Bm[12], w6[6];
-      mul_mass(Bs, M, Bm);
+      if (B.axial) mul_mass_axial(Bs, M, Bm);
+      else mul_mass(Bs, M, Bm);
       if (S == 1 && j == 1 && B.n_contact) {
         // contact points: their loads (from transform_tangents) act at P(q_k)
         for (int c = B.c_off[l]; c < B.c_off[l + 1]; ++c) {

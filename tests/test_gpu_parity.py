@@ -292,3 +292,46 @@ def test_eval_large_ball_rotations(S):
         assert abs(E[b] - Eo) <= REL_EVAL * max(abs(Eo), 1.0), b
         assert _relerr(resid[sl], ro) < REL_EVAL, b
         assert _relerr(grad[sl], go) < REL_EVAL, b
+
+
+def _general_moments(count, N, rng):
+    """Mass moments of a few point masses per link off the frame's z axis:
+    full symmetric Sigma and an off-axis centroid (not axially symmetric)."""
+    mm = np.zeros((count, N, 10))
+    for b in range(count):
+        for l in range(N):
+            M = np.zeros((4, 4))
+            for _ in range(4):
+                p = np.append(rng.normal(0, 0.2, 3) + [0, 0, -0.4], 1.0)
+                M += rng.uniform(0.1, 0.5) * np.outer(p, p)
+            mm[b, l] = [M[0, 0], M[0, 1], M[0, 2], M[1, 1], M[1, 2], M[2, 2], M[0, 3], M[1, 3],
+                        M[2, 3], M[3, 3]]
+    return mm
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_eval_general_mass_moments(S):
+    """Links that are not symmetric about their z axis take the general mass
+    product; E, r and dE/dq against the oracle."""
+    torch = _torch()
+    P = _pbad()
+    spec = I.ball_chain(7, 3, seed=15, radius=0.1)
+    rng = np.random.default_rng(16)
+    B, N, n, dt = spec.count, spec.n_links, spec.n_dof, 0.02
+    mm = _general_moments(B, N, rng)
+    rest = np.stack([O.rest_from_spec(spec, b) for b in range(B)])
+    model = P.Model(spec.parent, spec.jtype, spec.axis, mm, rest, spec.gravity)
+    batch = P.Batch([model], max_stages=S, max_history=8)
+    q_prev, q_cur, tau, qs = _random_case(spec, S, 17, dt)
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    E, grad, resid = P.eval_objective_grad(batch, t(qs), t(q_prev), t(q_cur), t(tau), dt, S)
+    torch.cuda.synchronize()
+    E, grad, resid = E.cpu().numpy(), grad.cpu().numpy(), resid.cpu().numpy()
+    for b in range(B):
+        om = O.OracleModel(spec.parent, spec.jtype, spec.axis, mm[b], rest[b], spec.gravity)
+        Eo, ro, go, _ = om.eval(S, dt, qs[b].reshape(-1), q_prev[b], q_cur[b], tau[b], True)
+        sl = slice(b * S * n, (b + 1) * S * n)
+        assert abs(E[b] - Eo) <= REL_EVAL * max(abs(Eo), 1.0), b
+        assert _relerr(resid[sl], ro) < REL_EVAL, b
+        assert _relerr(grad[sl], go) < REL_EVAL, b
