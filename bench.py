@@ -42,10 +42,10 @@ COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 # DRAM bytes (read + write) of the rollout kernel per instance-evaluation,
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one
 # pass) of a full 100-step k_rollout<3, 0> launch on 4096 ten-link ball
-# chains (profiles/k_rollout_ballchains4096_launches.md): 1797.7 GB over
+# chains (profiles/k_rollout_ballchains4096_launches.md): 1758.7 GB over
 # 56,284,962 instance-evaluations. The roofline's traffic field scales it by
 # the evaluations of the timed launch. Valid for the kernel as captured.
-ROLLOUT_DRAM_BYTES_PER_EVAL = 31939.4
+ROLLOUT_DRAM_BYTES_PER_EVAL = 31247.2
 
 
 def primal_flops_per_eval(jtypes, S):
