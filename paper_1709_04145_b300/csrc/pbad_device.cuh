@@ -173,9 +173,11 @@ __device__ __forceinline__ void rodrigues(const double* v, double c0, double c1,
 }
 
 // Scalar functions of x = |theta|^2 for the exponential map:
-//   b(x) = (1 - cos phi)/x, h(x) = (phi - sin phi)/phi^3 and their x-derivatives,
-//   plus cos phi and a = sin(phi)/phi. Power series below x = 1 (terms
-//   through x^8; the remainders are below 1e-17), closed forms above.
+//   b(x) = (1 - cos phi)/x, h(x) = (phi - sin phi)/phi^3, cos phi and
+//   a = sin(phi)/phi, and with DERIV the x-derivatives of b and h (the hot
+//   passes take those from exp_coef_deriv instead, when a tangent pass needs
+//   them). Power series below x = 1 (terms through x^8; the remainders are
+//   below 1e-17), closed forms above.
 struct ExpCoef {
   double c, a, b, h, db, dh;
 };
