@@ -894,6 +894,10 @@ def run_ours(args):
                                               budget_s=args.cpu_sample_seconds)
         line["cpu_baseline"] = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
                                 "sample": sample}
+        # the same oracle on one core (one process, one instance)
+        rate1, _, sample1 = cpu_oracle_rate(w, n_inst=1, n_steps=0,
+                                            budget_s=args.cpu_sample_seconds / 3)
+        line["cpu_baseline"]["single_core"] = {"value": rate1, "unit": UNIT, "sample": sample1}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
