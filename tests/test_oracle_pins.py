@@ -406,3 +406,20 @@ def test_step_adjoint_matches_finite_differences():
     assert relerr(gp, fd(lambda x: L(x, qc, tau), qp, h)) < 1e-5
     assert relerr(gc, fd(lambda x: L(qp, x, tau), qc, h)) < 1e-5
     assert relerr(gt, fd(lambda x: L(qp, qc, x), tau, h)) < 1e-5
+
+
+@pytest.mark.parametrize("k", [None, 0, 2])
+def test_expmap_continuous_across_series_switch(k):
+    """The oracle's exponential map switches from its power series to closed
+    forms at |theta| = 0.5: R, dR and d2R just below and just above agree to
+    rounding (a dropped or wrong low-order series term would show as a jump)."""
+    u = np.array([0.6, -0.48, 0.64])  # unit direction
+    lo, hi = 0.5 * (1 - 1e-14) * u, 0.5 * (1 + 1e-14) * u
+    assert np.linalg.norm(lo) < 0.5 <= np.linalg.norm(hi)
+    args = () if k is None else (k,)
+    a, b = O.joint_rot(1, [0, 0, 1], lo, *args), O.joint_rot(1, [0, 0, 1], hi, *args)
+    assert np.max(np.abs(a - b)) < 1e-13
+    if k is not None:
+        a2 = O.joint_rot(1, [0, 0, 1], lo, k, 1)
+        b2 = O.joint_rot(1, [0, 0, 1], hi, k, 1)
+        assert np.max(np.abs(a2 - b2)) < 1e-12
