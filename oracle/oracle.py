@@ -22,7 +22,8 @@ HINGE, BALL, TRANSLATION = 0, 1, 2
 # solver names of step/rollout: L-BFGS, Levenberg-Marquardt, and L-BFGS whose
 # two-loop recursion runs in binary32 (line search and evaluations binary64)
 SOLVERS = {"lbfgs": 0, "lm": 1, "lbfgs32": 2}
-STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE"}
+STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE",
+          5: "STALLED"}
 
 
 def build(force: bool = False) -> str:
@@ -72,10 +73,15 @@ def lib():
         L.om_resid_known_jac.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp]
         L.om_step.restype = C.c_int
         L.om_step.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, C.c_int, C.c_int,
-                              C.c_double, C.c_int, C.c_int, dp, ip, ip]
+                              C.c_double, C.c_int, C.c_int, dp, ip, ip, dp]
         L.om_rollout.restype = C.c_int
         L.om_rollout.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, C.c_int, C.c_int,
-                                 C.c_int, C.c_double, C.c_int, C.c_int, dp, dp, dp, dp, ip, ip]
+                                 C.c_int, C.c_double, C.c_int, C.c_int, dp, dp, dp, dp, ip, ip,
+                                 ip, dp]
+        L.om_floor.restype = C.c_double
+        L.om_floor.argtypes = [vp, C.c_int, C.c_double]
+        L.om_status_worse.restype = C.c_int
+        L.om_status_worse.argtypes = [C.c_int, C.c_int]
         L.om_step_adjoint.restype = C.c_int
         L.om_step_adjoint.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp, dp, dp]
         L.om_rnea.restype = C.c_int
@@ -301,15 +307,23 @@ class OracleModel:
         qs = np.zeros(S * n)
         it = C.c_int(0)
         ev = C.c_int(0)
+        rn = C.c_double(0)
         st = lib().om_step(self._h, S, dt, pp, cp, tp, sv, history, tol, max_iter,
                            int(precond), qs.ctypes.data_as(C.POINTER(C.c_double)),
-                           C.byref(it), C.byref(ev))
+                           C.byref(it), C.byref(ev), C.byref(rn))
+        self.last_rnorm = rn.value
         return qs.reshape(S, n), st, it.value, ev.value
+
+    def floor(self, S: int, dt: float) -> float:
+        """Rounding floor of |r|_2 for one step (see om_floor); a step whose
+        line search cannot lower E at |r| <= 1e3 floor ends STALLED."""
+        return lib().om_floor(self._h, S, dt)
 
     def rollout(self, S, dt, q_prev0, q_cur0, tau_seq, solver="lbfgs", history=8,
                 tol=1e-10, max_iter=None, precond=True):
-        """Returns dict(traj_prev, traj_cur (n_steps, n), q_prev, q_cur, status,
-        iters, evals)."""
+        """Returns dict(traj_prev, traj_cur (n_steps, n), q_prev, q_cur, status
+        (worst over the steps), iters, evals, step_status (n_steps,), step_rnorm
+        (n_steps,): each step's status and exit |r|_2)."""
         n = self.n_dof
         sv = SOLVERS[solver]
         if max_iter is None:
@@ -324,12 +338,15 @@ class OracleModel:
         qco = np.zeros(n)
         it = C.c_int(0)
         ev = C.c_int(0)
+        sst = np.zeros(n_steps, dtype=np.int32)
+        srn = np.zeros(n_steps)
         fp = lambda a: a.ctypes.data_as(C.POINTER(C.c_double))
         st = lib().om_rollout(self._h, S, dt, pp, cp, tsp, n_steps, sv, history, tol,
                               max_iter, int(precond), fp(tp_), fp(tc_), fp(qpo), fp(qco),
-                              C.byref(it), C.byref(ev))
+                              C.byref(it), C.byref(ev),
+                              sst.ctypes.data_as(C.POINTER(C.c_int)), fp(srn))
         return dict(traj_prev=tp_, traj_cur=tc_, q_prev=qpo, q_cur=qco, status=st,
-                    iters=it.value, evals=ev.value)
+                    iters=it.value, evals=ev.value, step_status=sst, step_rnorm=srn)
 
     def step_adjoint(self, S, dt, q_prev, q_cur, tau, qs, gbar):
         n = self.n_dof

@@ -1096,7 +1096,59 @@ static int lu_solve(double *A, int n, double *b) {
 /* ------------------------------------------------------------------ */
 
 enum { OM_CONVERGED = 0, OM_MAX_ITER = 1, OM_LS_FAIL = 2, OM_CHOL_FAIL = 3,
-       OM_NONFINITE = 4 };
+       OM_NONFINITE = 4, OM_STALLED = 5 };
+
+/* Severity order of the statuses for the worst over a rollout's steps:
+ * CONVERGED < STALLED (solved to the rounding floor) < MAX_ITER < LS_FAIL <
+ * CHOL_FAIL < NONFINITE. */
+static int status_rank(int st) { return st == OM_STALLED ? 1 : (st == OM_CONVERGED ? 0 : st + 1); }
+int om_status_worse(int a, int b) { return status_rank(b) > status_rank(a) ? b : a; }
+
+/* Rounding floor of |r|_2 for one step (the paper is silent on it). A stage
+ * residual of Eq. HOC (or the gradient of Eq. EQ) is a sum of terms of size
+ * |W_ij| |T M| |lever| that cancel down to the answer, so binary64 cannot
+ * resolve |r| below about eps times their size. The bound used:
+ *   floor = eps (What sum_l I_l + |g| sum_l (|m c_l| + m_l R_l)),
+ *   What = max_i sum_j |W_ij + 2 c V_ij| / dt^2 over all S+2 nodes (the
+ *          acceleration and drag weights of the seeds),
+ *   R_l  = sum of |t(X_a)| over the joints a on the root-to-l path (a bound
+ *          on the distance of link l's frame from the root in rest geometry),
+ *   I_l  = (sqrt(tr Sigma_l) + sqrt(m_l) R_l)^2 >= int rho |P|^2 over link l
+ *          about the root.
+ * Translation coordinates and contact points are not in the bound. A step
+ * whose line search (or LM damping) cannot lower E while |r| <= 1e3 floor
+ * ends STALLED instead of LS_FAIL: solved as far as binary64 resolves r. */
+double om_floor(void *p, int S, double dt) {
+  om_model *m = (om_model *)p;
+  int N = m->n_links, P = S + 2;
+  double nodes[16], W[8 * 16], Vw[8 * 16];
+  om_colloc(S, nodes, W);
+  om_colloc_vel(S, Vw);
+  double What = 0;
+  for (int i = 0; i < S; ++i) {
+    double row = 0;
+    for (int j = 0; j < P; ++j) row += fabs(W[i * P + j] + 2.0 * m->drag * Vw[i * P + j]);
+    if (row > What) What = row;
+  }
+  What /= dt * dt;
+  double sI = 0, sg = 0;
+  for (int l = 0; l < N; ++l) {
+    double R = 0;
+    for (int a = l; a >= 0; a = m->parent[a]) {
+      const double *X = m->rest + 12 * a;
+      R += sqrt(X[3] * X[3] + X[7] * X[7] + X[11] * X[11]);
+    }
+    const double *mm = m->mm + 10 * l;
+    double tr = mm[0] + mm[3] + mm[5];
+    double mass = mm[9];
+    double a = sqrt(tr > 0 ? tr : 0) + sqrt(mass > 0 ? mass : 0) * R;
+    sI += a * a;
+    sg += sqrt(mm[6] * mm[6] + mm[7] * mm[7] + mm[8] * mm[8]) + mass * R;
+  }
+  double gn = sqrt(m->g[0] * m->g[0] + m->g[1] * m->g[1] + m->g[2] * m->g[2]);
+  return 2.220446049250313e-16 * (What * sI + gn * sg);
+}
+#define STALL_FACTOR 1e3
 
 static double dot(const double *a, const double *b, int n) {
   double s = 0;
@@ -1376,7 +1428,7 @@ void om_lbfgs_direction(int Sn, int nh, int mh, int head, const double *sh,
 static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
                        const double *qc, const double *tau, int mh, double tol,
                        int max_iter, int use_precond, int f32dir, double *x,
-                       int *iters, int *evals) {
+                       int *iters, int *evals, double *rn_exit) {
   int n = m->n_dof, Sn = S * n;
   double *g = (double *)malloc(sizeof(double) * Sn);
   double *r = (double *)malloc(sizeof(double) * Sn);
@@ -1450,7 +1502,11 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
       a *= LS_SHRINK;
     }
     if (capped) { status = OM_MAX_ITER; break; }
-    if (!accepted) { status = OM_LS_FAIL; break; }
+    if (!accepted) {
+      double rn = sqrt(dot(r, r, Sn));
+      status = rn <= STALL_FACTOR * om_floor(m, S, dt) ? OM_STALLED : OM_LS_FAIL;
+      break;
+    }
     /* curvature pair */
     double sy = 0, ss = 0, yy = 0, yPy = 0;
     for (int i = 0; i < Sn; ++i) {
@@ -1482,6 +1538,7 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
   }
   *iters = k;
   *evals = ne;
+  if (rn_exit) *rn_exit = sqrt(dot(r, r, Sn));
   free(g); free(r); free(d); free(xt); free(gt); free(rt); free(Py); free(pc.Pb);
   free(sh); free(yh); free(rho); free(alp);
   return status;
@@ -1499,7 +1556,8 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
  * links on ball joints. */
 static int lm_solve(om_model *m, int S, double dt, const double *qp,
                     const double *qc, const double *tau, double tol,
-                    int max_iter, double *x, int *iters, int *evals) {
+                    int max_iter, double *x, int *iters, int *evals,
+                    double *rn_exit) {
   int n = m->n_dof, Sn = S * n;
   double *r = (double *)malloc(sizeof(double) * Sn);
   double *rt = (double *)malloc(sizeof(double) * Sn);
@@ -1559,7 +1617,11 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
       if (ok) { accepted = 1; E = Et; break; }
       lambda *= 10;
     }
-    if (!accepted) { status = last_chol_fail ? OM_CHOL_FAIL : OM_LS_FAIL; break; }
+    if (!accepted) {
+      if (last_chol_fail) status = OM_CHOL_FAIL;
+      else status = rn <= STALL_FACTOR * om_floor(m, S, dt) ? OM_STALLED : OM_LS_FAIL;
+      break;
+    }
     lambda = fmax(lambda * 0.1, 1e-20 * hmax);
     memcpy(x, xt, sizeof(double) * Sn);
     E = om_eval(m, S, dt, x, qp, qc, tau, r, NULL, J);
@@ -1567,6 +1629,7 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
   }
   *iters = k;
   *evals = ne;
+  if (rn_exit) *rn_exit = sqrt(dot(r, r, Sn));
   free(r); free(rt); free(J); free(H); free(A); free(gr); free(dx); free(xt); free(Hm);
   return status;
 }
@@ -1578,26 +1641,29 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
 int om_step(void *p, int S, double dt, const double *q_prev,
             const double *q_cur, const double *tau, int solver, int mh,
             double tol, int max_iter, int use_precond, double *qs_out,
-            int *iters, int *evals) {
+            int *iters, int *evals, double *rn_exit) {
   om_model *m = (om_model *)p;
   initial_guess(S, m->n_dof, q_prev, q_cur, qs_out);
   if (solver == 0 || solver == 2)
     return lbfgs_solve(m, S, dt, q_prev, q_cur, tau, mh, tol, max_iter,
-                       use_precond, solver == 2, qs_out, iters, evals);
+                       use_precond, solver == 2, qs_out, iters, evals, rn_exit);
   return lm_solve(m, S, dt, q_prev, q_cur, tau, tol, max_iter, qs_out, iters,
-                  evals);
+                  evals, rn_exit);
 }
 
 /* Rollout of n_steps steps. State after each step: q_prev' = stage S-1 (or
  * q_cur for S == 1, the node k-1+alpha_{S-1} of the next step), q_cur' =
  * stage S. tau_seq: [n_steps][n]. traj_prev/traj_cur (optional):
- * [n_steps][n] states after each step. status: worst status over the steps;
- * iters: total accepted iterations. */
+ * [n_steps][n] states after each step. Returns the worst status over the
+ * steps (om_status_worse order); iters: total accepted iterations;
+ * step_status / step_rnorm (optional, [n_steps]): each step's status and the
+ * |r|_2 of the point it ended at. */
 int om_rollout(void *p, int S, double dt, const double *q_prev0,
                const double *q_cur0, const double *tau_seq, int n_steps,
                int solver, int mh, double tol, int max_iter, int use_precond,
                double *traj_prev, double *traj_cur, double *q_prev_out,
-               double *q_cur_out, int *iters_total, int *evals_total) {
+               double *q_cur_out, int *iters_total, int *evals_total,
+               int *step_status, double *step_rnorm) {
   om_model *m = (om_model *)p;
   int n = m->n_dof;
   double *qp = (double *)malloc(sizeof(double) * n);
@@ -1608,9 +1674,12 @@ int om_rollout(void *p, int S, double dt, const double *q_prev0,
   int worst = 0, it_tot = 0, ev_tot = 0;
   for (int s = 0; s < n_steps; ++s) {
     int it = 0, ev = 0;
+    double rn = 0;
     int st = om_step(p, S, dt, qp, qc, tau_seq + (size_t)s * n, solver, mh, tol,
-                     max_iter, use_precond, qs, &it, &ev);
-    if (st > worst) worst = st;
+                     max_iter, use_precond, qs, &it, &ev, &rn);
+    worst = om_status_worse(worst, st);
+    if (step_status) step_status[s] = st;
+    if (step_rnorm) step_rnorm[s] = rn;
     it_tot += it;
     ev_tot += ev;
     if (S == 1) memcpy(qp, qc, sizeof(double) * n);
