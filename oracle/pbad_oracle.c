@@ -1548,12 +1548,17 @@ static int lbfgs_solve(om_model *m, int S, double dt, const double *qp,
  *   q <- q - [H + lambda I]^-1 grad,
  * H = Jr^T Jr and grad = Jr^T r for S >= 2 (Eq. EQHOC, sum of squares);
  * H = Hmass/dt^2 (Gauss-Newton of the integral of squares) and grad = dE/dq
- * for S == 1. lambda starts at 1e-12 max diag(H), is divided by 10 on an
- * accepted step (floor 1e-20 max diag(H)) and multiplied by 10 on a rejected
- * step or a failed factorisation. The paper only asks that lambda keep E
- * decreasing; the small start and floor keep lambda below the smallest
- * eigenvalues of Jr^T Jr, whose condition number reaches 1e12-1e16 for thin
- * links on ball joints. */
+ * for S == 1. lambda starts at 1e-12 max diag(H). A damped step that does
+ * not lower E is halved up to LM_HALVINGS times before lambda is multiplied
+ * by 10 (a failed factorisation multiplies it at once); lambda is divided by
+ * 10 (floor 1e-20 max diag(H)) after a full damped step is accepted and kept
+ * after a halved one. The paper only asks that lambda keep E decreasing; the
+ * small start and floor keep lambda below the smallest eigenvalues of
+ * Jr^T Jr, whose condition number reaches 1e12-1e16 for thin links on ball
+ * joints, and the halvings keep it there when the full Gauss-Newton step
+ * overshoots along the stiff modes (raising lambda instead would damp the
+ * soft modes by orders of magnitude and make the iteration crawl). */
+#define LM_HALVINGS 3
 static int lm_solve(om_model *m, int S, double dt, const double *qp,
                     const double *qc, const double *tau, double tol,
                     int max_iter, double *x, int *iters, int *evals,
@@ -1601,6 +1606,7 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
     for (int i = 0; i < Sn; ++i) hmax = fmax(hmax, H[i * Sn + i]);
     if (lambda < 0) lambda = 1e-12 * hmax;
     int accepted = 0, last_chol_fail = 0;
+    double a = 1.0; /* fraction of the damped step that was accepted */
     for (int t = 0; t < 60; ++t) {
       memcpy(A, H, sizeof(double) * Sn * Sn);
       for (int i = 0; i < Sn; ++i) A[i * Sn + i] += lambda;
@@ -1608,13 +1614,19 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
       if (cholesky(A, Sn) != 0) { lambda *= 10; last_chol_fail = 1; continue; }
       for (int i = 0; i < Sn; ++i) dx[i] = -gr[i];
       chol_solve(A, Sn, dx);
-      for (int i = 0; i < Sn; ++i) xt[i] = x[i] + dx[i];
-      double Et = om_eval(m, S, dt, xt, qp, qc, tau, rt, NULL, NULL);
-      ne++;
-      int ok = isfinite(Et) && all_finite(rt, Sn) &&
-               (Et < E || (S == 1 && Et <= E + LS_EPS * fabs(E) &&
-                           dot(rt, rt, Sn) < rn * rn));
-      if (ok) { accepted = 1; E = Et; break; }
+      /* the damped step, then its halves down to 1/8, before a larger lambda */
+      a = 1.0;
+      for (int h = 0; h <= LM_HALVINGS; ++h) {
+        for (int i = 0; i < Sn; ++i) xt[i] = x[i] + a * dx[i];
+        double Et = om_eval(m, S, dt, xt, qp, qc, tau, rt, NULL, NULL);
+        ne++;
+        int ok = isfinite(Et) && all_finite(rt, Sn) &&
+                 (Et < E || (S == 1 && Et <= E + LS_EPS * fabs(E) &&
+                             dot(rt, rt, Sn) < rn * rn));
+        if (ok) { accepted = 1; E = Et; break; }
+        a *= 0.5;
+      }
+      if (accepted) break;
       lambda *= 10;
     }
     if (!accepted) {
@@ -1622,7 +1634,7 @@ static int lm_solve(om_model *m, int S, double dt, const double *qp,
       else status = rn <= STALL_FACTOR * om_floor(m, S, dt) ? OM_STALLED : OM_LS_FAIL;
       break;
     }
-    lambda = fmax(lambda * 0.1, 1e-20 * hmax);
+    if (a == 1.0) lambda = fmax(lambda * 0.1, 1e-20 * hmax);
     memcpy(x, xt, sizeof(double) * Sn);
     E = om_eval(m, S, dt, x, qp, qc, tau, r, NULL, J);
     k++;
