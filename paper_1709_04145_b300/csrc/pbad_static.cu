@@ -8,7 +8,6 @@
 #include <cuda_runtime.h>
 
 #include <cstdio>
-#include <mutex>
 
 #include "../../include/pbad.h"
 #include "pbad_kernels.cuh"
@@ -29,27 +28,23 @@ using namespace pbad;
 static __device__ __align__(256) double g_pbad_static_scratch[PBAD_STATIC_SCRATCH_BYTES / sizeof(double)];
 
 namespace {
-constexpr int kMaxDevices = 256;
-std::mutex g_mu;
-double* g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device (looked up once per
-// device, with that device current).
-int scratch_address(int dev, double** out) {
-  if (dev < 0 || dev >= kMaxDevices) return set_error(PBAD_ERR_ARG, "device index out of range");
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&p, g_pbad_static_scratch);
-    if (e != cudaSuccess || !p) {
-      char msg[160];
-      std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the static scratch: %s",
-                    cudaGetErrorString(e));
-      return set_error(PBAD_ERR_CUDA, msg);
-    }
-    g_scratch_addr[dev] = static_cast<double*>(p);
+// Device address of the scratch in the current context. It is looked up on
+// every call rather than cached: after cudaDeviceReset, or with another
+// context current, the library's module is loaded again and the array may
+// sit at another address, so a cached pointer could point at freed memory.
+// Once the module is loaded in the context the lookup is a table read. The
+// first call in a context loads the module, which is why that call has to
+// come before any stream capture.
+int scratch_address(double** out) {
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_pbad_static_scratch);
+  if (e != cudaSuccess || !p) {
+    char msg[160];
+    std::snprintf(msg, sizeof(msg), "cudaGetSymbolAddress of the static scratch: %s",
+                  cudaGetErrorString(e));
+    return set_error(PBAD_ERR_CUDA, msg);
   }
-  *out = g_scratch_addr[dev];
+  *out = static_cast<double*>(p);
   return PBAD_OK;
 }
 }  // namespace
@@ -73,7 +68,7 @@ extern "C" int pbad_eval_objective_grad_static(const pbad_model* model, const do
   LaunchArgs A;
   int grid = 0;
   int64_t lanes = 0, per_lane = 0;
-  rc = scratch_address(dev, &scratch);
+  rc = scratch_address(&scratch);
   if (rc == PBAD_OK) rc = fill_launch_single(model, stages, dt, scratch, &A, &grid, &lanes, &per_lane);
   if (rc == PBAD_OK && (double)lanes * per_lane * sizeof(double) > (double)PBAD_STATIC_SCRATCH_BYTES) {
     char msg[200];
