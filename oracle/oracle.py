@@ -78,6 +78,9 @@ def lib():
         L.om_rollout.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, C.c_int, C.c_int,
                                  C.c_int, C.c_double, C.c_int, C.c_int, dp, dp, dp, dp, ip, ip,
                                  ip, dp]
+        L.om_eval_fast.restype = C.c_double
+        L.om_eval_fast.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp, dp, dp, dp]
+        L.om_model_set_fast.argtypes = [vp, C.c_int]
         L.om_floor.restype = C.c_double
         L.om_floor.argtypes = [vp, C.c_int, C.c_double]
         L.om_status_worse.restype = C.c_int
@@ -282,6 +285,25 @@ class OracleModel:
                           g.ctypes.data_as(C.POINTER(C.c_double)) if g is not None else _null(),
                           J.ctypes.data_as(C.POINTER(C.c_double)) if J is not None else _null())
         return E, r, g, J
+
+    def eval_fast(self, S: int, dt: float, qs, q_prev, q_cur, tau):
+        """(E, r, grad) by the O(N) evaluation (Algorithm DERIV and its
+        tangent) that the CPU baseline times; no contact points."""
+        n = self.n_dof
+        qs, qsp = _d(np.asarray(qs).reshape(S * n))
+        q_prev, pp = _d(q_prev)
+        q_cur, cp = _d(q_cur)
+        tau, tp = _d(tau)
+        r = np.zeros(S * n)
+        g = np.zeros(S * n)
+        E = lib().om_eval_fast(self._h, S, dt, qsp, pp, cp, tp,
+                               r.ctypes.data_as(C.POINTER(C.c_double)),
+                               g.ctypes.data_as(C.POINTER(C.c_double)))
+        return E, r, g
+
+    def set_fast(self, fast: bool):
+        """Makes step/rollout's L-BFGS evaluate in O(N) (om_eval_fast)."""
+        lib().om_model_set_fast(self._h, int(bool(fast)))
 
     def resid_known_jac(self, S: int, dt: float, qs, q_prev, q_cur):
         n = self.n_dof

@@ -56,6 +56,7 @@ typedef struct {
   double c_z0, c_d1, c_d2;
   int *path_len; /* number of joints from the root to l, inclusive */
   int *path;     /* [N][N]: path[l*N + k] = k-th joint on the root->l path */
+  int fast;      /* 1: L-BFGS evaluates with om_eval_fast (O(N)), see there */
 } om_model;
 
 void om_model_free(void *p) {
@@ -511,6 +512,225 @@ void om_deriv(void *p, const double *q, const double *G, double *r) {
   }
   free(F); free(T); free(Y);
 }
+
+/* ------------------------------------------------------------------ */
+/* O(N) evaluation: Algorithm DERIV and its tangent                     */
+/* ------------------------------------------------------------------ */
+/* Not the oracle's reference path (om_eval, brute force, checks the CUDA
+ * kernels): the O(N) CPU evaluation the CPU baseline times, checked against
+ * om_eval in the test suite. */
+int om_colloc(int S, double *nodes, double *W);
+int om_colloc_vel(int S, double *Vw);
+
+/* Forward kinematics by the recursion T_a = T_parent(a) F_a and the
+ * tangent Tdot_a = Tdot_parent F_a + T_parent Fdot_a along a direction v
+ * (Fdot_a = sum_k v_ak X_a dJm_a/dq_k). T, Td: [N][16]; Td may be NULL. */
+static void fk_tangent(const om_model *m, const double *q, const double *v, double *T,
+                       double *Td) {
+  for (int a = 0; a < m->n_links; ++a) {
+    int pa = m->parent[a];
+    double F[16], Fd[16], t1[16], t2[16];
+    joint_factor(m, a, q, F);
+    if (pa < 0) memcpy(T + 16 * a, F, sizeof(F));
+    else m4_mul(T + 16 * pa, F, T + 16 * a);
+    if (!Td) continue;
+    for (int i = 0; i < 16; ++i) Fd[i] = 0.0;
+    for (int k = 0; k < m->ndof[a]; ++k) {
+      double D[16];
+      joint_factor_d(m, a, q, k, D);
+      for (int i = 0; i < 16; ++i) Fd[i] += v[m->dof_off[a] + k] * D[i];
+    }
+    if (pa < 0) {
+      memcpy(Td + 16 * a, Fd, sizeof(Fd));
+    } else {
+      m4_mul(Td + 16 * pa, F, t1);
+      m4_mul(T + 16 * pa, Fd, t2);
+      for (int i = 0; i < 16; ++i) Td[16 * a + i] = t1[i] + t2[i];
+    }
+  }
+}
+
+/* d/de of om_deriv(q + e v, G) at e = 0 for fixed seeds G (the second
+ * derivatives of sum_l <G_l, T_l(q)> along v): with Y_a = G_a + sum_c Y_c
+ * F_c^T and r_ak = <Y_a, T_parent(a) X_a dJm_a/dq_k>,
+ *   Ydot_a = sum_c (Ydot_c F_c^T + Y_c Fdot_c^T),
+ *   rdot_ak = <Ydot_a, T_pa D_ak> + <Y_a, Tdot_pa D_ak>
+ *             + <Y_a, T_pa sum_j v_aj X_a d2Jm_a/dq_k dq_j>. */
+static void deriv_tangent(const om_model *m, const double *q, const double *v,
+                          const double *G, double *rd) {
+  int N = m->n_links;
+  double *F = (double *)malloc(sizeof(double) * 16 * N);
+  double *Fd = (double *)malloc(sizeof(double) * 16 * N);
+  double *T = (double *)malloc(sizeof(double) * 16 * N);
+  double *Td = (double *)malloc(sizeof(double) * 16 * N);
+  double *Y = (double *)malloc(sizeof(double) * 16 * N);
+  double *Yd = (double *)malloc(sizeof(double) * 16 * N);
+  fk_tangent(m, q, v, T, Td);
+  for (int a = 0; a < N; ++a) {
+    joint_factor(m, a, q, F + 16 * a);
+    for (int i = 0; i < 16; ++i) Fd[16 * a + i] = 0.0;
+    for (int k = 0; k < m->ndof[a]; ++k) {
+      double D[16];
+      joint_factor_d(m, a, q, k, D);
+      for (int i = 0; i < 16; ++i) Fd[16 * a + i] += v[m->dof_off[a] + k] * D[i];
+    }
+    for (int i = 0; i < 12; ++i) Y[16 * a + i] = G[12 * a + i];
+    for (int i = 12; i < 16; ++i) Y[16 * a + i] = 0.0;
+    for (int i = 0; i < 16; ++i) Yd[16 * a + i] = 0.0;
+  }
+  for (int a = N - 1; a >= 0; --a) {
+    int pa = m->parent[a];
+    for (int k = 0; k < m->ndof[a]; ++k) {
+      double D[16], DD[16], PD[16], PdD[16], PDD[16];
+      joint_factor_d(m, a, q, k, D);
+      for (int i = 0; i < 16; ++i) DD[i] = 0.0;
+      for (int j = 0; j < m->ndof[a]; ++j) {
+        double H[16];
+        joint_factor_dd(m, a, q, k, j, H);
+        for (int i = 0; i < 16; ++i) DD[i] += v[m->dof_off[a] + j] * H[i];
+      }
+      if (pa >= 0) {
+        m4_mul(T + 16 * pa, D, PD);
+        m4_mul(Td + 16 * pa, D, PdD);
+        m4_mul(T + 16 * pa, DD, PDD);
+      } else {
+        memcpy(PD, D, sizeof(PD));
+        for (int i = 0; i < 16; ++i) PdD[i] = 0.0;
+        memcpy(PDD, DD, sizeof(PDD));
+      }
+      double s = 0.0;
+      for (int i = 0; i < 16; ++i)
+        s += Yd[16 * a + i] * PD[i] + Y[16 * a + i] * (PdD[i] + PDD[i]);
+      rd[m->dof_off[a] + k] = s;
+    }
+    if (pa >= 0) {
+      /* Y_parent += Y_a F_a^T and its tangent */
+      for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+          double s = 0.0, sd = 0.0;
+          for (int t = 0; t < 4; ++t) {
+            s += Y[16 * a + 4 * i + t] * F[16 * a + 4 * j + t];
+            sd += Yd[16 * a + 4 * i + t] * F[16 * a + 4 * j + t] +
+                  Y[16 * a + 4 * i + t] * Fd[16 * a + 4 * j + t];
+          }
+          Y[16 * pa + 4 * i + j] += s;
+          Yd[16 * pa + 4 * i + j] += sd;
+        }
+    }
+  }
+  free(F); free(Fd); free(T); free(Td); free(Y); free(Yd);
+}
+
+/* E, r and dE/dq of one step in O(N) per stage (no contact points): the
+ * residual of every stage by om_deriv with the seeds of Eq. HOC; for S >= 2
+ * the gradient of Eq. EQHOC, 2 Jr^T r, by
+ *   (Jr^T v)_k = d/de om_deriv(q_k + e v_k, G_k)   (own-stage curvature)
+ *              + om_deriv(q_k, B_k),  B_k,l = (sum_i W_ik Tdot_i,l) M_l
+ * (the seeds' dependence on stage k; Tdot_i,l = dT_l(q_i)/dq_i v_i, M_l
+ * symmetric), with v = r. The same quantities as om_eval, in O(N). */
+double om_eval_fast(void *p, int S, double dt, const double *qs, const double *q_prev,
+                    const double *q_cur, const double *tau, double *r, double *grad) {
+  om_model *m = (om_model *)p;
+  int N = m->n_links, n = m->n_dof, P = S + 2, Sn = S * n;
+  double nodes[16], W[8 * 16], Vw[8 * 16], Wt[8 * 16];
+  om_colloc(S, nodes, W);
+  om_colloc_vel(S, Vw);
+  double idt2 = 1.0 / (dt * dt);
+  for (int k = 0; k < S * P; ++k) Wt[k] = (W[k] + 2.0 * m->drag * Vw[k]) * idt2;
+  double *T = (double *)malloc(sizeof(double) * 16 * N * P);
+  double *G = (double *)malloc(sizeof(double) * 12 * N);
+  double *rr = r ? r : (double *)malloc(sizeof(double) * Sn);
+  const double *qnode[16];
+  qnode[0] = q_prev;
+  qnode[1] = q_cur;
+  for (int i = 0; i < S; ++i) qnode[2 + i] = qs + i * n;
+  for (int j = 0; j < P; ++j) fk_tangent(m, qnode[j], NULL, T + 16 * N * j, NULL);
+  double E = 0.0;
+  for (int i = 0; i < S; ++i) {
+    for (int l = 0; l < N; ++l) {
+      double A[16], M[16], GG[16];
+      mm4(m->mm + 10 * l, M);
+      for (int k = 0; k < 16; ++k) {
+        double sum = 0;
+        for (int j = 0; j < P; ++j) sum += Wt[i * P + j] * T[16 * N * j + 16 * l + k];
+        A[k] = sum;
+      }
+      m4_mul(A, M, GG);
+      for (int rw = 0; rw < 3; ++rw)
+        for (int c = 0; c < 4; ++c) GG[4 * rw + c] -= m->g[rw] * m->mm[10 * l + 6 + c];
+      memcpy(G + 12 * l, GG, sizeof(double) * 12);
+    }
+    om_deriv(m, qnode[2 + i], G, rr + i * n);
+    for (int d = 0; d < n; ++d) rr[i * n + d] -= tau[d];
+  }
+  if (S == 1) {
+    for (int l = 0; l < N; ++l) {
+      double M[16], D[16], DM[16];
+      mm4(m->mm + 10 * l, M);
+      for (int k = 0; k < 16; ++k)
+        D[k] = T[16 * N * 2 + 16 * l + k] - 2 * T[16 * N + 16 * l + k] + T[16 * l + k];
+      m4_mul(D, M, DM);
+      E += 0.5 * idt2 * contract34(DM, D);
+      if (m->drag != 0.0) {
+        double Dv[16], DvM[16];
+        for (int k = 0; k < 16; ++k) Dv[k] = T[16 * N * 2 + 16 * l + k] - T[16 * N + 16 * l + k];
+        m4_mul(Dv, M, DvM);
+        E += m->drag * idt2 * contract34(DvM, Dv);
+      }
+      for (int rw = 0; rw < 3; ++rw)
+        for (int c = 0; c < 4; ++c)
+          E -= m->g[rw] * T[16 * N * 2 + 16 * l + 4 * rw + c] * m->mm[10 * l + 6 + c];
+    }
+    for (int d = 0; d < n; ++d) E -= tau[d] * qs[d];
+    if (grad) memcpy(grad, rr, sizeof(double) * Sn);
+  } else {
+    for (int k = 0; k < Sn; ++k) E += rr[k] * rr[k];
+    if (grad) {
+      double *Td = (double *)malloc(sizeof(double) * 16 * N * S);
+      double *Tt = (double *)malloc(sizeof(double) * 16 * N);
+      double *rd = (double *)malloc(sizeof(double) * n);
+      for (int i = 0; i < S; ++i) fk_tangent(m, qnode[2 + i], rr + i * n, Tt, Td + 16 * N * i);
+      for (int k = 0; k < S; ++k) {
+        /* own-stage curvature along v_k with the seeds G_k */
+        for (int l = 0; l < N; ++l) {
+          double A[16], M[16], GG[16];
+          mm4(m->mm + 10 * l, M);
+          for (int e = 0; e < 16; ++e) {
+            double sum = 0;
+            for (int j = 0; j < P; ++j) sum += Wt[k * P + j] * T[16 * N * j + 16 * l + e];
+            A[e] = sum;
+          }
+          m4_mul(A, M, GG);
+          for (int rw = 0; rw < 3; ++rw)
+            for (int c = 0; c < 4; ++c) GG[4 * rw + c] -= m->g[rw] * m->mm[10 * l + 6 + c];
+          memcpy(G + 12 * l, GG, sizeof(double) * 12);
+        }
+        deriv_tangent(m, qnode[2 + k], rr + k * n, G, grad + k * n);
+        /* dependence of every stage's seeds on stage k */
+        for (int l = 0; l < N; ++l) {
+          double Bs[16], M[16], BM[16];
+          mm4(m->mm + 10 * l, M);
+          for (int e = 0; e < 16; ++e) {
+            double sum = 0;
+            for (int i = 0; i < S; ++i) sum += Wt[i * P + 2 + k] * Td[16 * N * i + 16 * l + e];
+            Bs[e] = sum;
+          }
+          m4_mul(Bs, M, BM);
+          memcpy(G + 12 * l, BM, sizeof(double) * 12);
+        }
+        om_deriv(m, qnode[2 + k], G, rd);
+        for (int d = 0; d < n; ++d) grad[k * n + d] = 2.0 * (grad[k * n + d] + rd[d]);
+      }
+      free(Td); free(Tt); free(rd);
+    }
+  }
+  free(T); free(G);
+  if (!r) free(rr);
+  return E;
+}
+
+/* Makes the model's L-BFGS evaluate with om_eval_fast (1) or om_eval (0). */
+void om_model_set_fast(void *p, int fast) { ((om_model *)p)->fast = fast; }
 
 /* Accumulates H[d][e] += sum over (d,e) on the root->l path of
  * (d2 T_l / dq_d dq_e) : G, with G a 3x4 (12 entries) matrix. H: [n][n]. */
@@ -1310,9 +1530,13 @@ typedef struct {
   double *r, *g;
 } om_point;
 
+double om_eval_fast(void *p, int S, double dt, const double *qs, const double *q_prev,
+                    const double *q_cur, const double *tau, double *r, double *grad);
+
 static double eval_point(om_model *m, int S, double dt, const double *x,
                          const double *qp, const double *qc, const double *tau,
                          double *r, double *g) {
+  if (m->fast && m->n_contact == 0) return om_eval_fast(m, S, dt, x, qp, qc, tau, r, g);
   return om_eval(m, S, dt, x, qp, qc, tau, r, g, NULL);
 }
 

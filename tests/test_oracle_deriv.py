@@ -73,3 +73,41 @@ def test_deriv_reproduces_stage_residual(S):
             G[l] = A @ M - np.outer(g, s[6:10])
         ri = om.deriv(qs[i], G) - tau
         assert relerr(ri, r[i * n:(i + 1) * n]) < 1e-10, i
+
+
+@pytest.mark.parametrize("S", [1, 2, 3, 4])
+def test_o_n_evaluation_equals_brute_force(S):
+    """The O(N) evaluation the CPU baseline times (Algorithm DERIV for the
+    stage residuals and its tangent for the Eq. EQHOC gradient) gives the
+    brute-force evaluation's E, r and dE/dq on chains, a tree and a free
+    root, with drag."""
+    rng = np.random.default_rng(40 + S)
+    specs = [I.rod_chain(2, 5, name="rod5"), I.ball_chain(2, 6, seed=3, radius=0.15),
+             I.humanoid(2, seed=4), I.free_chain(2, 4, name="free4")]
+    for spec in specs:
+        for drag in (0.0, 0.4):
+            om = O.OracleModel.from_spec(spec, 1, drag=drag)
+            n = spec.n_dof
+            qc = rng.uniform(-0.6, 0.6, n)
+            qp = qc + rng.normal(0, 0.02, n)
+            qs = qc[None] + rng.normal(0, 0.03, (S, n))
+            tau = rng.normal(0, 0.3, n)
+            E, r, g, _ = om.eval(S, 0.033, qs, qp, qc, tau, True)
+            Ef, rf, gf = om.eval_fast(S, 0.033, qs, qp, qc, tau)
+            assert abs(E - Ef) <= 1e-12 * abs(E), (spec.name, drag)
+            assert np.max(np.abs(r - rf)) <= 1e-12 * np.max(np.abs(r)), (spec.name, drag)
+            assert np.max(np.abs(g - gf)) <= 1e-12 * np.max(np.abs(g)), (spec.name, drag)
+
+
+def test_o_n_lbfgs_rollout_follows_brute_force():
+    """The oracle's L-BFGS with the O(N) evaluation takes the same steps as
+    with the brute-force one (the evaluations agree to rounding)."""
+    w = I.pendulum3()
+    spec = w["spec"]
+    om = O.OracleModel.from_spec(spec, 0)
+    q0 = w["q0"][0]
+    ref = om.rollout(1, w["dt"], q0, q0, np.zeros((30, 3)), "lbfgs", 5, w["tol"], 1000)
+    om.set_fast(True)
+    fast = om.rollout(1, w["dt"], q0, q0, np.zeros((30, 3)), "lbfgs", 5, w["tol"], 1000)
+    assert ref["status"] == fast["status"] == 0
+    assert np.max(np.abs(ref["traj_cur"] - fast["traj_cur"])) <= 1e-9
