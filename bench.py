@@ -39,13 +39,32 @@ TANGENT_FLOPS = {0: 327, 1: 680}
 ENERGY_FLOPS = 54                   # Eq. EQ energy terms (one stage only)
 COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 
-# DRAM bytes (read + write) of the rollout kernel per instance-evaluation,
-# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum, one
-# pass) of a full 100-step k_rollout<3, 0> launch on 4096 ten-link ball
-# chains (profiles/k_rollout_ballchains4096_launches.md): 1758.7 GB over
-# 56,284,962 instance-evaluations. The roofline's traffic field scales it by
-# the evaluations of the timed launch. Valid for the kernel as captured.
-ROLLOUT_DRAM_BYTES_PER_EVAL = 31247.2
+# DRAM bytes (read + write) per instance-evaluation of the rollout kernel,
+# from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
+# launch named by the key (mapping, stages, links), valid only for the kernel
+# sources whose hash is stored with it: any change to csrc/ makes the
+# roofline's traffic null until the kernel is captured again.
+ROLLOUT_TRAFFIC = {}
+
+
+def csrc_hash() -> str:
+    """SHA-1 of the CUDA sources (the kernels the traffic figures describe)."""
+    import hashlib
+    h = hashlib.sha1()
+    d = os.path.join(ROOT, "paper_1709_04145_b300", "csrc")
+    for f in sorted(os.listdir(d)):
+        if f.endswith((".cu", ".cuh")):
+            with open(os.path.join(d, f), "rb") as fh:
+                h.update(f.encode() + fh.read())
+    return h.hexdigest()
+
+
+def rollout_traffic(mapping, S, N, evals_total):
+    """DRAM bytes of one rollout launch from the stored capture, or None."""
+    rec = ROLLOUT_TRAFFIC.get((mapping, S, N))
+    if rec is None or rec[0] != csrc_hash():
+        return None
+    return rec[1] * evals_total
 
 
 def primal_flops_per_eval(jtypes, S):
@@ -77,6 +96,30 @@ def rollout_flops(spec, S, m, evals, grads, iters):
             float(iters.sum()) * lbfgs_flops_per_iter(spec.n_dof, S, m))
 
 
+STATUS_NAMES = ("CONVERGED", "MAX_ITER", "LS_FAIL", "CHOL_FAIL", "NONFINITE", "STALLED")
+
+
+def step_outcomes(out, sl=None):
+    """Per-step outcome record of a rollout from its step logs: the fraction
+    of instance-steps that ended in each status, the fraction solved
+    (CONVERGED or STALLED) and the median / max |r|_2 at which the steps
+    ended. sl selects a slice of instances (a bucket)."""
+    import numpy as np
+    st = out["step_status"].cpu().numpy()
+    rn = out["step_rnorm"].cpu().numpy()
+    if sl is not None:
+        st, rn = st[:, sl], rn[:, sl]
+    n = st.size
+    frac = {nm: float((st == k).sum()) / n for k, nm in enumerate(STATUS_NAMES)}
+    fin = np.isfinite(rn)
+    return {"instance_steps": int(n),
+            "fractions": {k: v for k, v in frac.items() if v > 0},
+            "solved_fraction": frac["CONVERGED"] + frac["STALLED"],
+            "exit_rnorm_median": float(np.median(rn[fin])) if fin.any() else None,
+            "exit_rnorm_max": float(np.max(rn[fin])) if fin.any() else None,
+            "exit_rnorm_nonfinite": int((~fin).sum())}
+
+
 def lbfgs_flops_per_iter(n, S, m):
     """Two-loop recursion, preconditioner, dots and updates per iteration."""
     return S * n * (8 * m + 20 + 2 * 3 + 2 * S)
@@ -98,14 +141,18 @@ def parse():
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
     p.add_argument("--threads", type=int, default=0,
-                   help="threads per block (0 = autotune over 32/64/128 on a short rollout)")
+                   help="threads per block (0 = autotune the mapping and 32/64/128 threads on a "
+                        "short rollout)")
+    p.add_argument("--mapping", type=int, default=0,
+                   help="instance-to-lane mapping when --threads is given: 0 one lane per stage, "
+                        "1 one lane per stage and link")
     p.add_argument("--plain-instances", type=int, default=8,
                    help="instances timed in the plain form (one launch per instance-step)")
     p.add_argument("--plain-timesteps", type=int, default=10)
     p.add_argument("--throughput-instances", type=int, default=65536,
                    help="instances of the large-batch throughput point (0 = skip)")
     p.add_argument("--throughput-timesteps", type=int, default=20)
-    p.add_argument("--uneven-steps", type=int, default=4,
+    p.add_argument("--uneven-steps", type=int, default=20,
                    help="steps of the uneven three-bucket batch (0 = skip)")
     p.add_argument("--max-iter-uneven", type=int, default=100)
     p.add_argument("--drag-steps", type=int, default=20,
@@ -115,13 +162,23 @@ def parse():
                         "(0 = skip the mixed-precision section)")
     p.add_argument("--dt-sweep", action="store_true",
                    help="add a step-size sweep of both solvers (ball and hinge chains, dt 0.001-0.128)")
-    p.add_argument("--scaling-steps", type=int, default=1,
+    p.add_argument("--scaling-steps", type=int, default=50,
                    help="steps per rollout of the hinge-chain scaling study (0 = skip)")
+    p.add_argument("--scaling-budget", type=float, default=10.0,
+                   help="seconds per (links, solver) row of the scaling study: fewer steps are "
+                        "run when a one-step probe says the requested ones would take longer")
     p.add_argument("--scaling-links", type=int, nargs="+", default=[25, 50, 100, 200])
     p.add_argument("--max-iter-scaling", type=int, default=3,
                    help="iteration cap per step of the scaling study (a fixed budget: the study "
                         "compares the cost per iteration of the two solvers)")
-    p.add_argument("--adjoint-steps", type=int, default=8,
+    p.add_argument("--companion-steps-thin", type=int, default=20,
+                   help="steps of the 0.05 m capsule variants")
+    p.add_argument("--no-pendulum", dest="pendulum", action="store_false",
+                   help="skip the plain-method pendulum (batch 1, 200 steps)")
+    p.add_argument("--companion-steps", type=int, default=100,
+                   help="steps of the headline batch solved by Newton and of the 0.05 m capsule "
+                        "variants (0 = skip)")
+    p.add_argument("--adjoint-steps", type=int, default=64,
                    help="steps of the differentiable humanoid rollout timed forward and forward+adjoint "
                         "(0 = skip; the workload defines 64)")
     return p.parse_args()
@@ -223,11 +280,14 @@ def _oracle_worker_init():
 
 def _oracle_instance(job):
     """Runs the CPU oracle on one instance (spawned worker); returns its
-    compute seconds, iterations and evaluations."""
+    compute seconds, iterations and evaluations. fast: its L-BFGS evaluates
+    with the O(N) path (Algorithm DERIV and its tangent) instead of the
+    brute-force one."""
     import numpy as np
     from oracle import oracle as O
-    spec, b, qp, qc, S, dt, m, tol, max_iter, n_steps = job
+    spec, b, qp, qc, S, dt, m, tol, max_iter, n_steps, fast = job
     om = O.OracleModel.from_spec(spec, b)
+    om.set_fast(fast)
     t0 = time.perf_counter()
     res = om.rollout(S, dt, qp, qc, np.zeros((n_steps, om.n_dof)), "lbfgs", m, tol, max_iter)
     return time.perf_counter() - t0, res["iters"], res["evals"]
@@ -244,7 +304,7 @@ def _cpu_model() -> str:
     return "unknown"
 
 
-def cpu_oracle_rate(w, n_inst, n_steps, budget_s):
+def cpu_oracle_rate(w, n_inst, n_steps, budget_s, fast=False):
     """Oracle link-steps/s on the host cores over a bounded sample: the first
     n_inst instances of the workload, one process per core (spawn; started,
     imported and warmed before the timed map). n_steps = 0 picks the number
@@ -262,7 +322,7 @@ def cpu_oracle_rate(w, n_inst, n_steps, budget_s):
 
     def job(b, steps):
         return (spec.select([b]), 0, qp[b], w["q0"][b], S, dt, w["history"], w["tol"],
-                w["max_iter"], steps)
+                w["max_iter"], steps, fast)
 
     ctx = mp.get_context("spawn")
     with ctx.Pool(procs, initializer=_oracle_worker_init) as pool:
@@ -276,7 +336,8 @@ def cpu_oracle_rate(w, n_inst, n_steps, budget_s):
         wall = time.perf_counter() - t0
     link_steps = n_inst * spec.n_links * n_steps
     sample = (f"{n_inst} of {spec.count} instances x the first {n_steps} of {w['n_steps']} time "
-              f"steps, same solver settings; {wall:.1f} s wall on {procs} processes "
+              f"steps, same solver settings, {'O(N)' if fast else 'brute-force O(N^2)'} "
+              f"evaluations; {wall:.1f} s wall on {procs} processes "
               f"({sum(r[0] for r in res):.1f} s of oracle compute), {_cpu_model()}, "
               f"nproc {os.cpu_count()}")
     return link_steps / wall, procs, sample
@@ -284,31 +345,22 @@ def cpu_oracle_rate(w, n_inst, n_steps, budget_s):
 
 # --------------------------------------------------------------------- ours
 def autotune(P, batch, args, w):
-    """Picks the threads per block (instance-to-warp mapping) with the
-    shortest 2-step rollout of this workload."""
+    """Picks the instance-to-lane mapping (one lane per stage, or one per
+    stage and link) and the threads per block with the shortest 2-step
+    rollout of this workload. Returns (mapping, threads, trials)."""
     import torch
+    from paper_1709_04145_b300.tuning import autotune_mapping
     S, dt, m = w["stages"], w["dt"], w["history"]
     nodes, _ = P.colloc(S)
     dev = torch.device("cuda", torch.cuda.current_device())
     qc = torch.tensor(w["q0"].reshape(-1), device=dev)
     qp = torch.tensor((w["q0"] + nodes[0] * dt * w["qd0"]).reshape(-1), device=dev)
-    best, best_ms = 32, float("inf")
-    for threads in (32, 64, 128):
-        batch.set_threads(threads)
-        P.rollout(batch, qp, qc, None, 1, dt, S, P.LBFGS, m, w["tol"], min(w["max_iter"], 20), want_traj=False)
-        torch.cuda.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record()
-        P.rollout(batch, qp, qc, None, 2, dt, S, P.LBFGS, m, w["tol"], min(w["max_iter"], 20), want_traj=False)
-        e1.record()
-        torch.cuda.synchronize()
-        ms = e0.elapsed_time(e1)
-        if ms < best_ms:
-            best, best_ms = threads, ms
-    return best
+    probe = lambda: P.rollout(batch, qp, qc, None, 2, dt, S, P.LBFGS, m, w["tol"],
+                              min(w["max_iter"], 20), want_traj=False, want_step_log=False)
+    return autotune_mapping(batch, probe, mappings=(P.MAP_STAGE, P.MAP_LINK))
 
 
-def measure_throughput_point(P, args, dev, threads):
+def measure_throughput_point(P, args, dev, threads, mapping):
     """The same rollout on a large batch (65536 ten-link ball chains, 20
     steps): every FP64 sub-partition busy. Returns link-steps/s and the FP64
     roofline fraction."""
@@ -323,6 +375,7 @@ def measure_throughput_point(P, args, dev, threads):
     nodes, _ = P.colloc(S)
     batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=S, max_history=m)
     batch.set_threads(threads)
+    batch.set_mapping(mapping)
     qp = torch.tensor((w["q0"] + nodes[0] * dt * w["qd0"]).reshape(-1), device=dev)
     qc = torch.tensor(w["q0"].reshape(-1), device=dev)
     T = w["n_steps"]
@@ -339,7 +392,7 @@ def measure_throughput_point(P, args, dev, threads):
     flops = rollout_flops(spec, S, m, ev, out["grads"].cpu().numpy(), it)
     return {"value": spec.count * spec.n_links * T / (ms / 1e3), "unit": UNIT, "ms": ms,
             "instances": spec.count, "timesteps": T, "achieved_tflops": flops / (ms / 1e3) / 1e12,
-            "evals_per_step": float(ev.mean() / T)}
+            "evals_per_step": float(ev.mean() / T), "step_outcomes": step_outcomes(out)}
 
 
 def measure_plain(P, w, args, dev):
@@ -374,6 +427,79 @@ def measure_plain(P, w, args, dev):
     return {"value": n_inst * spec.n_links * T / (ms / 1e3), "unit": UNIT, "ms": ms,
             "sample": f"{n_inst} instances x {T} time steps, one pbad_step launch per "
                       "instance-step, no graph"}
+
+
+def measure_pendulum(P, args, dev):
+    """The plain method, batch 1: the 3-link rod pendulum (dt = 0.01, one
+    stage, L-BFGS m = 5, |r| < 1e-10, 200 steps) as one persistent rollout
+    launch under each mapping, and as 200 pbad_step launches (one per
+    step, no graph)."""
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    w = I.pendulum3()
+    spec, T = w["spec"], w["n_steps"]
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=1,
+                    max_history=w["history"])
+    q0 = torch.tensor(w["q0"].reshape(-1), device=dev)
+    out = {"instances": 1, "links": spec.n_links, "timesteps": T, "dt": w["dt"], "stages": 1,
+           "history": w["history"], "tol": w["tol"]}
+    for name, mp in (("rollout_stage_mapping", P.MAP_STAGE), ("rollout_link_mapping", P.MAP_LINK)):
+        batch.set_mapping(mp)
+        run = lambda: P.rollout(batch, q0, q0, None, T, w["dt"], 1, P.LBFGS, w["history"], w["tol"],
+                                1000, want_traj=False)
+        run()
+        ms, res = _timed(run)
+        out[name] = {"ms": ms, "value": spec.n_links * T / (ms / 1e3), "unit": UNIT,
+                     "iters_per_step": float(res["iters"].float().mean().item() / T),
+                     "step_outcomes": step_outcomes(res)}
+    batch.set_mapping(P.MAP_STAGE)
+
+    def per_step():
+        qp, qc = q0, q0
+        for _ in range(T):
+            o = P.step(batch, qp, qc, None, w["dt"], 1, P.LBFGS, w["history"], w["tol"], 1000)
+            qp, qc = o["q_prev"], o["q_cur"]
+        return qc
+    per_step()
+    ms, _ = _timed(per_step)
+    out["per_step_launches"] = {"ms": ms, "value": spec.n_links * T / (ms / 1e3), "unit": UNIT,
+                                "launches": T}
+    return out
+
+
+def measure_companions(P, args, dev):
+    """The headline batch (4096 ten-link ball chains, dt = 0.033, three
+    stages, 100 steps) solved by Newton (LM) instead of L-BFGS, and both
+    solvers on the same chains with the 0.05 m capsule radius first proposed
+    for them; one timed rollout each after a warm-up rollout, with the
+    per-step outcomes."""
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    rows = {}
+    for radius in (0.15, 0.05):
+        T = args.companion_steps if radius == 0.15 else args.companion_steps_thin
+        w = I.ball_chains(count=args.instances, n_links=args.links, n_steps=T, radius=radius)
+        spec, S, dt, m = w["spec"], w["stages"], w["dt"], w["history"]
+        batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=S, max_history=m,
+                        newton=True)
+        qp, qc = _state_tensors(P, [(w["q0"], w["qd0"])], S, dt, dev)
+        for name, sv, mi in (("newton", P.NEWTON, 100), ("lbfgs", P.LBFGS, args.max_iter)):
+            if radius == 0.15 and sv == P.LBFGS:
+                continue  # the headline itself
+            run = lambda T_: P.rollout(batch, qp, qc, None, T_, dt, S, sv, m, args.tol, mi,
+                                       want_traj=False)
+            run(2)
+            ms, out = _timed(lambda: run(T))
+            it = out["iters"].float().mean().item() / T
+            rows[f"{name}_radius{radius}"] = {
+                "solver": name, "capsule_radius_m": radius, "instances": spec.count,
+                "links": spec.n_links, "timesteps": T, "dt": dt, "stages": S, "tol": args.tol,
+                "max_iter_per_step": mi, "ms": ms,
+                "value": spec.count * spec.n_links * T / (ms / 1e3), "unit": UNIT,
+                "iters_per_step": it, "step_outcomes": step_outcomes(out)}
+        del batch
+        torch.cuda.empty_cache()
+    return rows
 
 
 def measure_adjoint(P, args, dev):
@@ -412,18 +538,22 @@ def measure_adjoint(P, args, dev):
     b.record()
     torch.cuda.synchronize()
     fwd = a.elapsed_time(b)
+    adj = torch.empty(spec.count, dtype=torch.int32, device=dev)
     a, b = ev(), ev()
     a.record()
-    qc, _, st = rollout_differentiable(batch, x0, v0, tt, **kw)
+    qc, _, st = rollout_differentiable(batch, x0, v0, tt, adjoint_status=adj, **kw)
     loss = ((points_differentiable(batch, qc, [w["ee_link"]], tip) - target) ** 2).sum()
     loss.backward()
     b.record()
     torch.cuda.synchronize()
     stc = st.cpu().numpy()
+    adjc = adj.cpu().numpy()
     return {"fwd_ms": fwd, "fwd_adjoint_ms": a.elapsed_time(b), "steps": steps,
             "workload_steps": 64, "instances": spec.count,
-            "converged_fraction": float((stc == 0).mean()),
-            "note": f"{steps} of the workload's 64 steps timed"}
+            "all_steps_converged_fraction": float((stc == 0).mean()),
+            "gradient_valid_fraction": float(np.isin(adjc, [0, 5]).mean()),
+            "note": "gradients of instances with an unsolved step (or a singular adjoint "
+                    "system) are NaN (the implicit-function theorem needs r = 0)"}
 
 
 def _state_tensors(P, spec_states, S, dt, dev):
@@ -484,7 +614,8 @@ def measure_uneven(P, args, dev):
                         "dofs": spec.n_dof, "solver": u["solvers"][k],
                         "converged_fraction": float((st[a:b] == 0).mean()),
                         "iters_per_step": float(it[a:b].mean() / T),
-                        "evals_per_step": float(evl[a:b].mean() / T)})
+                        "evals_per_step": float(evl[a:b].mean() / T),
+                        "step_outcomes": step_outcomes(out, slice(a, b))})
     res = {"value": link_steps / (ms / 1e3), "unit": UNIT, "ms": ms, "timesteps": T,
            "launches": 1, "threads_per_block": best,
            "autotune_ms_per_step": {str(k): v for k, v in tuned.items()},
@@ -511,7 +642,9 @@ def measure_uneven(P, args, dev):
         "buckets": [{"model": spec.name,
                      "probe": {names[r.solver]: {"ms": r.ms, "converged_fraction": r.converged / r.total}
                                for r in report[k]},
-                     "converged_fraction": float((st_c[int(batch.inst_off[k]):int(batch.inst_off[k + 1])] == 0).mean())}
+                     "converged_fraction": float((st_c[int(batch.inst_off[k]):int(batch.inst_off[k + 1])] == 0).mean()),
+                     "step_outcomes": step_outcomes(out_c, slice(int(batch.inst_off[k]),
+                                                                 int(batch.inst_off[k + 1])))}
                     for k, spec in enumerate(u["specs"])]}
     return res
 
@@ -539,7 +672,8 @@ def measure_drag(P, args, dev):
                        "instances": spec.count, "links": spec.n_links, "timesteps": T, "dt": dt,
                        "stages": S, "drag": w["drag"], "tol": w["tol"],
                        "converged_fraction": float((st == 0).mean()),
-                       "iters_per_step": float(res["iters"].float().mean().item() / T)}
+                       "iters_per_step": float(res["iters"].float().mean().item() / T),
+                       "step_outcomes": step_outcomes(res)}
     # Section 6.2's swimmer body: 4 links on a free 6-DOF root (9 DOFs)
     w = I.swimmers_free(n_steps=args.drag_steps)
     spec, S, dt, m = w["spec"], w["stages"], w["dt"], w["history"]
@@ -557,7 +691,8 @@ def measure_drag(P, args, dev):
                                  "dofs": spec.n_dof, "timesteps": T, "dt": dt, "stages": S,
                                  "drag": w["drag"], "tol": w["tol"],
                                  "converged_fraction": float((st == 0).mean()),
-                                 "iters_per_step": float(res["iters"].float().mean().item() / T)}
+                                 "iters_per_step": float(res["iters"].float().mean().item() / T),
+                                 "step_outcomes": step_outcomes(res)}
     # Section 6.2's spider on the ground (free root, 4 legs, 22 DOFs, six
     # contact points of Eq. FRI), one stage, both solvers
     w = I.spiders(n_steps=args.drag_steps)
@@ -577,7 +712,8 @@ def measure_drag(P, args, dev):
             "instances": spec.count, "links": bodies, "dofs": spec.n_dof, "timesteps": T, "dt": dt,
             "stages": S, "contact_points": len(w["contact"]["link"]), "tol": w["tol"],
             "max_iter_per_step": mi, "worst_status_converged_fraction": float((st == 0).mean()),
-            "iters_per_step": float(res["iters"].float().mean().item() / T)}
+            "iters_per_step": float(res["iters"].float().mean().item() / T),
+            "step_outcomes": step_outcomes(res)}
     wb = I.ball_chains(count=args.instances, n_links=args.links, n_steps=5)
     spec = wb["spec"]
     S, dt, m = wb["stages"], wb["dt"], wb["history"]
@@ -590,7 +726,8 @@ def measure_drag(P, args, dev):
         run()
         ms, res = _timed(run)
         row[f"c={c}"] = {"ms": ms, "value": spec.count * spec.n_links * 5 / (ms / 1e3),
-                         "evals_per_step": float(res["evals"].float().mean().item() / 5)}
+                         "evals_per_step": float(res["evals"].float().mean().item() / 5),
+                         "step_outcomes": step_outcomes(res)}
     out["ball_chains_5_steps"] = row
     return out
 
@@ -616,7 +753,8 @@ def measure_mixed_precision(P, args, dev):
             row[label] = {"ms": ms, "value": units * T / (ms / 1e3), "unit": UNIT,
                           "iters_per_step": float(res["iters"].float().mean().item() / T),
                           "evals_per_step": float(res["evals"].float().mean().item() / T),
-                          "status_counts": np.bincount(st, minlength=5).tolist()}
+                          "status_counts": np.bincount(st, minlength=6).tolist(),
+                          "step_outcomes": step_outcomes(res)}
         row["speedup"] = row["f64"]["ms"] / row["f32_direction"]["ms"]
         row.update({"timesteps": T, "stages": S, "dt": dt, "tol": tol, "max_iter": max_iter})
         out[name] = row
@@ -645,6 +783,47 @@ def measure_mixed_precision(P, args, dev):
     return out
 
 
+def measure_df64(P, args, dev):
+    """Double-float residual pass against the binary64 one on the batched
+    workload's 4096 ten-link ball chains (three stages, link mapping): time
+    per evaluation launch (E, r and the binary64 gradient tangent pass) at
+    the steps' initial guesses, and the difference of the residuals at
+    solved steps (Newton to |r| < 1e-8) against the tolerance."""
+    import numpy as np
+    import torch
+    from paper_1709_04145_b300 import inputs as I
+    w = I.ball_chains(count=args.instances, n_links=args.links, n_steps=1)
+    spec, S, dt = w["spec"], w["stages"], w["dt"]
+    nodes, _ = P.colloc(S)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    qp, qc = t(w["q0"] + nodes[0] * dt * w["qd0"]), t(w["q0"])
+    batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=S, max_history=8,
+                    newton=True)
+    step = P.step(batch, qp, qc, None, dt, S, P.NEWTON, 8, 1e-8, 100)
+    solved = step["status"].cpu().numpy() == 0
+    guess = torch.cat([qc.view(spec.count, 1, -1) + (nodes[2 + i] / (0 - nodes[0])) *
+                       (qc - qp).view(spec.count, 1, -1) for i in range(S)], dim=1).reshape(-1)
+    out = {"instances": spec.count, "stages": S, "launches_timed": 50}
+    res = {}
+    batch.set_mapping(P.MAP_LINK)
+    for name, prec in (("f64", P.PRECISION_F64), ("df64", P.PRECISION_DF64)):
+        batch.set_precision(prec)
+        run = lambda: [P.eval_objective_grad(batch, guess, qp, qc, None, dt, S) for _ in range(50)]
+        run()
+        ms, _ = _timed(run)
+        out[f"{name}_ms_per_eval"] = ms / 50
+        _, _, r = P.eval_objective_grad(batch, step["q_stages"], qp, qc, None, dt, S)
+        res[name] = r.cpu().numpy().reshape(spec.count, -1)
+    batch.set_precision(P.PRECISION_F64)
+    out["df64_speedup"] = out["f64_ms_per_eval"] / out["df64_ms_per_eval"]
+    d = np.linalg.norm(res["df64"] - res["f64"], axis=1)[solved]
+    out["solved_steps"] = int(solved.sum())
+    out["residual_difference_at_solved_steps"] = {
+        "median": float(np.median(d)), "max": float(np.max(d)), "tol": 1e-8,
+        "fraction_above_tol": float((d > 1e-8).mean())}
+    return out
+
+
 def measure_dt_sweep(P, args, dev):
     """Step-size sweep of both solvers on two bodies: 512 ten-link ball chains
     (three stages) and 512 five-link hinge-rod chains (two stages), two
@@ -667,17 +846,19 @@ def measure_dt_sweep(P, args, dev):
 
 def measure_scaling(P, args, dev):
     """Scaling study: serial hinge-rod chains of N links, batch 256, dt = 0.1,
-    four stages; L-BFGS (m = 8) and Newton on the same inputs; a forward
-    rollout and a forward + adjoint pass (end-state loss) of
-    args.scaling_steps steps each."""
+    four stages; L-BFGS (m = 8) and Newton on the same inputs, at most
+    args.max_iter_scaling iterations per step (the study compares the cost
+    per iteration). Each (N, solver) runs args.scaling_steps steps forward
+    in one launch, fewer when a one-step probe says they would take more
+    than args.scaling_budget seconds (the row says how many), and a forward
+    + adjoint pass (end-state loss) over the first min(steps, 8) steps."""
     import numpy as np
     import torch
     from paper_1709_04145_b300 import inputs as I
     from paper_1709_04145_b300.autograd import rollout_differentiable
-    T = args.scaling_steps
     rows = []
     for N in args.scaling_links:
-        w = I.scaling_chains(N, n_steps=T)
+        w = I.scaling_chains(N, n_steps=args.scaling_steps)
         spec = w["spec"]
         S, dt, m = w["stages"], w["dt"], w["history"]
         batch = P.Batch([P.Model.from_spec(spec, device=dev.index)], max_stages=S, max_history=m,
@@ -685,11 +866,14 @@ def measure_scaling(P, args, dev):
         qp, qc = _state_tensors(P, [(w["q0"], w["qd0"])], S, dt, dev)
         x0 = torch.tensor(w["q0"].reshape(-1), device=dev)
         v0 = torch.tensor(w["qd0"].reshape(-1), device=dev)
-        tau = torch.zeros((T, batch.D), dtype=torch.float64, device=dev)
         for name, sv in (("lbfgs", P.LBFGS), ("newton", P.NEWTON)):
-            ms, out = _timed(lambda: P.rollout(batch, qp, qc, None, T, dt, S, sv, m, w["tol"],
-                                               args.max_iter_scaling, want_traj=False))
-            st = out["status"].cpu().numpy()
+            run = lambda T_: P.rollout(batch, qp, qc, None, T_, dt, S, sv, m, w["tol"],
+                                       args.max_iter_scaling, want_traj=False)
+            ms1, _ = _timed(lambda: run(1))
+            T = int(max(1, min(args.scaling_steps, args.scaling_budget * 1e3 // max(ms1, 1e-3))))
+            ms, out = _timed(lambda: run(T))
+            Ta = min(T, 8)
+            tau = torch.zeros((Ta, batch.D), dtype=torch.float64, device=dev)
 
             def fwd_adj():
                 xg = x0.clone().requires_grad_()
@@ -697,20 +881,21 @@ def measure_scaling(P, args, dev):
                 tg = tau.clone().requires_grad_()
                 qe, _, _ = rollout_differentiable(batch, xg, vg, tg, dt, S, solver=sv, history=m,
                                                   tol=w["tol"], max_iter=args.max_iter_scaling,
-                                                  checkpoint_every=8)
+                                                  checkpoint_every=8, on_unsolved="keep")
                 (qe ** 2).sum().backward()
                 return tg.grad
             ms_fa, _ = _timed(fwd_adj)
             its = float(out["iters"].float().mean().item() / T)
             rows.append({"links": N, "solver": name, "instances": spec.count, "timesteps": T,
-                         "fwd_ms": ms, "fwd_adjoint_ms": ms_fa,
+                         "fwd_ms": ms, "fwd_ms_per_step": ms / T,
                          "fwd_ms_per_iteration": ms / max(its * T, 1e-9),
                          "fwd_link_steps_per_s": spec.count * N * T / (ms / 1e3),
-                         "converged_fraction": float((st == 0).mean()),
-                         "iters_per_step": its})
+                         "fwd_adjoint_steps": Ta, "fwd_adjoint_ms": ms_fa,
+                         "iters_per_step": its, "step_outcomes": step_outcomes(out)})
         del batch
         torch.cuda.empty_cache()
-    return {"rows": rows, "dt": 0.1, "stages": 4, "max_iter_per_step": args.max_iter_scaling}
+    return {"rows": rows, "dt": 0.1, "stages": 4, "max_iter_per_step": args.max_iter_scaling,
+            "steps_requested": args.scaling_steps, "budget_s_per_row": args.scaling_budget}
 
 
 def run_ours(args):
@@ -736,8 +921,12 @@ def run_ours(args):
     q_cur0_h = w["q0"].reshape(-1)
     model = P.Model.from_spec(spec, device=local)
     batch = P.Batch([model], max_stages=S, max_history=m)
-    tuned = autotune(P, batch, args, w) if args.threads == 0 else args.threads
+    if args.threads == 0:
+        mapping, tuned, trials = autotune(P, batch, args, w)
+    else:
+        mapping, tuned, trials = args.mapping, args.threads, []
     batch.set_threads(tuned)
+    batch.set_mapping(mapping)
     q_prev0 = torch.tensor(q_prev0_h, device=dev)
     q_cur0 = torch.tensor(q_cur0_h, device=dev)
     T = w["n_steps"]
@@ -747,6 +936,10 @@ def run_ours(args):
                iters=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
                evals=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
                grads=torch.empty(batch.n_instances, dtype=torch.int32, device=dev),
+               step_status=torch.empty((w["n_steps"], batch.n_instances), dtype=torch.int32,
+                                       device=dev),
+               step_rnorm=torch.empty((w["n_steps"], batch.n_instances), dtype=torch.float64,
+                                      device=dev),
                traj_prev=None, traj_cur=None)
 
     def launch():
@@ -851,18 +1044,28 @@ def run_ours(args):
                    "instances_per_gpu": spec.count, "links": spec.n_links, "timesteps": T,
                    "stages": S, "solver": "lbfgs", "history": m, "tol": w["tol"],
                    "max_iter_per_step": w["max_iter"], "parallelism": f"instances sharded, {world} GPU",
-                   "threads_per_block": tuned, "capsule_radius_m": float(spec.radius[0, 0]),
+                   "threads_per_block": tuned,
+                   "mapping": "link (one lane per stage and link)" if mapping == P.MAP_LINK
+                              else "stage (one lane per stage)",
+                   "autotune_ms_2_steps": {f"{'link' if t.mapping else 'stage'}/{t.threads}":
+                                           (t.ms if np.isfinite(t.ms) else None) for t in trials},
+                   "capsule_radius_m": float(spec.radius[0, 0]),
                    "l2": "flushed between timed steps (512 MB write outside the events)"},
         "solver_stats": {"converged_fraction": float((status == 0).mean()),
-                         "status_counts": {P.STATUS[k]: int((status == k).sum()) for k in range(5)},
+                         "worst_status_counts": {P.STATUS[k]: int((status == k).sum())
+                                                 for k in range(6)},
+                         "step_outcomes": step_outcomes(out),
+                         "floor_note": "STALLED = line search failed at |r| <= 1e3 x the binary64 "
+                                       "rounding floor of r (solved to rounding)",
                          "iters_per_step": float(iters.mean() / T),
                          "evals_per_step": float(evals.mean() / T),
                          "gradient_evals_per_step": float(grads.mean() / T)},
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                      "frac": achieved / peak,
-                     "traffic": (ROLLOUT_DRAM_BYTES_PER_EVAL * float(evals.sum())
-                                 if (S, spec.n_links) == (3, 10) and spec.jtype.min() == 1 else None),
-                     "traffic_unit": "bytes per launch (DRAM read + write, scaled from an ncu capture)",
+                     "traffic": rollout_traffic(mapping, S, spec.n_links, float(evals.sum())),
+                     "traffic_unit": "bytes per launch (DRAM read + write per instance-evaluation "
+                                     "from an ncu capture of this kernel build, times the "
+                                     "launch's evaluations; null without a capture of this build)",
                      "peak_source": "measured FP64 FMA probe (pbad_fp64_peak) on this GPU",
                      "flops_per_launch": flops},
         "gpu_launches": args.steps,
@@ -873,8 +1076,12 @@ def run_ours(args):
         plain = measure_plain(P, w, args, dev)
         line["plain"] = plain
         line["batched_vs_plain"] = value / world / plain["value"]
+    if rank == 0 and args.pendulum:
+        line["plain_pendulum"] = measure_pendulum(P, args, dev)
+    if rank == 0 and args.companion_steps > 0:
+        line["companions"] = measure_companions(P, args, dev)
     if rank == 0 and args.throughput_instances > 0:
-        tp = measure_throughput_point(P, args, dev, tuned)
+        tp = measure_throughput_point(P, args, dev, tuned, mapping)
         tp["frac_of_fp64_peak"] = tp["achieved_tflops"] / peak
         line["throughput_point"] = tp
     if rank == 0 and args.adjoint_steps > 0:
@@ -887,6 +1094,7 @@ def run_ours(args):
         line["drag"] = measure_drag(P, args, dev)
     if rank == 0 and args.f32_steps > 0:
         line["mixed_precision"] = measure_mixed_precision(P, args, dev)
+        line["mixed_precision"]["double_float_residual"] = measure_df64(P, args, dev)
     if rank == 0 and args.dt_sweep:
         line["dt_sweep"] = measure_dt_sweep(P, args, dev)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
@@ -898,6 +1106,14 @@ def run_ours(args):
         rate1, _, sample1 = cpu_oracle_rate(w, n_inst=1, n_steps=0,
                                             budget_s=args.cpu_sample_seconds / 3)
         line["cpu_baseline"]["single_core"] = {"value": rate1, "unit": UNIT, "sample": sample1}
+        # the fair CPU baseline: the same L-BFGS with O(N) evaluations
+        # (Algorithm DERIV for the residuals, its tangent for the gradient)
+        rate_f, cores_f, sample_f = cpu_oracle_rate(w, n_inst=min(os.cpu_count() or 1, 16),
+                                                    n_steps=0, budget_s=args.cpu_sample_seconds,
+                                                    fast=True)
+        line["cpu_baseline"]["o_n_evaluation"] = {"value": rate_f, "unit": UNIT, "cores": cores_f,
+                                                  "kind": "oracle L-BFGS, O(N) evaluation",
+                                                  "sample": sample_f}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:

@@ -82,12 +82,24 @@ extern "C" {
  * rounding level. A mixed-precision option, not the default. */
 #define PBAD_LBFGS_F32 2
 
-/* per-instance solver status (the worst over the steps of a rollout) */
+/* Per-step solver status. A rollout's per-instance `status` is the worst over
+ * its steps in the order CONVERGED < STALLED < MAX_ITER < LS_FAIL <
+ * CHOL_FAIL < NONFINITE. */
 #define PBAD_CONVERGED 0  /* |r|_2 < tol */
 #define PBAD_MAX_ITER 1   /* iteration cap reached */
 #define PBAD_LS_FAIL 2    /* line search / damping could not decrease E */
 #define PBAD_CHOL_FAIL 3  /* Newton system not factorable for any damping */
 #define PBAD_NONFINITE 4  /* NaN or Inf in E, r or the gradient */
+/* The line search / damping could not decrease E while |r|_2 was at most
+ * 1e3 times the binary64 rounding floor of r: solved as far as binary64
+ * resolves the step equations (the paper is silent on floors). The floor of
+ * an instance, for S stages and step dt, is
+ *   eps (What sum_l I_l + |g| sum_l (|m c_l| + m_l R_l)),
+ * eps = 2^-52, What = max_i sum_j |W_ij + 2 c V_ij| / dt^2 over the S+2
+ * nodes (acceleration and drag weights), R_l = sum of |t(X_a)| over the
+ * joints a on the root-to-l path (rest translations), I_l = (sqrt(tr
+ * Sigma_l) + sqrt(m_l) R_l)^2 from link l's mass moment. */
+#define PBAD_STALLED 5
 
 #define PBAD_BATCH_NEWTON 1 /* batch flag: reserve the dense Newton/adjoint workspace */
 
@@ -168,8 +180,46 @@ PBAD_API int pbad_batch_info(const pbad_batch* batch, int64_t* n_instances, int6
                     int64_t* workspace_bytes);
 
 /* Threads per block of the solver kernels (32, 64, 96 or 128; default 32):
- * the instance-to-warp mapping knob the autotuner sets. */
+ * one of the instance-to-warp mapping knobs the autotuner sets. */
 PBAD_API int pbad_batch_set_threads(pbad_batch* batch, int32_t threads);
+
+/* Instance-to-lane mappings of the evaluation and L-BFGS kernels (Section
+ * 5.2, Fig. GPU: a group of GPU lanes per trajectory).
+ *   PBAD_MAP_STAGE (default): one lane per collocation stage, S lanes per
+ *     instance, floor(32/S) instances per warp; each lane walks the link tree
+ *     in order (Algorithm DERIV, tree form). Every topology and solver.
+ *   PBAD_MAP_LINK: one lane per stage and link, S N lanes per instance,
+ *     floor(32/(S N)) instances per warp; forward kinematics and the subtree
+ *     sums of Algorithm DERIV become shuffle scans across the links' lanes
+ *     (the work-efficient counterpart of Algorithm DERIVP), and the solver
+ *     state sits in shared memory. For buckets that are serial chains
+ *     (parent[l] = l - 1) with S N <= 32, solved by PBAD_LBFGS (one stage:
+ *     without drag or contact).
+ * Results agree with the stage mapping to rounding (sums taken in another
+ * order). pbad_step_backward and Newton always use one warp per instance.
+ * With PBAD_MAP_LINK set, pbad_eval_objective_grad, pbad_step and
+ * pbad_rollout return PBAD_ERR_UNSUPPORTED (nothing launched) when a
+ * bucket does not qualify. Errors: PBAD_ERR_ARG for a null batch or an
+ * unknown mapping. */
+#define PBAD_MAP_STAGE 0
+#define PBAD_MAP_LINK 1
+PBAD_API int pbad_batch_set_mapping(pbad_batch* batch, int32_t mapping);
+
+/* Arithmetic of the residual pass of pbad_eval_objective_grad (a
+ * mixed-precision experiment; the paper states no precision):
+ *   PBAD_PRECISION_F64 (default): binary64 throughout.
+ *   PBAD_PRECISION_DF64: the joint rotations in binary64, everything after
+ *     them (forward kinematics, seeds of Eq. HOC, wrenches, subtree sums,
+ *     contraction: E and r) in double-float arithmetic, a value being the
+ *     unevaluated sum of two binary32 numbers (about 48 significant bits),
+ *     on the binary32 pipes; the gradient's tangent pass stays binary64.
+ *     Needs PBAD_MAP_LINK (else PBAD_ERR_UNSUPPORTED). The residual's
+ *     rounding floor is about 2^5 times the binary64 one.
+ * Rollouts and steps always evaluate in binary64. Errors: PBAD_ERR_ARG for
+ * a null batch or an unknown precision. */
+#define PBAD_PRECISION_F64 0
+#define PBAD_PRECISION_DF64 1
+PBAD_API int pbad_batch_set_precision(pbad_batch* batch, int32_t precision);
 
 /* Instance queue of pbad_step / pbad_rollout (Section 5.2's dynamic
  * assignment of work to the GPU's cores): when the L-BFGS buckets of a
@@ -213,13 +263,18 @@ PBAD_API int pbad_step(pbad_batch* batch, const double* q_prev, const double* q_
  * the evaluations that also formed dE/dq (L-BFGS: a step's first point,
  * accepted trials and trials the approximate-Wolfe test had to read; a trial
  * rejected on E alone needs none) or Jr (Newton); each of
- * status/iters/evals/grad_evals [instances] may be NULL. */
+ * status/iters/evals/grad_evals [instances] may be NULL. step_status
+ * [n_steps][instances] receives every step's own status and step_rnorm
+ * [n_steps][instances] the |r|_2 of the point the step ended at (the
+ * accepted point it returns); either may be NULL. stages_traj
+ * [n_steps][S*D] (NULL = skip) receives every step's stages, stage-packed
+ * (what pbad_rollout_backward reads). */
 PBAD_API int pbad_rollout(pbad_batch* batch, const double* q_prev0, const double* q_cur0,
                  const double* tau_seq, int32_t n_steps, double dt, int32_t stages,
                  const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
                  double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
                  int32_t* status, int32_t* iters, int32_t* evals, int32_t* grad_evals,
-                 void* stream);
+                 int32_t* step_status, double* step_rnorm, double* stages_traj, void* stream);
 
 /* Implicit-function-theorem adjoint of one converged step (no counterpart
  * in the paper, which has no adjoint; it differentiates the stage equations
@@ -234,6 +289,28 @@ PBAD_API int pbad_step_backward(pbad_batch* batch, const double* q_prev, const d
                                 const double* tau, const double* q_star, const double* g_bar,
                                 double dt, int32_t stages, double* gq_prev, double* gq_cur,
                                 double* gtau, int32_t* status, void* stream);
+
+/* The implicit-function-theorem adjoint of n_steps consecutive steps in one
+ * launch, in reverse (a checkpoint segment of a differentiable rollout; no
+ * counterpart in the paper). stages_traj [n_steps][S*D] holds every step's
+ * converged stages as pbad_rollout writes them from the segment's start
+ * state (q_prev0, q_cur0 [D]); tau_seq [n_steps][D] (NULL = zero). From the
+ * loss gradients a_prev, a_cur [D] of the state after the last step, each
+ * step applies the adjoint of pbad_step_backward with g_bar = a_cur on stage
+ * S-1 (+ a_prev on stage S-2 for S >= 2) and passes on a_prev' = -(dr/
+ * dq_prev)^T mu, a_cur' = -(dr/dq_cur)^T mu (+ a_prev for one stage, whose
+ * next q_prev is q_cur); g_tau [n_steps][D] receives dL/dtau of every step,
+ * a_prev_out / a_cur_out [D] the gradients of the segment's start state.
+ * status [instances] (NULL = skip): PBAD_CONVERGED, or PBAD_CHOL_FAIL when
+ * some step's Jr is singular (that instance's outputs are NaN from there
+ * on). The steps must have converged for the adjoint to hold (the caller's
+ * check). Needs a batch created with PBAD_BATCH_NEWTON. Errors: PBAD_ERR_ARG
+ * for null arrays, n_steps < 1, stages or dt out of range. */
+PBAD_API int pbad_rollout_backward(pbad_batch* batch, const double* q_prev0, const double* q_cur0,
+                                   const double* tau_seq, const double* stages_traj,
+                                   int32_t n_steps, double dt, int32_t stages, const double* a_prev,
+                                   const double* a_cur, double* a_prev_out, double* a_cur_out,
+                                   double* g_tau, int32_t* status, void* stream);
 
 /* World position of one body point per instance and its Jacobian:
  * link[n_models] (host) is the link carrying the point in each model,
@@ -255,15 +332,22 @@ PBAD_API int pbad_link_points(pbad_batch* batch, const double* q, const int32_t*
  * wholly owned by its own allocator, or a latency-bound control loop that
  * cannot afford an allocation's implicit synchronisation.
  *   Arrays as for pbad_eval_objective_grad with D = count * n of the model.
- *   The first call on a device looks up the scratch's device address with
- *   that device current; make that first call before any stream capture.
+ *   Every call looks up the scratch's device address in the current
+ *   context (the model's device is made current for the call), so the
+ *   address stays right after cudaDeviceReset or under another context. The
+ *   first call in a context also loads the library's device code there;
+ *   make that first call before any stream capture.
  *   Every call shares the one scratch array and it keeps the last call's
  *   contents (each evaluation writes every scratch word before reading it,
  *   so nothing needs clearing); calls whose kernels overlap on the GPU race
  *   on it, so serialise them (one stream, or events).
  * Errors: PBAD_ERR_ARG when the model needs more scratch than
  * PBAD_STATIC_SCRATCH_BYTES (the message gives both sizes), or for the
- * argument errors of pbad_eval_objective_grad. */
+ * argument errors of pbad_eval_objective_grad (null arrays, stages outside
+ * 1..PBAD_MAX_STAGES, dt <= 0); PBAD_ERR_UNSUPPORTED for a model with
+ * penalty contact points (Eq. FRI) and stages != 1; PBAD_ERR_CUDA when
+ * selecting the model's device, the scratch address lookup or the launch
+ * fails. */
 PBAD_API int pbad_eval_objective_grad_static(const pbad_model* model, const double* q_star,
                                              const double* q_prev, const double* q_cur,
                                              const double* tau, double dt, int32_t stages,
@@ -272,6 +356,13 @@ PBAD_API int pbad_eval_objective_grad_static(const pbad_model* model, const doub
 /* Measures the device's FP64 FMA throughput (GFLOP/s, FMA = 2 flops) with
  * the library's own probe kernel; synchronises the device. */
 PBAD_API int pbad_fp64_peak(int32_t device, double* gflops);
+
+/* Measures the device's FP64 tensor-core throughput (GFLOP/s) with the
+ * library's own probe: warp-wide mma.sync m8n8k4 with binary64 operands,
+ * eight independent accumulator tiles per warp. It decides whether dense
+ * FP64 products (the Gram matrix Jr^T Jr of the Newton solver, Section 5)
+ * would gain from the tensor cores; synchronises the device. */
+PBAD_API int pbad_fp64_mma_peak(int32_t device, double* gflops);
 
 #ifdef __cplusplus
 }

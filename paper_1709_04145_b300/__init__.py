@@ -16,14 +16,22 @@ from . import inputs
 from ._native import PBADError, check, lib
 
 __all__ = ["Model", "Batch", "colloc", "eval_objective_grad", "step", "rollout", "fp64_peak",
-           "step_backward", "PBADError", "LBFGS", "NEWTON", "LBFGS_F32", "STATUS", "inputs"]
+           "step_backward", "rollout_backward", "PBADError", "LBFGS", "NEWTON", "LBFGS_F32", "MAP_STAGE", "MAP_LINK",
+           "STATUS", "inputs"]
 
 LBFGS = 0
 NEWTON = 1
 # L-BFGS with the two-loop recursion in binary32 (line search and every
 # evaluation binary64): the mixed-precision option
 LBFGS_F32 = 2
-STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE"}
+# instance-to-lane mappings (pbad_batch_set_mapping)
+MAP_STAGE = 0
+MAP_LINK = 1
+# arithmetic of the evaluation's residual pass (pbad_batch_set_precision)
+PRECISION_F64 = 0
+PRECISION_DF64 = 1
+STATUS = {0: "CONVERGED", 1: "MAX_ITER", 2: "LS_FAIL", 3: "CHOL_FAIL", 4: "NONFINITE",
+          5: "STALLED"}
 
 
 def _dptr(a: np.ndarray):
@@ -61,6 +69,13 @@ def fp64_peak(device: int = 0) -> float:
     """Measured FP64 FMA throughput of the device, GFLOP/s."""
     out = C.c_double(0)
     check(lib().pbad_fp64_peak(device, C.byref(out)), "pbad_fp64_peak")
+    return out.value
+
+
+def fp64_mma_peak(device: int = 0) -> float:
+    """Measured FP64 tensor-core (mma.sync m8n8k4) throughput, GFLOP/s."""
+    out = C.c_double(0)
+    check(lib().pbad_fp64_mma_peak(device, C.byref(out)), "pbad_fp64_mma_peak")
     return out.value
 
 
@@ -160,6 +175,19 @@ class Batch:
         check(lib().pbad_batch_set_threads(self._h, int(threads)), "pbad_batch_set_threads")
         self.threads = int(threads)
 
+    def set_mapping(self, mapping: int):
+        """Instance-to-lane mapping of the evaluation and L-BFGS kernels:
+        MAP_STAGE (one lane per stage, the default) or MAP_LINK (one lane
+        per stage and link; serial chains with stages * links <= 32)."""
+        check(lib().pbad_batch_set_mapping(self._h, int(mapping)), "pbad_batch_set_mapping")
+        self.mapping = int(mapping)
+
+    def set_precision(self, precision: int):
+        """Arithmetic of eval_objective_grad's residual pass: PRECISION_F64
+        (default) or PRECISION_DF64 (double-float after the joint rotations;
+        needs MAP_LINK). Rollouts always evaluate in binary64."""
+        check(lib().pbad_batch_set_precision(self._h, int(precision)), "pbad_batch_set_precision")
+
     def set_queue(self, max_blocks: int):
         """Instance queue of the L-BFGS rollouts: at most max_blocks blocks,
         groups take the next instance when done (0 = the GPU's resident
@@ -233,11 +261,14 @@ def step(batch: Batch, q_prev, q_cur, tau, dt: float, stages: int, solver=LBFGS,
 
 def rollout(batch: Batch, q_prev0, q_cur0, tau_seq, n_steps: int, dt: float, stages: int,
             solver=LBFGS, history: int = 8, tol: float = 1e-10, max_iter: int = 1000,
-            want_traj: bool = True, out=None, stream=None):
+            want_traj: bool = True, want_step_log: bool = True, want_stages: bool = False,
+            out=None, stream=None):
     """n_steps steps in one persistent launch. tau_seq: (n_steps*D) or None.
     Returns dict(traj_prev, traj_cur (n_steps, D) or None, q_prev, q_cur,
-    status, iters, evals, grads). ``out`` may supply preallocated output tensors (same keys)
-    so that the call allocates nothing (e.g. inside a CUDA graph)."""
+    status (worst over the steps), iters, evals, grads, step_status, step_rnorm
+    ((n_steps, instances): each step's status and the |r|_2 it ended at, or
+    None)). ``out`` may supply preallocated output tensors (same keys) so that
+    the call allocates nothing (e.g. inside a CUDA graph)."""
     import torch
     dev = q_cur0.device
     if out is None:
@@ -251,6 +282,14 @@ def rollout(batch: Batch, q_prev0, q_cur0, tau_seq, n_steps: int, dt: float, sta
         if want_traj:
             out["traj_prev"] = torch.empty((n_steps, batch.D), dtype=torch.float64, device=dev)
             out["traj_cur"] = torch.empty((n_steps, batch.D), dtype=torch.float64, device=dev)
+        if want_stages:
+            out["stages_traj"] = torch.empty((n_steps, stages * batch.D), dtype=torch.float64,
+                                             device=dev)
+        if want_step_log:
+            out["step_status"] = torch.empty((n_steps, batch.n_instances), dtype=torch.int32,
+                                             device=dev)
+            out["step_rnorm"] = torch.empty((n_steps, batch.n_instances), dtype=torch.float64,
+                                            device=dev)
     sv = _solvers(batch, solver)
     check(lib().pbad_rollout(batch._h, _tptr(q_prev0), _tptr(q_cur0), _tptr(tau_seq),
                              int(n_steps), float(dt), int(stages),
@@ -259,8 +298,28 @@ def rollout(batch: Batch, q_prev0, q_cur0, tau_seq, n_steps: int, dt: float, sta
                              _tptr(out.get("traj_cur")), _tptr(out["q_prev"]),
                              _tptr(out["q_cur"]), _tptr(out["status"]), _tptr(out["iters"]),
                              _tptr(out.get("evals")), _tptr(out.get("grads")),
-                             _stream(stream)), "pbad_rollout")
+                             _tptr(out.get("step_status")), _tptr(out.get("step_rnorm")),
+                             _tptr(out.get("stages_traj")), _stream(stream)), "pbad_rollout")
     return out
+
+
+def rollout_backward(batch: Batch, q_prev0, q_cur0, tau_seq, stages_traj, n_steps: int, dt: float,
+                     stages: int, a_prev, a_cur, stream=None):
+    """Implicit-function adjoint of n_steps consecutive steps in one launch
+    (reverse order): returns (a_prev0, a_cur0, g_tau (n_steps, D), status)
+    for the loss gradients a_prev, a_cur of the state after the last step;
+    stages_traj (n_steps, S*D) as a rollout with want_stages writes it."""
+    import torch
+    dev = q_cur0.device
+    ap = torch.empty(batch.D, dtype=torch.float64, device=dev)
+    ac = torch.empty_like(ap)
+    gt = torch.empty((n_steps, batch.D), dtype=torch.float64, device=dev)
+    st = torch.empty(batch.n_instances, dtype=torch.int32, device=dev)
+    check(lib().pbad_rollout_backward(batch._h, _tptr(q_prev0), _tptr(q_cur0), _tptr(tau_seq),
+                                      _tptr(stages_traj), int(n_steps), float(dt), int(stages),
+                                      _tptr(a_prev), _tptr(a_cur), _tptr(ap), _tptr(ac), _tptr(gt),
+                                      _tptr(st), _stream(stream)), "pbad_rollout_backward")
+    return ap, ac, gt, st
 
 
 def step_backward(batch: Batch, q_prev, q_cur, tau, q_star, g_bar, dt: float, stages: int,

@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpbad.so")
 STAGE_COUNTS = (1, 2, 3, 4, 5)  # pbad_kernels.cu is compiled once per stage count
 SOURCES = ["pbad_kernels.cu", "pbad_capi.cu", "pbad_static.cu"]
-HEADERS = ["pbad_device.cuh", "pbad_kernels.cuh"]
+HEADERS = ["pbad_device.cuh", "pbad_kernels.cuh", "pbad_lp.cuh", "pbad_df64.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

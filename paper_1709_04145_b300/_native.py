@@ -18,7 +18,8 @@ SYMBOLS = ("pbad_version", "pbad_last_error", "pbad_colloc", "pbad_model_create"
            "pbad_batch_info", "pbad_eval_objective_grad", "pbad_step", "pbad_rollout",
            "pbad_fp64_peak", "pbad_eval_objective_grad_static", "pbad_step_backward",
            "pbad_link_points", "pbad_batch_set_threads", "pbad_model_set_drag",
-           "pbad_model_set_contact", "pbad_batch_set_queue")
+           "pbad_model_set_contact", "pbad_batch_set_queue", "pbad_batch_set_mapping",
+           "pbad_fp64_mma_peak", "pbad_batch_set_precision", "pbad_rollout_backward")
 
 
 class PBADError(RuntimeError):
@@ -52,10 +53,15 @@ def lib():
         L.pbad_step.argtypes = [vp, dp, dp, dp, f64, i32, C.POINTER(C.c_int32), i32, f64, i32,
                                 dp, dp, dp, ip, ip, vp]
         L.pbad_rollout.argtypes = [vp, dp, dp, dp, i32, f64, i32, C.POINTER(C.c_int32), i32, f64,
-                                   i32, dp, dp, dp, dp, ip, ip, ip, ip, vp]
+                                   i32, dp, dp, dp, dp, ip, ip, ip, ip, ip, dp, dp, vp]
+        L.pbad_rollout_backward.argtypes = [vp, dp, dp, dp, dp, i32, f64, i32, dp, dp, dp, dp, dp,
+                                            ip, vp]
         L.pbad_fp64_peak.argtypes = [i32, C.POINTER(C.c_double)]
+        L.pbad_fp64_mma_peak.argtypes = [i32, C.POINTER(C.c_double)]
         L.pbad_batch_set_threads.argtypes = [vp, i32]
         L.pbad_batch_set_queue.argtypes = [vp, i32]
+        L.pbad_batch_set_mapping.argtypes = [vp, i32]
+        L.pbad_batch_set_precision.argtypes = [vp, i32]
         L.pbad_model_set_drag.argtypes = [vp, f64]
         L.pbad_model_set_contact.argtypes = [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                              f64, f64, f64]

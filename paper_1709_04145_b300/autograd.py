@@ -1,7 +1,16 @@
 """Differentiable rollouts: a torch.autograd.Function over the CUDA rollout
 whose backward pass applies the implicit-function-theorem adjoint of every
-converged step (pbad_step_backward), recomputing the steps of each segment
-from states checkpointed every ``checkpoint_every`` steps.
+converged step. States are checkpointed every ``checkpoint_every`` steps;
+going back over each segment takes two launches: a rollout that recomputes
+the segment's steps and keeps their stages, and pbad_rollout_backward,
+which walks them in reverse.
+
+The adjoint of a step is the implicit-function theorem at its root, r = 0,
+so it holds only for steps solved to the tolerance (CONVERGED) or to the
+binary64 floor of r (STALLED). An instance with any other step (MAX_ITER,
+LS_FAIL, CHOL_FAIL, NONFINITE), or whose adjoint system is singular, gets
+NaN gradients by default (``on_unsolved="nan"``; ``"zero"`` masks them,
+``"keep"`` applies the adjoint anyway), and ``adjoint_status`` reports it.
 
 State convention: a rollout starts from (q0, qd0); the node before t_0 is
 q_prev0 = q0 + node_prev * dt * qd0 (node_prev < 0 in units of dt), and each
@@ -15,16 +24,25 @@ import ctypes as C
 import numpy as np
 import torch
 
-from . import Batch, LBFGS, NEWTON, colloc, rollout, step, step_backward
+from . import Batch, LBFGS, NEWTON, colloc, rollout, rollout_backward
 from ._native import check, lib
 
+CONVERGED, STALLED = 0, 5
+_RANK = torch.tensor([0, 2, 3, 4, 5, 1], dtype=torch.int32)  # severity of status 0..5
 
-def _scatter_stage(batch: Batch, S: int, stage: int, vec: torch.Tensor, out: torch.Tensor):
-    """out (stage-packed) [:, stage, :] += vec (DOF-packed), model by model."""
-    for k, m in enumerate(batch.models):
-        a, b = int(batch.dof_off[k]), int(batch.dof_off[k + 1])
-        blk = out[S * a:S * b].view(m.count, S, m.n_dof)
-        blk[:, stage, :] += vec[a:b].view(m.count, m.n_dof)
+
+def worse_status(a: torch.Tensor, b: torch.Tensor) -> torch.Tensor:
+    """Element-wise worst of two status tensors in the order CONVERGED <
+    STALLED < MAX_ITER < LS_FAIL < CHOL_FAIL < NONFINITE."""
+    rank = _RANK.to(a.device)
+    return torch.where(rank[b.long()] > rank[a.long()], b, a)
+
+
+def _dof_instance(batch: Batch, dev) -> torch.Tensor:
+    """Instance index of every DOF of the batch's DOF-packed arrays."""
+    idx = [np.repeat(np.arange(int(batch.inst_off[k]), int(batch.inst_off[k + 1])), m.n_dof)
+           for k, m in enumerate(batch.models)]
+    return torch.tensor(np.concatenate(idx), dtype=torch.long, device=dev)
 
 
 class _Rollout(torch.autograd.Function):
@@ -41,9 +59,10 @@ class _Rollout(torch.autograd.Function):
             ckpts.append((s0, s1, q_prev.clone(), q_cur.clone()))
             out = rollout(batch, q_prev, q_cur, tau_seq[s0:s1].contiguous(), s1 - s0, dt, S,
                           cfg["solver"], cfg["history"], cfg["tol"], cfg["max_iter"],
-                          want_traj=False)
-            status = torch.maximum(status, out["status"])
+                          want_traj=False, want_step_log=False)
+            status = worse_status(status, out["status"])
             q_prev, q_cur = out["q_prev"], out["q_cur"]
+        ckpts.append((n_steps, n_steps, q_prev.clone(), q_cur.clone()))  # the end state
         ctx.batch, ctx.cfg, ctx.ckpts = batch, cfg, ckpts
         ctx.save_for_backward(tau_seq)
         ctx.node_prev = float(nodes[0])
@@ -59,39 +78,63 @@ class _Rollout(torch.autograd.Function):
         a_cur = g_cur.clone() if g_cur is not None else torch.zeros(batch.D, dtype=torch.float64, device=dev)
         a_prev = g_prev.clone() if g_prev is not None else torch.zeros_like(a_cur)
         g_tau = torch.zeros_like(tau_seq)
-        for s0, s1, qp0, qc0 in reversed(ctx.ckpts):
-            # recompute the segment step by step, keeping every step's stages
-            states = []
-            qp, qc = qp0, qc0
-            for t in range(s0, s1):
-                out = step(batch, qp, qc, tau_seq[t].contiguous(), dt, S, cfg["solver"],
-                           cfg["history"], cfg["tol"], cfg["max_iter"])
-                states.append((qp, qc, out["q_stages"]))
-                qp, qc = out["q_prev"], out["q_cur"]
-            for t in range(s1 - 1, s0 - 1, -1):
-                qp, qc, qs = states[t - s0]
-                gbar = torch.zeros(S * batch.D, dtype=torch.float64, device=dev)
-                _scatter_stage(batch, S, S - 1, a_cur, gbar)
-                if S >= 2:
-                    _scatter_stage(batch, S, S - 2, a_prev, gbar)
-                gp, gc, gt, st = step_backward(batch, qp, qc, tau_seq[t].contiguous(), qs, gbar, dt, S)
-                if S == 1:  # q_prev' = q_cur passes through
-                    gc = gc + a_prev
-                a_prev, a_cur = gp, gc
-                g_tau[t] = gt
+        # worst over the steps of (the step's own status, the adjoint's status)
+        adj = torch.zeros(batch.n_instances, dtype=torch.int32, device=dev)
+        segs = ctx.ckpts
+        for si in range(len(segs) - 2, -1, -1):
+            s0, s1, qp0, qc0 = segs[si]
+            tau_seg = tau_seq[s0:s1].contiguous()
+            # recompute the segment in one launch, keeping every step's stages
+            out = rollout(batch, qp0, qc0, tau_seg, s1 - s0, dt, S, cfg["solver"], cfg["history"],
+                          cfg["tol"], cfg["max_iter"], want_traj=False, want_step_log=False,
+                          want_stages=True)
+            adj = worse_status(adj, out["status"])
+            # the same launch on the same inputs: the recomputed segment must
+            # end bitwise where the forward pass's did
+            ep, ec = segs[si + 1][2], segs[si + 1][3]
+            if not (torch.equal(out["q_prev"], ep) and torch.equal(out["q_cur"], ec)):
+                raise RuntimeError("rollout recompute diverged from the forward pass "
+                                   f"(steps {s0}..{s1 - 1})")
+            # the adjoint of the segment's steps, in reverse, in one launch
+            a_prev, a_cur, g_seg, st = rollout_backward(batch, qp0, qc0, tau_seg,
+                                                        out["stages_traj"], s1 - s0, dt, S,
+                                                        a_prev.contiguous(), a_cur.contiguous())
+            adj = worse_status(adj, st)
+            g_tau[s0:s1] = g_seg
         g_q0 = a_prev + a_cur
         g_qd0 = ctx.node_prev * dt * a_prev
+        if cfg["adjoint_status"] is not None:
+            cfg["adjoint_status"].copy_(adj)
+        mode = cfg["on_unsolved"]
+        if mode != "keep":
+            bad_inst = (adj != CONVERGED) & (adj != STALLED)
+            if bool(bad_inst.any()):
+                bad = bad_inst[_dof_instance(batch, dev)]
+                fill = float("nan") if mode == "nan" else 0.0
+                g_q0 = g_q0.masked_fill(bad, fill)
+                g_qd0 = g_qd0.masked_fill(bad, fill)
+                g_tau = g_tau.masked_fill(bad[None, :].expand_as(g_tau), fill)
         return g_q0, g_qd0, g_tau, None, None
 
 
 def rollout_differentiable(batch: Batch, q0, qd0, tau_seq, dt: float, stages: int,
                            solver=NEWTON, history: int = 8, tol: float = 1e-10,
-                           max_iter: int = 100, checkpoint_every: int = 8):
+                           max_iter: int = 100, checkpoint_every: int = 8,
+                           on_unsolved: str = "nan", adjoint_status=None):
     """Differentiable rollout of tau_seq.shape[0] steps from (q0, qd0).
-    Returns (q_cur, q_prev, status) after the last step; q_cur and q_prev
-    carry gradients to q0, qd0 and tau_seq."""
+    Returns (q_cur, q_prev, status) after the last step (status: the worst
+    step status per instance); q_cur and q_prev carry gradients to q0, qd0
+    and tau_seq. The implicit-function adjoint is valid at steps that ended
+    CONVERGED or STALLED; the gradients of an instance with any other step,
+    or with a singular adjoint system, are set to NaN (on_unsolved="nan"),
+    to zero ("zero"), or left as computed ("keep"). adjoint_status, an int32
+    CUDA tensor (instances,), receives in the backward pass the worst over
+    the steps of each recomputed step's status and its adjoint's status."""
+    if on_unsolved not in ("nan", "zero", "keep"):
+        raise ValueError("on_unsolved must be 'nan', 'zero' or 'keep'")
     cfg = dict(stages=stages, dt=dt, n_steps=int(tau_seq.shape[0]), solver=solver,
-               history=history, tol=tol, max_iter=max_iter, checkpoint_every=checkpoint_every)
+               history=history, tol=tol, max_iter=max_iter, checkpoint_every=checkpoint_every,
+               on_unsolved=on_unsolved, adjoint_status=adjoint_status)
     return _Rollout.apply(q0, qd0, tau_seq, batch, cfg)
 
 

@@ -10,13 +10,18 @@
 
 #include "../../include/pbad.h"
 #include "pbad_kernels.cuh"
+#include "pbad_lp.cuh"
 
 namespace pbad {
 #define PBAD_DECL(S)                                                                \
   cudaError_t launch_eval_s##S(const LaunchArgs& A, int grid, cudaStream_t s);     \
   cudaError_t launch_rollout_s##S(const LaunchArgs& A, int grid, cudaStream_t s);  \
   int rollout_blocks_per_sm_s##S(const LaunchArgs& A, int threads);
-#define PBAD_DECL_BWD(S) cudaError_t launch_backward_s##S(const LaunchArgs& A, int grid, cudaStream_t s);
+#define PBAD_DECL_BWD(S)                                                                        \
+  cudaError_t launch_backward_s##S(const LaunchArgs& A, int grid, cudaStream_t s);             \
+  cudaError_t launch_segment_backward_s##S(const LaunchArgs& A, int grid, cudaStream_t s);     \
+  cudaError_t launch_eval_lp_s##S(const LaunchArgs& A, int grid, size_t smem, cudaStream_t s); \
+  cudaError_t launch_rollout_lp_s##S(const LaunchArgs& A, int grid, size_t smem, cudaStream_t s);
 PBAD_DECL_BWD(1)
 PBAD_DECL_BWD(2)
 PBAD_DECL_BWD(3)
@@ -28,6 +33,7 @@ PBAD_DECL(3)
 PBAD_DECL(4)
 PBAD_DECL(5)
 cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters);
+cudaError_t launch_dmma_peak(double* out, int blocks, int threads, int iters);
 cudaError_t launch_link_points(const LaunchArgs& A, int grid, cudaStream_t s);
 
 cudaError_t launch_eval(int S, const LaunchArgs& A, int grid, cudaStream_t s) {
@@ -47,6 +53,36 @@ cudaError_t launch_backward(int S, const LaunchArgs& A, int grid, cudaStream_t s
     case 3: return launch_backward_s3(A, grid, s);
     case 4: return launch_backward_s4(A, grid, s);
     case 5: return launch_backward_s5(A, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_segment_backward(int S, const LaunchArgs& A, int grid, cudaStream_t s) {
+  switch (S) {
+    case 1: return launch_segment_backward_s1(A, grid, s);
+    case 2: return launch_segment_backward_s2(A, grid, s);
+    case 3: return launch_segment_backward_s3(A, grid, s);
+    case 4: return launch_segment_backward_s4(A, grid, s);
+    case 5: return launch_segment_backward_s5(A, grid, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_eval_lp(int S, const LaunchArgs& A, int grid, size_t smem, cudaStream_t s) {
+  switch (S) {
+    case 1: return launch_eval_lp_s1(A, grid, smem, s);
+    case 2: return launch_eval_lp_s2(A, grid, smem, s);
+    case 3: return launch_eval_lp_s3(A, grid, smem, s);
+    case 4: return launch_eval_lp_s4(A, grid, smem, s);
+    case 5: return launch_eval_lp_s5(A, grid, smem, s);
+  }
+  return cudaErrorInvalidValue;
+}
+cudaError_t launch_rollout_lp(int S, const LaunchArgs& A, int grid, size_t smem, cudaStream_t s) {
+  switch (S) {
+    case 1: return launch_rollout_lp_s1(A, grid, smem, s);
+    case 2: return launch_rollout_lp_s2(A, grid, smem, s);
+    case 3: return launch_rollout_lp_s3(A, grid, smem, s);
+    case 4: return launch_rollout_lp_s4(A, grid, smem, s);
+    case 5: return launch_rollout_lp_s5(A, grid, smem, s);
   }
   return cudaErrorInvalidValue;
 }
@@ -116,6 +152,8 @@ struct pbad_batch {
   // many blocks, < 0 (the default) turns the queue off
   int* d_queue = nullptr;
   int queue_blocks = -1;
+  int mapping = PBAD_MAP_STAGE;  // instance-to-lane mapping of the L-BFGS and eval kernels
+  int precision = PBAD_PRECISION_F64;  // arithmetic of pbad_eval_objective_grad's residual pass
 };
 
 namespace {
@@ -421,6 +459,38 @@ bool apply_queue(pbad_batch* bt, int S, LaunchArgs* A, int* grid) {
   return true;
 }
 
+// Link-parallel launch over every bucket (PBAD_MAP_LINK): each bucket must
+// be a serial chain with S N <= 32 lanes per instance, solved by binary64
+// L-BFGS (solvers may be null for an evaluation), and for one stage carry no
+// drag or contact. On success *smem is the dynamic shared memory per block.
+int fill_launch_lp(pbad_batch* bt, int S, double dt, const int32_t* solvers, int history,
+                   LaunchArgs* A, int* grid, size_t* smem) {
+  int rc = fill_launch(bt, S, dt, solvers, history, A, grid);
+  if (rc != PBAD_OK) return rc;
+  const int wpb = bt->threads / 32;
+  int blocks = 0;
+  for (int k = 0; k < A->nb; ++k) {
+    const pbad_model* m = bt->models[k];
+    if (!m->chain) return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: the model is not a serial chain");
+    if (S * m->N > 32)
+      return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: stages x links exceeds the 32 lanes of a warp");
+    if (solvers && solvers[k] != PBAD_LBFGS)
+      return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: binary64 L-BFGS only");
+    if (S == 1 && (m->drag != 0.0 || m->n_contact > 0))
+      return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: no one-stage drag or contact");
+    const int per_warp = 32 / (S * m->N);
+    const int64_t warps = (m->count + per_warp - 1) / per_warp;
+    A->bk[k].block_begin = blocks;
+    A->bk[k].queue = nullptr;
+    blocks += (int)((warps + wpb - 1) / wpb);
+  }
+  LpLayout L;
+  L.make(history);
+  *smem = (size_t)wpb * 32 * L.total * sizeof(double);
+  *grid = blocks;
+  return PBAD_OK;
+}
+
 int check_common(pbad_batch* bt, int32_t stages, double dt) {
   if (!bt) return fail(PBAD_ERR_ARG, "null batch");
   if (stages < 1 || stages > bt->max_stages)
@@ -434,7 +504,8 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
                  const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
                  double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
                  double* q_stages_out, int32_t* status, int32_t* iters, int32_t* evals,
-                 int32_t* grads, void* stream) {
+                 int32_t* grads, int32_t* step_status, double* step_rnorm, double* stages_traj,
+                 void* stream) {
   int rc = check_common(bt, stages, dt);
   if (rc != PBAD_OK) return rc;
   if (!q_prev0 || !q_cur0) return fail(PBAD_ERR_ARG, "null state");
@@ -453,7 +524,15 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   DeviceGuard dg(bt->device);
   LaunchArgs A;
   int grid = 0;
-  rc = fill_launch(bt, stages, dt, solvers, history, &A, &grid);
+  size_t smem = 0;
+  const bool lp = bt->mapping == PBAD_MAP_LINK;
+  if (lp) {
+    std::vector<int32_t> sv(bt->models.size(), PBAD_LBFGS);
+    if (solvers) sv.assign(solvers, solvers + bt->models.size());
+    rc = fill_launch_lp(bt, stages, dt, sv.data(), history, &A, &grid, &smem);
+  } else {
+    rc = fill_launch(bt, stages, dt, solvers, history, &A, &grid);
+  }
   if (rc != PBAD_OK) return rc;
   A.q_prev0 = q_prev0;
   A.q_cur0 = q_cur0;
@@ -466,11 +545,20 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   A.q_prev_out = q_prev_out;
   A.q_cur_out = q_cur_out;
   A.q_stages_out = q_stages_out;
+  A.stages_traj = stages_traj;
   A.status = status;
+  A.step_status = step_status;
+  A.step_rnorm = step_rnorm;
+  A.n_inst = bt->n_inst;
   A.iters = iters;
   A.evals = evals;
   A.grads = grads;
   cudaStream_t s = (cudaStream_t)stream;
+  if (lp) {
+    const cudaError_t e = launch_rollout_lp(stages, A, grid, smem, s);
+    if (e != cudaSuccess) return cuda_fail(e, "link-parallel rollout launch");
+    return PBAD_OK;
+  }
   if (apply_queue(bt, stages, &A, &grid)) {
     const cudaError_t e = cudaMemsetAsync(bt->d_queue, 0, sizeof(int) * kMaxBuckets, s);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
@@ -484,7 +572,7 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
 
 extern "C" {
 
-int pbad_version(void) { return 100; }
+int pbad_version(void) { return 200; }
 
 const char* pbad_last_error(void) { return g_err.c_str(); }
 
@@ -787,8 +875,14 @@ int pbad_eval_objective_grad(pbad_batch* bt, const double* q_star, const double*
   DeviceGuard dg(bt->device);
   LaunchArgs A;
   int grid = 0;
-  rc = fill_launch(bt, stages, dt, nullptr, 0, &A, &grid);
+  size_t smem = 0;
+  const bool lp = bt->mapping == PBAD_MAP_LINK;
+  if (bt->precision == PBAD_PRECISION_DF64 && !lp)
+    return fail(PBAD_ERR_UNSUPPORTED, "the double-float residual pass runs in the link-parallel mapping");
+  if (lp) rc = fill_launch_lp(bt, stages, dt, nullptr, 0, &A, &grid, &smem);
+  else rc = fill_launch(bt, stages, dt, nullptr, 0, &A, &grid);
   if (rc != PBAD_OK) return rc;
+  A.df64 = bt->precision == PBAD_PRECISION_DF64;
   A.q_prev0 = q_prev;
   A.q_cur0 = q_cur;
   A.tau = tau;
@@ -798,7 +892,7 @@ int pbad_eval_objective_grad(pbad_batch* bt, const double* q_star, const double*
   A.resid_out = resid;
   A.n_steps = 1;
   cudaStream_t s = (cudaStream_t)stream;
-  const cudaError_t e = launch_eval(stages, A, grid, s);
+  const cudaError_t e = lp ? launch_eval_lp(stages, A, grid, smem, s) : launch_eval(stages, A, grid, s);
   if (e != cudaSuccess) return cuda_fail(e, "eval launch");
   return PBAD_OK;
 }
@@ -808,10 +902,10 @@ int pbad_rollout(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
                  const int32_t* solvers, int32_t history, double tol, int32_t max_iter,
                  double* traj_prev, double* traj_cur, double* q_prev_out, double* q_cur_out,
                  int32_t* status, int32_t* iters, int32_t* evals, int32_t* grad_evals,
-                 void* stream) {
+                 int32_t* step_status, double* step_rnorm, double* stages_traj, void* stream) {
   return rollout_impl(bt, q_prev0, q_cur0, tau_seq, n_steps, dt, stages, solvers, history, tol,
                       max_iter, traj_prev, traj_cur, q_prev_out, q_cur_out, nullptr, status, iters,
-                      evals, grad_evals, stream);
+                      evals, grad_evals, step_status, step_rnorm, stages_traj, stream);
 }
 
 int pbad_step(pbad_batch* bt, const double* q_prev, const double* q_cur, const double* tau,
@@ -820,7 +914,7 @@ int pbad_step(pbad_batch* bt, const double* q_prev, const double* q_cur, const d
               int32_t* status, int32_t* iters, void* stream) {
   return rollout_impl(bt, q_prev, q_cur, tau, 1, dt, stages, solvers, history, tol, max_iter,
                       nullptr, nullptr, q_prev_out, q_cur_out, q_stages_out, status, iters,
-                      nullptr, nullptr, stream);
+                      nullptr, nullptr, nullptr, nullptr, nullptr, stream);
 }
 
 int pbad_step_backward(pbad_batch* bt, const double* q_prev, const double* q_cur,
@@ -853,6 +947,39 @@ int pbad_step_backward(pbad_batch* bt, const double* q_prev, const double* q_cur
   return PBAD_OK;
 }
 
+int pbad_rollout_backward(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
+                          const double* tau_seq, const double* stages_traj, int32_t n_steps,
+                          double dt, int32_t stages, const double* a_prev, const double* a_cur,
+                          double* a_prev_out, double* a_cur_out, double* g_tau, int32_t* status,
+                          void* stream) {
+  int rc = check_common(bt, stages, dt);
+  if (rc != PBAD_OK) return rc;
+  if (!q_prev0 || !q_cur0 || !stages_traj || !a_prev || !a_cur || !a_prev_out || !a_cur_out || !g_tau)
+    return fail(PBAD_ERR_ARG, "null array");
+  if (n_steps < 1) return fail(PBAD_ERR_ARG, "n_steps must be positive");
+  if (!(bt->flags & PBAD_BATCH_NEWTON))
+    return fail(PBAD_ERR_ARG, "the adjoint needs a batch created with PBAD_BATCH_NEWTON");
+  DeviceGuard dg(bt->device);
+  LaunchArgs A;
+  int grid = 0;
+  rc = fill_launch(bt, stages, dt, nullptr, 0, &A, &grid, true);
+  if (rc != PBAD_OK) return rc;
+  A.q_prev0 = q_prev0;
+  A.q_cur0 = q_cur0;
+  A.tau = tau_seq;
+  A.stages_traj = const_cast<double*>(stages_traj);
+  A.g_bar = a_prev;
+  A.a_cur_in = a_cur;
+  A.gq_prev = a_prev_out;
+  A.gq_cur = a_cur_out;
+  A.gtau = g_tau;
+  A.status = status;
+  A.n_steps = n_steps;
+  const cudaError_t e = launch_segment_backward(stages, A, grid, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "segment backward launch");
+  return PBAD_OK;
+}
+
 int pbad_link_points(pbad_batch* bt, const double* q, const int32_t* link,
                      const double* point_local, double* pos, double* jac, void* stream) {
   if (!bt) return fail(PBAD_ERR_ARG, "null batch");
@@ -872,6 +999,21 @@ int pbad_link_points(pbad_batch* bt, const double* q, const int32_t* link,
   for (size_t k = 0; k < bt->models.size(); ++k) A.point_link[k] = link[k];  // in the parameter block
   const cudaError_t e = launch_link_points(A, grid, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "points launch");
+  return PBAD_OK;
+}
+
+int pbad_batch_set_mapping(pbad_batch* bt, int32_t mapping) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (mapping != PBAD_MAP_STAGE && mapping != PBAD_MAP_LINK) return fail(PBAD_ERR_ARG, "unknown mapping");
+  bt->mapping = mapping;
+  return PBAD_OK;
+}
+
+int pbad_batch_set_precision(pbad_batch* bt, int32_t precision) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (precision != PBAD_PRECISION_F64 && precision != PBAD_PRECISION_DF64)
+    return fail(PBAD_ERR_ARG, "unknown precision");
+  bt->precision = precision;
   return PBAD_OK;
 }
 
@@ -913,6 +1055,41 @@ int pbad_fp64_peak(int32_t device, double* gflops) {
   cudaFree(d);
   if (e != cudaSuccess) return cuda_fail(e, "probe");
   *gflops = 2.0 * 8.0 * iters * (double)threads * blocks / (best * 1e-3) / 1e9;
+  return PBAD_OK;
+}
+
+int pbad_fp64_mma_peak(int32_t device, double* gflops) {
+  if (!gflops) return fail(PBAD_ERR_ARG, "null output");
+  DeviceGuard dg(device);
+  if (!dg.ok) return fail(PBAD_ERR_CUDA, "cudaSetDevice failed");
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return cuda_fail(e, "attribute");
+  const int threads = 256, blocks = sms * 4, iters = 4000;
+  double* d = nullptr;
+  if ((e = cudaMalloc(&d, sizeof(double) * threads * blocks)) != cudaSuccess)
+    return fail(PBAD_ERR_ALLOC, "probe buffer");
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0);
+    launch_dmma_peak(d, blocks, threads, iters);
+    cudaEventRecord(e1);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (rep > 0 && ms < best) best = ms;
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFree(d);
+  if (e != cudaSuccess) return cuda_fail(e, "probe");
+  // per warp and iteration: 8 mma of 8 x 8 x 4 FMA (2 flops each)
+  const double warps = (double)threads / 32 * blocks;
+  *gflops = 2.0 * 256.0 * 8.0 * iters * warps / (best * 1e-3) / 1e9;
   return PBAD_OK;
 }
 

@@ -8,11 +8,9 @@
 
 namespace pbad {
 
-__device__ __forceinline__ int find_bucket(const LaunchArgs& A) {
-  int bk = 0;
-  while (bk + 1 < A.nb && (int)blockIdx.x >= A.bk[bk + 1].block_begin) ++bk;
-  return bk;
-}
+}  // namespace pbad
+#include "pbad_lp.cuh"
+namespace pbad {
 
 // Lane identity inside a bucket: groups of S lanes, floor(32/S) groups per warp.
 template <int S>
@@ -94,6 +92,8 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
   int step = 0, phase = kFirst, k = 0, trials = 0, nh = 0, head = 0, step_evals = 0;
   int worst = kConverged, iters_total = 0, evals_total = 0, grads_total = 0;
   double E = 0.0, alpha = 1.0, gd = 0.0, gamma = 1.0;
+  double rn_x = 0.0;  // |r|_2 at the current (last accepted) point
+  double rstall = kStallFactor * c.rnorm_floor();
   const int max_evals = 4 * A.max_iter + kLsMax;  // evaluations per step
   c.setup(true);
   if (!active) phase = kDone;
@@ -121,6 +121,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     if (nb >= B.count) return false;
     b = nb;
     c.b = nb;
+    rstall = kStallFactor * c.rnorm_floor();
     for (int d = 0; d < n; ++d) {
       ws[L.qp + d] = A.q_prev0[gdof(d)];
       ws[L.qc + d] = A.q_cur0[gdof(d)];
@@ -188,7 +189,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     int fin_st = -1;  // status of a step that ends on this trip
     if (trial && !ok) {
       if (step_evals >= max_evals) fin_st = kMaxIter;
-      else if (++trials >= kLsMax) fin_st = kLsFail;
+      else if (++trials >= kLsMax) fin_st = rn_x <= rstall ? kStalled : kLsFail;
       else alpha *= 0.5;
     }
     const bool back = trial && !ok && fin_st < 0;  // next trial along the same d
@@ -295,6 +296,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     bool start = false;
     if (acc) {
       E = Et;
+      rn_x = sqrt(rr);
       if (first) {
         k = 0;
         nh = 0;
@@ -316,8 +318,13 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
     const bool fin = fin_st >= 0;
     if (__any_sync(kAll, fin)) {
       if (fin) {
-        worst = max(worst, fin_st);
+        worst = status_worse(worst, fin_st);
         step_evals = 0;
+        if (cv.i == 0) {
+          const int64_t o = (int64_t)step * A.n_inst + B.inst_off + b;
+          if (A.step_status) A.step_status[o] = fin_st;
+          if (A.step_rnorm) A.step_rnorm[o] = rn_x;
+        }
       }
       for (int d = 0; d < n; ++d) {
         const double xv = ws[L.x + d];
@@ -331,6 +338,7 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
             if (A.traj_prev) A.traj_prev[(int64_t)step * D + gdof(d)] = xp;
           }
           if (A.q_stages_out && step == A.n_steps - 1) A.q_stages_out[gstage(d)] = xv;
+          if (A.stages_traj) A.stages_traj[(int64_t)step * S * D + gstage(d)] = xv;
         }
       }
       bool next = false;
@@ -424,14 +432,17 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
 // Persistent Newton (Levenberg-Marquardt) rollout, Section 5:
 //   q <- q - [H + lambda I]^-1 g,  H = Jr^T Jr, g = Jr^T r   (S >= 2)
 //                                  H = int dP/dq^T dP/dq / dt^2, g = dE/dq (S == 1)
-// lambda starts at 1e-12 max diag(H) per step, x0.1 (floor 1e-20 max diag)
-// after an accepted step, x10 after a rejected step or a failed Cholesky
-// factorisation; a step is accepted when E decreases. One warp per instance:
+// lambda starts at 1e-12 max diag(H) per step; a damped step that does not
+// lower E is halved up to three times before lambda grows x10 (a failed
+// Cholesky factorisation grows it at once); lambda shrinks x0.1 (floor 1e-20
+// max diag) after a full damped step is accepted and stays after a halved
+// one; a step is accepted when E decreases. One warp per instance:
 // R = 32/S replicas of the stage group evaluate the same point and split the
 // S n Jacobian columns; the Gram matrix, Cholesky and solves are shared by
 // the warp's lanes (the paper's workgroup per trajectory, Fig. GPU).
 // ------------------------------------------------------------------------
 constexpr int kLmMaxTrials = 60;
+constexpr int kLmHalvings = 3;  // halvings of a damped step before lambda grows
 
 // Lane identity of the warp-per-instance mapping.
 template <int S>
@@ -469,9 +480,11 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     ws[L.qp + d] = A.q_prev0[c.gdof(d)];
     ws[L.qc + d] = A.q_cur0[c.gdof(d)];
   }
-  int step = 0, phase = kFirst, k = 0, trials = 0;
+  int step = 0, phase = kFirst, k = 0, trials = 0, halvings = 0;
   int worst = kConverged, iters_total = 0, evals_total = 0, grads_total = 0;
-  double E = 0.0, lambda = -1.0, hmax = 0.0;
+  double E = 0.0, lambda = -1.0, hmax = 0.0, alpha = 1.0;
+  double rn_x = 0.0;  // |r|_2 at the current (last accepted) point
+  const double rstall = kStallFactor * c.rnorm_floor();
   c.setup(true);
   if (!active) phase = kDone;  // warp-uniform
 
@@ -483,7 +496,12 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
   };
 
   auto finish = [&](int st) {
-    worst = max(worst, st);
+    worst = status_worse(worst, st);
+    if (writer && c.i == 0) {
+      const int64_t o = (int64_t)step * A.n_inst + B.inst_off + b;
+      if (A.step_status) A.step_status[o] = st;
+      if (A.step_rnorm) A.step_rnorm[o] = rn_x;
+    }
     for (int d = 0; d < n; ++d) {
       const double xs = c.grp.from_full(ws[L.x + d], S - 1);
       const double xp = (S == 1) ? ws[L.qc + d] : c.grp.from_full(ws[L.x + d], S - 2);
@@ -496,6 +514,8 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     }
     if (writer && A.q_stages_out && step == A.n_steps - 1)
       for (int d = 0; d < n; ++d) A.q_stages_out[c.gstage(d)] = ws[L.x + d];
+    if (writer && A.stages_traj)
+      for (int d = 0; d < n; ++d) A.stages_traj[(int64_t)step * S * D + c.gstage(d)] = ws[L.x + d];
     ++step;
     if (step >= A.n_steps) {
       phase = kDone;
@@ -525,6 +545,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
       }
       E = Et;
       rr = rrt;
+      rn_x = sqrt(rr);
       k = 0;
       lambda = -1.0;
       need = 1;
@@ -541,13 +562,20 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
         }
         E = Et;
         rr = rrt;
-        lambda = fmax(lambda * 0.1, 1e-20 * hmax);
+        rn_x = sqrt(rr);
+        if (alpha == 1.0) lambda = fmax(lambda * 0.1, 1e-20 * hmax);
         ++k;
         ++iters_total;
         need = 1;
+      } else if (halvings < kLmHalvings) {
+        // half of the damped step before a larger lambda
+        ++halvings;
+        alpha *= 0.5;
+        for (int d = 0; d < n; ++d) ws[L.xt + d] = fma(alpha, Dn[DL.dl + c.i * n + d], ws[L.x + d]);
+        __syncwarp();
       } else {
         lambda *= 10.0;
-        if (++trials >= kLmMaxTrials) finish(kLsFail);
+        if (++trials >= kLmMaxTrials) finish(rn_x <= rstall ? kStalled : kLsFail);
         else need = 2;
       }
     }
@@ -581,6 +609,8 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
         finish(kCholFail);
       } else {
         for (int d = 0; d < n; ++d) ws[L.xt + d] = ws[L.x + d] + Dn[DL.dl + c.i * n + d];
+        alpha = 1.0;
+        halvings = 0;
         phase = kTrial;
       }
       __syncwarp();
@@ -673,6 +703,99 @@ __global__ void __launch_bounds__(128) k_step_backward(const __grid_constant__ L
 }
 
 // ------------------------------------------------------------------------
+// The same adjoint over n_steps consecutive steps of a rollout in one launch
+// (a checkpoint segment of a differentiable rollout): from the loss
+// gradients a_prev, a_cur of the state after the last step, the steps are
+// taken in reverse; step t's stages come from stages_traj[t] (written by the
+// recomputing rollout), the state before it from the stages of step t - 1
+// (the segment's start state for its first step). Per step:
+//   g_bar = a_cur on stage S-1 (+ a_prev on stage S-2 for S >= 2),
+//   Jr^T mu = g_bar, a_prev' = -(dr/dq_prev)^T mu,
+//   a_cur' = -(dr/dq_cur)^T mu (+ a_prev for one stage, whose q_prev' = q_cur),
+//   dL/dtau_t = sum_i mu_i.
+// a_prev and a_cur live in the lane workspace's g and d slices.
+// ------------------------------------------------------------------------
+template <int S>
+__global__ void __launch_bounds__(128) k_segment_backward(const __grid_constant__ LaunchArgs A) {
+  const Bucket& B = A.bk[find_bucket(A)];
+  const WarpId<S> id(B);
+  const bool active = id.inst < B.count;
+  if (!active) return;  // warp-uniform
+  const int b = (int)id.inst;
+  Ctx<S> c(B, A.K, b, id.lane_id, 0, A.dense_stages);
+  const int n = c.n;
+  const auto& L = c.L;
+  const Lane& ws = c.ws;
+  const bool writer = id.rep == 0;
+  const int64_t D = A.D;
+  double* Dn = B.dense + (int64_t)b * B.dense_stride;
+  DenseLayout DL;
+  DL.make(S * n);
+  // stage j of step t (stage-packed), instance b
+  auto stage_of = [&](int t, int j, int d) {
+    return A.stages_traj[(int64_t)t * S * D + (int64_t)S * B.dof_off + ((int64_t)b * S + j) * n + d];
+  };
+  for (int d = 0; d < n; ++d) {
+    ws[L.g + d] = A.g_bar[c.gdof(d)];     // a_prev (dL/dq_prev after the last step)
+    ws[L.d + d] = A.a_cur_in[c.gdof(d)];  // a_cur
+  }
+  int worst = kConverged;
+  for (int t = A.n_steps - 1; t >= 0; --t) {
+    for (int d = 0; d < n; ++d) {
+      double qp, qc;
+      if (t == 0) {
+        qp = A.q_prev0[c.gdof(d)];
+        qc = A.q_cur0[c.gdof(d)];
+      } else if (S == 1) {
+        qp = t == 1 ? A.q_cur0[c.gdof(d)] : stage_of(t - 2, 0, d);
+        qc = stage_of(t - 1, 0, d);
+      } else {
+        qp = stage_of(t - 1, S - 2, d);
+        qc = stage_of(t - 1, S - 1, d);
+      }
+      ws[L.qp + d] = qp;
+      ws[L.qc + d] = qc;
+    }
+    c.setup(true);
+    for (int d = 0; d < n; ++d) ws[L.xt + d] = stage_of(t, c.i, d);
+    if (writer)
+      for (int d = 0; d < n; ++d) {
+        double gb = c.i == S - 1 ? ws[L.d + d] : 0.0;
+        if (S >= 2 && c.i == S - 2) gb += ws[L.g + d];
+        Dn[DL.gb + c.i * n + d] = gb;
+      }
+    const double* tau = A.tau ? A.tau + (int64_t)t * D : nullptr;
+    c.primal(tau);
+    __syncwarp();
+    c.build_jacobian_warp(Dn, DL, id.rep, id.R, true);
+    const bool ok = c.lu_solve_transposed_warp(Dn, DL);
+    __syncwarp();
+    for (int d = 0; d < n; ++d) ws[L.x + d] = Dn[DL.dl + c.i * n + d];
+    c.transform_tangents(L.x);
+    c.known_node_vjp(0, L.qp, L.r);
+    c.known_node_vjp(1, L.qc, L.rt);
+    if (!ok) worst = status_worse(worst, kCholFail);
+    for (int d = 0; d < n; ++d) {
+      double gt = 0.0;
+      for (int j = 0; j < S; ++j) gt += Dn[DL.dl + j * n + d];
+      const double ap = ok ? -ws[L.r + d] : NAN;
+      const double ac = ok ? -ws[L.rt + d] + (S == 1 ? ws[L.g + d] : 0.0) : NAN;
+      ws[L.g + d] = ap;
+      ws[L.d + d] = ac;
+      if (writer && c.i == 0) A.gtau[(int64_t)t * D + c.gdof(d)] = ok ? gt : NAN;
+    }
+    __syncwarp();
+  }
+  if (writer && c.i == 0) {
+    for (int d = 0; d < n; ++d) {
+      A.gq_prev[c.gdof(d)] = ws[L.g + d];
+      A.gq_cur[c.gdof(d)] = ws[L.d + d];
+    }
+    if (A.status) A.status[B.inst_off + b] = worst;
+  }
+}
+
+// ------------------------------------------------------------------------
 // World position of one body point per instance and its Jacobian dp/dq
 // (column d: w_d x (p - o_d) for the joints on the root-to-link path), from
 // the forward kinematics of Section 5. One lane per instance.
@@ -748,6 +871,36 @@ __global__ void k_fp64_peak(double* out, int iters, double a, double b) {
 }
 #endif
 
+// ------------------------------------------------------------------------
+// FP64 tensor-core (DMMA) throughput probe: mma.sync m8n8k4 with binary64
+// operands and accumulators, 8 independent accumulator tiles per warp, so
+// that the decision whether to assemble the Newton Gram matrix Jr^T Jr on
+// the tensor cores rests on a measured rate. One mma = 8*8*4 FMA per warp.
+// ------------------------------------------------------------------------
+#if PBAD_S == 1
+__global__ void k_dmma_peak(double* out, int iters, double a0, double b0) {
+  const int lane = threadIdx.x & 31;
+  double a = a0 + 1e-3 * lane, b = b0 - 1e-3 * lane;
+  double c[8][2];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    c[k][0] = 1e-3 * k;
+    c[k][1] = -1e-3 * k;
+  }
+  for (int it = 0; it < iters; ++it) {
+#pragma unroll
+    for (int k = 0; k < 8; ++k)
+      asm volatile("mma.sync.aligned.m8n8k4.row.col.f64.f64.f64.f64 {%0, %1}, {%2}, {%3}, {%0, %1};"
+                   : "+d"(c[k][0]), "+d"(c[k][1])
+                   : "d"(a), "d"(b));
+  }
+  double s = 0.0;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s += c[k][0] + c[k][1];
+  out[(int64_t)blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+#endif
+
 // Host-side launchers for the stage count this translation unit is built for
 // (PBAD_S): the library compiles this file once per stage count.
 #define PBAD_CAT2(a, b) a##b
@@ -758,6 +911,10 @@ cudaError_t PBAD_CAT(launch_eval_s, PBAD_S)(const LaunchArgs& A, int grid, cudaS
 }
 cudaError_t PBAD_CAT(launch_backward_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
   k_step_backward<PBAD_S><<<grid, A.threads, 0, s>>>(A);
+  return cudaGetLastError();
+}
+cudaError_t PBAD_CAT(launch_segment_backward_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
+  k_segment_backward<PBAD_S><<<grid, A.threads, 0, s>>>(A);
   return cudaGetLastError();
 }
 cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cudaStream_t s) {
@@ -775,6 +932,28 @@ cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cu
   } else {
     k_rollout<PBAD_S, 2><<<grid, A.threads, 0, s>>>(A);
   }
+  return cudaGetLastError();
+}
+// Link-parallel launches (every bucket a serial chain with S N <= 32): the
+// dynamic shared memory is smem bytes per block.
+cudaError_t PBAD_CAT(launch_eval_lp_s, PBAD_S)(const LaunchArgs& A, int grid, size_t smem,
+                                              cudaStream_t s) {
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_eval_lp<PBAD_S>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_eval_lp<PBAD_S><<<grid, A.threads, smem, s>>>(A);
+  return cudaGetLastError();
+}
+cudaError_t PBAD_CAT(launch_rollout_lp_s, PBAD_S)(const LaunchArgs& A, int grid, size_t smem,
+                                                 cudaStream_t s) {
+  if (smem > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(k_rollout_lp<PBAD_S>,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  k_rollout_lp<PBAD_S><<<grid, A.threads, smem, s>>>(A);
   return cudaGetLastError();
 }
 // Blocks of the queue variant of the rollout kernel for these buckets (all
@@ -797,6 +976,10 @@ cudaError_t launch_link_points(const LaunchArgs& A, int grid, cudaStream_t s) {
 }
 cudaError_t launch_fp64_peak(double* out, int blocks, int threads, int iters) {
   k_fp64_peak<<<blocks, threads>>>(out, iters, 0.999999, 1e-7);
+  return cudaGetLastError();
+}
+cudaError_t launch_dmma_peak(double* out, int blocks, int threads, int iters) {
+  k_dmma_peak<<<blocks, threads>>>(out, iters, 0.5, 1e-9);
   return cudaGetLastError();
 }
 #endif

@@ -22,7 +22,21 @@ constexpr int kLsMax = 40;         // backtracking trials
 constexpr double kCurvEps = 1e-14; // curvature-pair acceptance
 
 enum Phase { kFirst = 1, kTrial = 2, kDone = 3 };
-enum Status { kConverged = 0, kMaxIter = 1, kLsFail = 2, kCholFail = 3, kNonFinite = 4 };
+enum Status { kConverged = 0, kMaxIter = 1, kLsFail = 2, kCholFail = 3, kNonFinite = 4,
+              kStalled = 5 };
+// A step whose line search (or LM damping) cannot lower E while |r|_2 is at
+// most kStallFactor times the rounding floor (Ctx::rnorm_floor) ends
+// kStalled: solved as far as binary64 resolves r.
+constexpr double kStallFactor = 1e3;
+
+// Worst of two statuses in the order CONVERGED < STALLED < MAX_ITER <
+// LS_FAIL < CHOL_FAIL < NONFINITE.
+__host__ __device__ __forceinline__ int status_rank(int st) {
+  return st == kStalled ? 1 : (st == kConverged ? 0 : st + 1);
+}
+__host__ __device__ __forceinline__ int status_worse(int a, int b) {
+  return status_rank(b) > status_rank(a) ? b : a;
+}
 
 // Offsets (in doubles) of one lane's workspace.
 struct WsLayout {
@@ -94,12 +108,18 @@ struct LaunchArgs {
   double* traj_prev;       // [n_steps][D] or null
   double* traj_cur;        // [n_steps][D] or null
   double* q_stages_out;    // [S*D] or null (last step's stages)
+  double* stages_traj;     // [n_steps][S*D] or null (every step's stages)
   int* status;             // [instances] or null
+  int* step_status;        // [n_steps][n_inst] each step's status, or null
+  double* step_rnorm;      // [n_steps][n_inst] |r|_2 where each step ended, or null
+  int64_t n_inst;          // instances of the launch (row length of the step logs)
+  int df64;                // 1: the link-parallel evaluation's residual pass in double-float
   int* iters;              // [instances] or null
   int* evals;              // [instances] or null (objective evaluations)
   int* grads;              // [instances] or null (evaluations that formed dE/dq or Jr)
   // step backward (implicit-function adjoint)
-  const double* g_bar;     // [S*D] dL/dq_* (stage-packed)
+  const double* g_bar;     // [S*D] dL/dq_* (stage-packed); segment adjoint: a_prev [D]
+  const double* a_cur_in;  // segment adjoint: a_cur [D]
   double* gq_prev;         // [D]
   double* gq_cur;          // [D]
   double* gtau;            // [D]
@@ -109,6 +129,13 @@ struct LaunchArgs {
   double* point_pos;       // [instances][3]
   double* point_jac;       // [3 * D] per model block [count][3][n], or null
 };
+
+// Bucket served by this block (buckets own consecutive block ranges).
+__device__ __forceinline__ int find_bucket(const LaunchArgs& A) {
+  int bk = 0;
+  while (bk + 1 < A.nb && (int)blockIdx.x >= A.bk[bk + 1].block_begin) ++bk;
+  return bk;
+}
 
 // ------------------------------------------------------------------------
 // per-lane context
@@ -240,6 +267,39 @@ struct Ctx {
         for (int r = 0; r < 3; ++r)
           w[3 * k + r] = fma(T[4 * r], Jr[k], fma(T[4 * r + 1], Jr[3 + k], T[4 * r + 2] * Jr[6 + k]));
     }
+  }
+
+  // Rounding floor of |r|_2 for one step of this instance: binary64 cannot
+  // resolve the stage residuals of Eq. HOC (or the gradient of Eq. EQ) below
+  // about eps times the size of the terms that cancel in them. The bound:
+  //   eps (What sum_l I_l + |g| sum_l (|m c_l| + m_l R_l)),
+  // What = the largest stage row sum of |seed weights| (acceleration and
+  // drag, over all S + 2 nodes), R_l = sum of |t(X_a)| over the joints on
+  // the root-to-l path, I_l = (sqrt(tr Sigma_l) + sqrt(m_l) R_l)^2 (a bound
+  // on int rho |P|^2 over link l about the root). Identical on the lanes of
+  // a group (group-mask shuffles only).
+  __device__ double rnorm_floor() const {
+    double row = fabs(wk[0]) + fabs(wk[1]);
+#pragma unroll
+    for (int j = 0; j < S; ++j) row += fabs(wu_row[j]);
+    double What = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) What = fmax(What, grp.from(row, j));
+    double sI = 0.0, sg = 0.0;
+    for (int l = 0; l < N; ++l) {
+      double R = 0.0;
+      for (int a = l; a >= 0; a = B.parent[a]) {
+        const double x = rest(a, 3), y = rest(a, 7), z = rest(a, 11);
+        R += sqrt(x * x + y * y + z * z);
+      }
+      const MassMoment M = mass(l);
+      const double tr = M.s[0] + M.s[3] + M.s[5], m = M.s[9];
+      const double a = sqrt(fmax(tr, 0.0)) + sqrt(fmax(m, 0.0)) * R;
+      sI += a * a;
+      sg += sqrt(M.s[6] * M.s[6] + M.s[7] * M.s[7] + M.s[8] * M.s[8]) + m * R;
+    }
+    const double gn = sqrt(B.g[0] * B.g[0] + B.g[1] * B.g[1] + B.g[2] * B.g[2]);
+    return 2.220446049250313e-16 * (What * sI + gn * sg);
   }
 
   // ----------------------------------------------------------- step setup

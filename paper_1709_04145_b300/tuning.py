@@ -125,3 +125,46 @@ def dt_sweep(model, q0, qd0, dts, stages: int, steps: int = 2, history: int = 8,
 
 
 __all__ = ["ProbeResult", "pick", "probe", "choose_solvers", "dt_sweep"]
+
+
+# ---------------------------------------------------------------- mapping
+@dataclass
+class MappingTrial:
+    """Device milliseconds of one probe launch under an instance-to-lane
+    mapping and a block size (ms = inf: the mapping does not serve it)."""
+    mapping: int
+    threads: int
+    ms: float
+
+
+def pick_mapping(trials):
+    """(mapping, threads) of the fastest trial; ties go to the stage mapping
+    (every topology and solver) and then to fewer threads per block."""
+    trials = [t for t in trials if np.isfinite(t.ms)]
+    if not trials:
+        raise ValueError("no mapping served the probe")
+    best = min(trials, key=lambda t: (t.ms, t.mapping, t.threads))
+    return best.mapping, best.threads
+
+
+def autotune_mapping(batch: Batch, probe_fn, mappings=(0, 1), threads=(32, 64, 128), repeats=1):
+    """Times probe_fn() (a short rollout of the workload on `batch`) under
+    every mapping and block size, after one untimed call of each, and leaves
+    the batch at the fastest. Returns (mapping, threads, trials)."""
+    from ._native import PBADError
+    trials = []
+    for mp in mappings:
+        batch.set_mapping(mp)
+        for th in threads:
+            batch.set_threads(th)
+            try:
+                probe_fn()
+            except PBADError:
+                trials.append(MappingTrial(mp, th, float("inf")))
+                continue
+            ms = min(_timed(probe_fn)[0] for _ in range(repeats))
+            trials.append(MappingTrial(mp, th, ms))
+    mp, th = pick_mapping(trials)
+    batch.set_mapping(mp)
+    batch.set_threads(th)
+    return mp, th, trials

@@ -201,3 +201,107 @@ def test_step_backward_large_ball_rotations(S):
         assert _relerr(gt[sl], rt) < 1e-7, b
         checked += 1
     assert checked >= B - 1
+
+
+def test_unsolved_steps_flag_their_instances_gradients():
+    """A step that ends unsolved (here MAX_ITER under a one-iteration cap)
+    breaks the implicit-function theorem: its instance's gradients come back
+    NaN (or zero), adjoint_status names the failure, and instances whose
+    steps all converged keep the gradients they get without the flag."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    from paper_1709_04145_b300.autograd import rollout_differentiable
+    dev = torch.device("cuda:0")
+    S, dt, n_steps = 2, 0.033, 4
+    spec = I.ball_chain(6, 4, seed=81, radius=0.15)
+    q0, qd0 = I.random_state(spec, 82, pose_scale=0.3, vel_sigma=0.3)
+    tau = I.torques(spec, n_steps, 83, sigma=0.1)
+    # instances 0-2 move fast (their steps need five LM iterations), 3-5
+    # slowly (four): a four-iteration cap leaves only the first three unsolved
+    qd0[:3] *= 8.0
+    qd0[3:] *= 0.1
+    tau[:, 3:] *= 0.1
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    n = spec.n_dof
+    grads = {}
+    for mode in ("keep", "nan", "zero"):
+        x0 = torch.tensor(q0.reshape(-1), device=dev, requires_grad=True)
+        v0 = torch.tensor(qd0.reshape(-1), device=dev, requires_grad=True)
+        tt = torch.tensor(tau.reshape(n_steps, -1), device=dev, requires_grad=True)
+        adj = torch.full((spec.count,), -1, dtype=torch.int32, device=dev)
+        qc, qp, st = rollout_differentiable(batch, x0, v0, tt, dt, S, P.NEWTON, tol=1e-10,
+                                            max_iter=4, checkpoint_every=2, on_unsolved=mode,
+                                            adjoint_status=adj)
+        qc.sum().backward()
+        grads[mode] = (x0.grad.cpu().numpy(), v0.grad.cpu().numpy(), tt.grad.cpu().numpy(),
+                       st.cpu().numpy(), adj.cpu().numpy())
+    st, adj = grads["nan"][3], grads["nan"][4]
+    unsolved = ~np.isin(st, [0, 5])
+    assert unsolved.any() and not unsolved.all(), st
+    assert np.array_equal(unsolved, ~np.isin(adj, [0, 5])), (st, adj)
+    for b in range(spec.count):
+        sl = slice(b * n, (b + 1) * n)
+        gk, gn, gz = grads["keep"], grads["nan"], grads["zero"]
+        for k in range(3):
+            blk = (lambda a: a[sl]) if k < 2 else (lambda a: a[:, sl])
+            if unsolved[b]:
+                assert np.all(np.isnan(blk(gn[k]))), (b, k)
+                assert np.all(blk(gz[k]) == 0.0), (b, k)
+                assert np.all(np.isfinite(blk(gk[k]))), (b, k)
+            else:
+                assert np.array_equal(blk(gn[k]), blk(gk[k])), (b, k)
+                assert np.array_equal(blk(gz[k]), blk(gk[k])), (b, k)
+
+
+@pytest.mark.parametrize("S", [1, 2])
+def test_segment_backward_equals_chained_step_backward(S):
+    """pbad_rollout_backward over a segment (one launch) gives what chaining
+    pbad_step_backward step by step from the host gives."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    dev = torch.device("cuda:0")
+    dt, T = 0.033, 5
+    spec = I.humanoid(5, seed=91)
+    q0, qd0 = I.random_state(spec, 92, pose_scale=0.3, vel_sigma=0.3)
+    tau = I.torques(spec, T, 93, sigma=0.1).reshape(T, -1)
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    nodes, _ = O.colloc(S)
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    qp0, qc0, tt = t(q0 + nodes[0] * dt * qd0), t(q0), t(tau).view(T, -1)
+    # (the comparison is of two orchestrations of the same per-step adjoint:
+    # it holds whether or not the steps converged)
+    out = P.rollout(batch, qp0, qc0, tt.reshape(-1), T, dt, S, P.NEWTON, 8, 1e-10, 100,
+                    want_stages=True)
+    rng = np.random.default_rng(94)
+    a_prev, a_cur = t(rng.normal(size=batch.D)), t(rng.normal(size=batch.D))
+    ap, ac, gt, st = P.rollout_backward(batch, qp0, qc0, tt.reshape(-1), out["stages_traj"], T, dt,
+                                        S, a_prev, a_cur)
+    assert (st.cpu().numpy() == 0).all()
+    # the same chain from the host, one pbad_step_backward per step
+    states, qp, qc = [], qp0, qc0
+    for k in range(T):
+        o = P.step(batch, qp, qc, tt[k].contiguous(), dt, S, P.NEWTON, 8, 1e-10, 100)
+        states.append((qp, qc, o["q_stages"]))
+        qp, qc = o["q_prev"], o["q_cur"]
+    n = spec.n_dof
+    bp, bc = a_prev.clone(), a_cur.clone()
+    gts = [None] * T
+    for k in range(T - 1, -1, -1):
+        qpk, qck, qs = states[k]
+        gbar = torch.zeros(S * batch.D, dtype=torch.float64, device=dev)
+        gv = gbar.view(spec.count, S, n)
+        gv[:, S - 1, :] += bc.view(spec.count, n)
+        if S >= 2:
+            gv[:, S - 2, :] += bp.view(spec.count, n)
+        gp_, gc_, g_, _ = P.step_backward(batch, qpk, qck, tt[k].contiguous(), qs, gbar, dt, S)
+        if S == 1:
+            gc_ = gc_ + bp
+        bp, bc = gp_, gc_
+        gts[k] = g_
+    def rel(x, y):
+        x, y = x.cpu().numpy(), y.cpu().numpy()
+        return np.max(np.abs(x - y)) / np.max(np.abs(y))
+    assert rel(ap, bp) < 1e-12 and rel(ac, bc) < 1e-12
+    assert rel(gt, torch.stack(gts)) < 1e-12

@@ -27,3 +27,30 @@ def test_pick_ties_go_to_lbfgs():
     a = ProbeResult(LBFGS, ms=20.0, converged=10, total=10)
     b = ProbeResult(NEWTON, ms=20.0, converged=10, total=10)
     assert pick([b, a]) == LBFGS
+
+
+def test_worse_status_order():
+    import torch
+
+    from paper_1709_04145_b300.autograd import worse_status
+    order = [0, 5, 1, 2, 3, 4]
+    a = torch.tensor([x for x in order for _ in order], dtype=torch.int32)
+    b = torch.tensor([y for _ in order for y in order], dtype=torch.int32)
+    got = worse_status(a, b).tolist()
+    want = [order[max(i, j)] for i in range(6) for j in range(6)]
+    assert got == want
+
+
+def test_pick_mapping_fastest_then_stage_then_fewer_threads():
+    from paper_1709_04145_b300.tuning import MappingTrial, pick_mapping
+    inf = float("inf")
+    t = [MappingTrial(0, 32, 10.0), MappingTrial(1, 32, 6.0), MappingTrial(1, 64, 6.0),
+         MappingTrial(0, 64, 9.0), MappingTrial(1, 128, inf)]
+    assert pick_mapping(t) == (1, 32)
+    t = [MappingTrial(1, 32, 5.0), MappingTrial(0, 64, 5.0)]
+    assert pick_mapping(t) == (0, 64)
+    t = [MappingTrial(1, 32, inf), MappingTrial(0, 128, 7.0)]
+    assert pick_mapping(t) == (0, 128)
+    import pytest
+    with pytest.raises(ValueError):
+        pick_mapping([MappingTrial(1, 32, inf)])
