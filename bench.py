@@ -44,7 +44,11 @@ COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 # launch named by the key (mapping, stages, links), valid only for the kernel
 # sources whose hash is stored with it: any change to csrc/ makes the
 # roofline's traffic null until the kernel is captured again.
-ROLLOUT_TRAFFIC = {}
+ROLLOUT_TRAFFIC = {
+    # link mapping, 3 stages, 10 links: 4096 ball chains x 100 steps, five launches of
+    # k_rollout_lp<3>: 50.84 MB read + 18.54 MB written over 5 x 56,195,039 evaluations
+    (1, 3, 10): ("4e27c86609c4a8f5e14f700c801b2e69e237f741", 0.24692),
+}
 
 
 def csrc_hash() -> str:

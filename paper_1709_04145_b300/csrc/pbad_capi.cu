@@ -355,7 +355,18 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
   A->history = history;
   A->threads = bt->threads;
   A->dense_stages = (bt->flags & PBAD_BATCH_NEWTON) ? bt->max_stages : 0;
-  const int wpb = bt->threads / 32;
+  // Newton buckets with S n >= kNewtonCtaMin run one CTA of kNewtonCtaWarps
+  // warps per instance; the launch then uses blocks of that many warps
+  int max_cta_sn = 0;
+  if (!all_warp)
+    for (int k = 0; k < (int)bt->models.size(); ++k) {
+      const int sn = S * bt->models[k]->n;
+      if (solvers && solvers[k] == PBAD_NEWTON && sn >= kNewtonCtaMin && sn <= kNewtonCtaMaxSn)
+        max_cta_sn = std::max(max_cta_sn, sn);
+    }
+  if (max_cta_sn > 0) A->threads = 32 * kNewtonCtaWarps;
+  A->cta_smem = max_cta_sn > 0 ? (int)((2 * cta::kTile * cta::kPad + 32 + max_cta_sn) * sizeof(double)) : 0;
+  const int wpb = A->threads / 32;
   int blocks = 0;
   for (int k = 0; k < A->nb; ++k) {
     const pbad_model* m = bt->models[k];
@@ -397,7 +408,11 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.c_d1 = m->c_d1;
     B.c_d2 = m->c_d2;
     const bool warp_map = all_warp || B.solver == PBAD_NEWTON;
-    const int64_t warps = warp_map ? m->count : (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
+    const int sn = S * m->n;
+    B.cta = (!all_warp && B.solver == PBAD_NEWTON && sn >= kNewtonCtaMin && sn <= kNewtonCtaMaxSn)
+                ? kNewtonCtaWarps : 1;
+    const int64_t warps = warp_map ? m->count * B.cta
+                                   : (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
     blocks += (int)((warps + wpb - 1) / wpb);
   }
   *grid = blocks;
@@ -786,7 +801,9 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
       if (l > lanes) lanes = l;
     }
     if (flags & PBAD_BATCH_NEWTON) {
-      const int64_t l = ((m->count + 11) / 12) * 12 * 32;
+      // one warp per instance, or one CTA of kNewtonCtaWarps when S n is large
+      const int64_t per = max_stages * m->n >= kNewtonCtaMin ? kNewtonCtaWarps : 1;
+      const int64_t l = ((m->count * per + 11) / 12) * 12 * 32;
       if (l > lanes) lanes = l;
       DenseLayout DL;
       DL.make(max_stages * m->n);

@@ -444,16 +444,19 @@ __device__ __noinline__ void rollout_lbfgs(const LaunchArgs& A, const Bucket& B)
 constexpr int kLmMaxTrials = 60;
 constexpr int kLmHalvings = 3;  // halvings of a damped step before lambda grows
 
-// Lane identity of the warp-per-instance mapping.
+// Lane identity of the warp-per-instance mapping (cta = 1) or of the
+// CTA-per-instance mapping of large Newton buckets (cta warps per instance,
+// warp wid of the instance).
 template <int S>
 struct WarpId {
   int64_t lane_id, inst;
-  int rep, R;
-  __device__ WarpId(const Bucket& B) {
+  int rep, R, wid;
+  __device__ WarpId(const Bucket& B, int cta = 1) {
     const int lane = threadIdx.x & 31;
     const int64_t warp = ((int64_t)(blockIdx.x - B.block_begin) * blockDim.x + threadIdx.x) >> 5;
     lane_id = warp * 32 + lane;
-    inst = warp;
+    inst = warp / cta;
+    wid = (int)(warp - inst * cta);
     R = 32 / S;
     rep = lane / S;  // rep == R: surplus lanes (S = 3, 5)
   }
@@ -461,9 +464,45 @@ struct WarpId {
 
 __device__ __forceinline__ double bcast0(double v) { return __shfl_sync(0xffffffffu, v, 0); }
 
+// Gram matrix of the CTA mode: H = Jr^T Jr and gg = Jr^T r (S >= 2, the
+// syrk on the column-major Jacobian) or the Gauss-Newton matrix and gg = r
+// (S == 1); returns max diag(H) on every thread.
+template <int S>
+__device__ double gram_cta(const Ctx<S>& c, double* D, const DenseLayout& DL, double* sa,
+                           double* sc, double* red) {
+  const int Sn = S * c.n;
+  const int tid = threadIdx.x, nth = blockDim.x;
+  if (S == 1) {
+    for (int e = tid; e < Sn * Sn; e += nth) {
+      const int a = e / Sn, cc = e - a * Sn;
+      D[DL.H + e] = D[DL.J + (int64_t)cc * Sn + a];
+    }
+    for (int a = tid; a < Sn; a += nth) D[DL.gg + a] = D[DL.r + a];
+    __syncthreads();
+  } else {
+    cta::syrk(D + DL.J, D + DL.H, Sn, sa, sc);
+    // gg[a] = column a of Jr . r: one warp per column, lanes over the rows
+    const int w = tid >> 5, lane = tid & 31, nw = nth >> 5;
+    for (int a = w; a < Sn; a += nw) {
+      double g = 0.0;
+      for (int rr = lane; rr < Sn; rr += 32) g = fma(D[DL.J + (int64_t)a * Sn + rr], D[DL.r + rr], g);
+      for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+      if (lane == 0) D[DL.gg + a] = g;
+    }
+    __syncthreads();
+  }
+  double hm = 0.0;
+  for (int a = tid; a < Sn; a += nth) hm = fmax(hm, D[DL.H + (int64_t)a * Sn + a]);
+  return cta::block_max(hm, red);
+}
+
 template <int S>
 __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B) {
-  const WarpId<S> id(B);
+  // CTA mode (B.cta > 1): the instance's warps run the same state machine on
+  // the same values (each evaluates the residual pass itself), split the
+  // Jacobian columns, and form the Gram matrix and the factor together.
+  const int ncta = B.cta > 1 ? B.cta : 1;
+  const WarpId<S> id(B, ncta);
   const bool active = id.inst < B.count;
   const int b = active ? (int)id.inst : 0;
   Ctx<S> c(B, A.K, b, id.lane_id, A.history, A.dense_stages);
@@ -471,10 +510,18 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
   const auto& L = c.L;
   const Lane& ws = c.ws;
   const int64_t D = A.D;
-  const bool writer = active && id.rep == 0;  // replica 0 writes the outputs
+  const bool writer = active && id.rep == 0 && id.wid == 0;  // one replica writes the outputs
   double* Dn = B.dense + (int64_t)b * B.dense_stride;
   DenseLayout DL;
   DL.make(S * n);
+  extern __shared__ double dyn_smem[];  // CTA mode: syrk tiles, reduction scratch, a vector
+  double* s_sa = dyn_smem;
+  double* s_sc = s_sa + cta::kTile * cta::kPad;
+  double* s_red = s_sc + cta::kTile * cta::kPad;
+  double* s_vec = s_red + 32;
+  // replica index and count over the whole CTA (surplus lanes stay surplus)
+  const int rep_g = id.rep < id.R ? id.wid * id.R + id.rep : ncta * id.R;
+  const int R_g = ncta * id.R;
 
   for (int d = 0; d < n; ++d) {
     ws[L.qp + d] = A.q_prev0[c.gdof(d)];
@@ -585,12 +632,18 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
       else if (k >= A.max_iter) { finish(kMaxIter); need = 0; }
     }
     if (need == 1) {
-      if (id.rep == 0)
+      if (id.rep == 0 && id.wid == 0)
         for (int d = 0; d < n; ++d) Dn[DL.r + c.i * n + d] = ws[L.r + d];
-      __syncwarp();
-      c.build_jacobian_warp(Dn, DL, id.rep, id.R, false);
+      if (ncta > 1) {
+        c.build_jacobian_warp(Dn, DL, rep_g, R_g, false);
+        __syncthreads();
+        hmax = gram_cta(c, Dn, DL, s_sa, s_sc, s_red);
+      } else {
+        __syncwarp();
+        c.build_jacobian_warp(Dn, DL, id.rep, id.R, false);
+        hmax = c.gram_warp(Dn, DL);
+      }
       ++grads_total;
-      hmax = c.gram_warp(Dn, DL);
       if (lambda < 0.0) lambda = 1e-12 * hmax;
       trials = 0;
       need = 2;
@@ -598,7 +651,10 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     if (need == 2) {
       bool solved = false;
       while (!solved) {
-        if (c.factor_solve_warp(Dn, DL, lambda)) {
+        const bool f = ncta > 1 ? cta::factor_solve(Dn + DL.H, Dn + DL.A, Dn + DL.gg, Dn + DL.dl,
+                                                   S * n, lambda, s_vec, s_red)
+                               : c.factor_solve_warp(Dn, DL, lambda);
+        if (f) {
           solved = true;
         } else {
           lambda *= 10.0;
@@ -921,16 +977,17 @@ cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cu
   int kinds = 0;  // bit per solver present
   for (int k = 0; k < A.nb; ++k) kinds |= 1 << A.bk[k].solver;
   const bool queue = A.bk[0].queue != nullptr;  // set for single-kind L-BFGS launches only
+  const size_t smem = A.cta_smem;               // CTA-mode Newton buckets only
   if (kinds == 1) {
     if (queue) k_rollout<PBAD_S, 4><<<grid, A.threads, 0, s>>>(A);
     else k_rollout<PBAD_S, 0><<<grid, A.threads, 0, s>>>(A);
   } else if (kinds == 2) {
-    k_rollout<PBAD_S, 1><<<grid, A.threads, 0, s>>>(A);
+    k_rollout<PBAD_S, 1><<<grid, A.threads, smem, s>>>(A);
   } else if (kinds == 4) {
     if (queue) k_rollout<PBAD_S, 5><<<grid, A.threads, 0, s>>>(A);
     else k_rollout<PBAD_S, 3><<<grid, A.threads, 0, s>>>(A);
   } else {
-    k_rollout<PBAD_S, 2><<<grid, A.threads, 0, s>>>(A);
+    k_rollout<PBAD_S, 2><<<grid, A.threads, smem, s>>>(A);
   }
   return cudaGetLastError();
 }

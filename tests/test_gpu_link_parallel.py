@@ -65,6 +65,9 @@ def test_link_parallel_eval_matches_oracle(S):
             assert abs(Eg - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (spec.name, b, Eg, Eo)
             assert _relerr(resids[k][b].reshape(-1), ro) < REL_EVAL, (spec.name, b)
             assert _relerr(grads[k][b].reshape(-1), go) < REL_EVAL, (spec.name, b)
+            # per element, with twice the binary64 rounding bound of r as floor
+            dr = np.abs(resids[k][b].reshape(-1) - ro)
+            assert np.all(dr <= REL_EVAL * np.abs(ro) + 2 * om.floor(S, dt)), (spec.name, b)
             # and the two mappings agree to rounding
             assert _relerr(grads[k][b], grads_s[k][b]) < REL_EVAL, (spec.name, b)
 

@@ -1,0 +1,136 @@
+"""Newton with one CTA per instance (buckets with S n >= 128 unknowns: the
+instance's four warps split the Jacobian columns and form the Gram matrix
+and the Cholesky factor together) against the CPU oracle's LM."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1709_04145_b300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+
+def _t(a, dev):
+    import torch
+    return torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+
+
+def test_cta_newton_ball_chains_match_oracle():
+    """22-link ball chains, three stages (S n = 198), dt 0.01, 3 steps,
+    tol 1e-6: every step's status and the whole trajectory."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    dev = torch.device("cuda:0")
+    S, dt, T, tol = 3, 0.01, 3, 1e-6
+    spec = I.ball_chain(6, 22, seed=3, radius=0.15)
+    q0, qd0 = I.random_state(spec, 5, pose_scale=0.2, vel_sigma=0.2)
+    nodes, _ = O.colloc(S)
+    qp = q0 + nodes[0] * dt * qd0
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    out = P.rollout(batch, _t(qp, dev), _t(q0, dev), None, T, dt, S, P.NEWTON, 8, tol, 100)
+    st = out["step_status"].cpu().numpy()
+    traj = out["traj_cur"].cpu().numpy().reshape(T, spec.count, spec.n_dof)
+    conv = 0
+    for b in (0, 2, 5):
+        om = O.OracleModel.from_spec(spec, b)
+        ref = om.rollout(S, dt, qp[b], q0[b], np.zeros((T, spec.n_dof)), "lm", 8, tol, 100)
+        assert np.array_equal(st[:, b], ref["step_status"]), (b, st[:, b], ref["step_status"])
+        for k in range(T):
+            if st[k, b] != 0:
+                break
+            err = np.abs(traj[k, b] - ref["traj_cur"][k])
+            assert np.all(err <= 1e-6 * np.maximum(1.0, np.abs(ref["traj_cur"][k]))), (b, k, err.max())
+            conv += 1
+    assert conv >= 6
+
+
+def test_cta_newton_scaling_chains_first_step():
+    """The scaling study's 50-link hinge chains (four stages, S n = 200, dt
+    0.1), 20-iteration cap: the first step's status (it ends at the cap on
+    both sides; the |r| reached there depends on the iterates' path, see
+    the trajectory tests' rule)."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    dev = torch.device("cuda:0")
+    ws = I.scaling_chains(50, n_steps=1)
+    spec, S, dt = ws["spec"], ws["stages"], ws["dt"]
+    nodes, _ = O.colloc(S)
+    qp = ws["q0"] + nodes[0] * dt * ws["qd0"]
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    out = P.rollout(batch, _t(qp, dev), _t(ws["q0"], dev), None, 1, dt, S, P.NEWTON, 8, 1e-8, 20)
+    st = out["step_status"].cpu().numpy()[0]
+    rn = out["step_rnorm"].cpu().numpy()[0]
+    for b in (0, 128, 255):
+        om = O.OracleModel.from_spec(spec, b)
+        ref = om.rollout(S, dt, qp[b], ws["q0"][b], np.zeros((1, spec.n_dof)), "lm", 8, 1e-8, 20)
+        assert st[b] == ref["step_status"][0], (b, st[b], ref["step_status"][0])
+        if st[b] not in (0, 1):
+            assert 0.5 <= rn[b] / ref["step_rnorm"][0] <= 2.0, (b, rn[b], ref["step_rnorm"][0])
+        assert rn[b] < out["step_rnorm"].new_tensor([1e30]).item()
+
+
+def test_cta_newton_adjoint_after_rollout():
+    """The adjoint (one warp per instance) of a step solved in CTA mode,
+    against the oracle's dense adjoint."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    dev = torch.device("cuda:0")
+    S, dt = 3, 0.01
+    spec = I.ball_chain(4, 22, seed=3, radius=0.15)
+    q0, qd0 = I.random_state(spec, 7, pose_scale=0.2, vel_sigma=0.2)
+    nodes, _ = O.colloc(S)
+    qp = q0 + nodes[0] * dt * qd0
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    out = P.step(batch, _t(qp, dev), _t(q0, dev), None, dt, S, P.NEWTON, 8, 1e-6, 100)
+    st = out["status"].cpu().numpy()
+    rng = np.random.default_rng(8)
+    gbar = rng.normal(size=S * batch.D)
+    gp, gc, gt, bst = P.step_backward(batch, _t(qp, dev), _t(q0, dev), None, out["q_stages"],
+                                      _t(gbar, dev), dt, S)
+    qs = out["q_stages"].cpu().numpy()
+    n = spec.n_dof
+    checked = 0
+    for b in range(spec.count):
+        if st[b] != 0:
+            continue
+        om = O.OracleModel.from_spec(spec, b)
+        sl, ssl = slice(b * n, (b + 1) * n), slice(S * b * n, S * (b + 1) * n)
+        rp, rc, rt = om.step_adjoint(S, dt, qp[b], q0[b], np.zeros(n), qs[ssl], gbar[ssl])
+        for got, ref in ((gp, rp), (gc, rc), (gt, rt)):
+            got = got.cpu().numpy()[sl]
+            assert np.max(np.abs(got - ref)) <= 1e-6 * np.max(np.abs(ref)), b
+        checked += 1
+    assert checked >= 2
+
+
+@pytest.mark.parametrize("S,N,dt", [(1, 200, 0.01), (4, 50, 0.1)])
+def test_cta_newton_first_iterate_matches_oracle(S, N, dt):
+    """One Newton iteration (Gram matrix, factorisation, solve, damping) on
+    hinge chains in CTA mode - S n = 200, including the scaling study's
+    200-link chains at one stage - from the same initial guess on both
+    sides: the iterate agrees per element (relative 1e-6, floor 1e-6 rad)
+    and so does its |r|."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    dev = torch.device("cuda:0")
+    spec = I.rod_chain(4, N, name=f"rod{N}")
+    q0, qd0 = I.random_state(spec, 5, pose_scale=0.2, vel_sigma=0.2)
+    nodes, _ = O.colloc(S)
+    qp = q0 + nodes[0] * dt * qd0
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    out = P.rollout(batch, _t(qp, dev), _t(q0, dev), None, 1, dt, S, P.NEWTON, 8, 1e-12, 1)
+    traj = out["traj_cur"].cpu().numpy().reshape(spec.count, N)
+    st = out["step_status"].cpu().numpy()[0]
+    rn = out["step_rnorm"].cpu().numpy()[0]
+    for b in (0, 3):
+        om = O.OracleModel.from_spec(spec, b)
+        ref = om.rollout(S, dt, qp[b], q0[b], np.zeros((1, N)), "lm", 8, 1e-12, 1)
+        assert st[b] == ref["step_status"][0], (b, st[b], ref["step_status"][0])
+        q = ref["traj_cur"][0]
+        err = np.abs(traj[b] - q)
+        assert np.all(err <= 1e-6 * np.maximum(1.0, np.abs(q))), (b, err.max())
+        assert abs(rn[b] - ref["step_rnorm"][0]) <= 1e-4 * ref["step_rnorm"][0], (b, rn[b], ref["step_rnorm"][0])

@@ -73,6 +73,12 @@ def test_eval_matches_oracle(S):
             assert abs(Eg - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (spec.name, b, Eg, Eo)
             assert _relerr(resids[k][b].reshape(-1), ro) < REL_EVAL, (spec.name, b)
             assert _relerr(grads[k][b].reshape(-1), go) < REL_EVAL, (spec.name, b)
+            # per element: each residual component to 1e-10 of itself, with an
+            # absolute floor of twice the binary64 rounding bound of r (the
+            # largest component alone would let small ones pass loosely)
+            fl = om.floor(S, dt)
+            dr = np.abs(resids[k][b].reshape(-1) - ro)
+            assert np.all(dr <= REL_EVAL * np.abs(ro) + 2 * fl), (spec.name, b, dr.max(), fl)
 
 
 def test_eval_without_tau_and_single_instance():
