@@ -42,24 +42,30 @@ COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 # DRAM bytes (read + write) per instance-evaluation of the rollout kernel,
 # from one ncu capture (dram__bytes_read.sum + dram__bytes_write.sum) of the
 # launch named by the key (mapping, stages, links), valid only for the kernel
-# sources whose hash is stored with it: any change to csrc/ makes the
-# roofline's traffic null until the kernel is captured again.
+# sources whose hash is stored with it: any change to the files the kernel's
+# device code comes from (ROLLOUT_KERNEL_SOURCES) makes the roofline's
+# traffic null until the kernel is captured again.
 ROLLOUT_TRAFFIC = {
     # link mapping, 3 stages, 10 links: 4096 ball chains x 100 steps, five launches of
-    # k_rollout_lp<3>: 50.84 MB read + 18.54 MB written over 5 x 56,195,039 evaluations
-    (1, 3, 10): ("4e27c86609c4a8f5e14f700c801b2e69e237f741", 0.24692),
+    # k_rollout_lp<3>: 50.45 MB read + 17.97 MB written over 5 x 56,195,059 evaluations
+    (1, 3, 10): ("79966d603667746e4bbee43847db3e3e02c098f6", 0.24351),
 }
 
 
-def csrc_hash() -> str:
-    """SHA-1 of the CUDA sources (the kernels the traffic figures describe)."""
+# the headers k_rollout_lp's device code is compiled from (its body, the
+# per-lane passes, the launch arguments, the model layout, double-float)
+ROLLOUT_KERNEL_SOURCES = ("pbad_device.cuh", "pbad_df64.cuh", "pbad_kernels.cuh", "pbad_lp.cuh")
+
+
+def csrc_hash(files=ROLLOUT_KERNEL_SOURCES) -> str:
+    """SHA-1 of the named CUDA sources (the kernel the traffic figure
+    describes)."""
     import hashlib
     h = hashlib.sha1()
     d = os.path.join(ROOT, "paper_1709_04145_b300", "csrc")
-    for f in sorted(os.listdir(d)):
-        if f.endswith((".cu", ".cuh")):
-            with open(os.path.join(d, f), "rb") as fh:
-                h.update(f.encode() + fh.read())
+    for f in sorted(files):
+        with open(os.path.join(d, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
     return h.hexdigest()
 
 
@@ -150,9 +156,9 @@ def parse():
     p.add_argument("--mapping", type=int, default=0,
                    help="instance-to-lane mapping when --threads is given: 0 one lane per stage, "
                         "1 one lane per stage and link")
-    p.add_argument("--plain-instances", type=int, default=8,
+    p.add_argument("--plain-instances", type=int, default=64,
                    help="instances timed in the plain form (one launch per instance-step)")
-    p.add_argument("--plain-timesteps", type=int, default=10)
+    p.add_argument("--plain-timesteps", type=int, default=2)
     p.add_argument("--throughput-instances", type=int, default=65536,
                    help="instances of the large-batch throughput point (0 = skip)")
     p.add_argument("--throughput-timesteps", type=int, default=20)
@@ -172,6 +178,8 @@ def parse():
                    help="seconds per (links, solver) row of the scaling study: fewer steps are "
                         "run when a one-step probe says the requested ones would take longer")
     p.add_argument("--scaling-links", type=int, nargs="+", default=[25, 50, 100, 200])
+    p.add_argument("--damped-links", type=int, default=200,
+                   help="links of the damped-system (Gram + Cholesky) timing, S = 4; 0 skips it")
     p.add_argument("--max-iter-scaling", type=int, default=3,
                    help="iteration cap per step of the scaling study (a fixed budget: the study "
                         "compares the cost per iteration of the two solvers)")
@@ -605,6 +613,9 @@ def measure_uneven(P, args, dev):
         tuned[threads] = _timed(lambda: run(1))[0]
     best = min(tuned, key=tuned.get)
     batch.set_threads(best)
+    from paper_1709_04145_b300.tuning import autotune_bucket_mapping
+    mapping_names = {P.MAP_STAGE: "stage", P.MAP_LINK: "link"}
+    bmap, btrials = autotune_bucket_mapping(batch, lambda: run(1))
     ms, out = _timed(lambda: run(T))
     st = out["status"].cpu().numpy()
     it = out["iters"].cpu().numpy()
@@ -623,9 +634,15 @@ def measure_uneven(P, args, dev):
     res = {"value": link_steps / (ms / 1e3), "unit": UNIT, "ms": ms, "timesteps": T,
            "launches": 1, "threads_per_block": best,
            "autotune_ms_per_step": {str(k): v for k, v in tuned.items()},
+           "bucket_mapping": {"chosen": [mapping_names[x] for x in bmap],
+                              "rule": "greedy per bucket: link-map bucket k if a one-step "
+                                      "launch gets faster (refused where not a chain, S N > 32 "
+                                      "or Newton)",
+                              "one_step_ms_stage_then_link": btrials},
            "max_iter_per_step": args.max_iter_uneven, "tol": u["tol"], "buckets": buckets}
     # per-bucket solver choice from one-step probes, then the same rollout
     from paper_1709_04145_b300.tuning import choose_solvers
+    batch.set_bucket_mapping(None)
     t0 = time.perf_counter()
     chosen, report = choose_solvers(batch, qp, qc, tau, dt, S, probe_steps=1, history=m,
                                     tol=u["tol"], max_iter={P.LBFGS: args.max_iter_uneven,
@@ -634,6 +651,7 @@ def measure_uneven(P, args, dev):
     probe_s = time.perf_counter() - t0
     run_c = lambda steps: P.rollout(batch, qp, qc, tau[:steps].reshape(-1).contiguous(), steps, dt,
                                     S, chosen, m, u["tol"], args.max_iter_uneven, want_traj=False)
+    bmap_c, _ = autotune_bucket_mapping(batch, lambda: run_c(1))
     ms_c, out_c = _timed(lambda: run_c(T))
     st_c = out_c["status"].cpu().numpy()
     names = {P.LBFGS: "lbfgs", P.NEWTON: "newton"}
@@ -642,6 +660,7 @@ def measure_uneven(P, args, dev):
                 "over a one-step probe of the bucket alone",
         "probe_wall_s": probe_s,
         "chosen": [names[c] for c in chosen],
+        "bucket_mapping": [mapping_names[x] for x in bmap_c],
         "value": link_steps / (ms_c / 1e3), "ms": ms_c,
         "buckets": [{"model": spec.name,
                      "probe": {names[r.solver]: {"ms": r.ms, "converged_fraction": r.converged / r.total}
@@ -902,6 +921,32 @@ def measure_scaling(P, args, dev):
             "steps_requested": args.scaling_steps, "budget_s_per_row": args.scaling_budget}
 
 
+def measure_damped_system(P, args, dev, peak_tflops):
+    """The LM iteration's damped system alone (pbad_damped_gram_solve: Gram
+    matrix, Cholesky, solves; one CTA per instance) at the scaling study's
+    largest Newton size: 256 instances, S n = 4 x args.damped_links, random
+    J = N(0, 1) + 3 I, lambda = 1e-3. Algorithmic flops per instance: the
+    lower triangle of J^T J, n^2 (n + 1) / 2 FMAs; the Cholesky, n^3 / 3
+    flops; the two solves, 2 n^2."""
+    import torch
+    n, count = 4 * args.damped_links, 256
+    gen = torch.Generator(device=dev).manual_seed(11)
+    J = torch.randn((count, n, n), dtype=torch.float64, device=dev, generator=gen)
+    J += 3.0 * torch.eye(n, dtype=torch.float64, device=dev)
+    g = torch.randn((count, n), dtype=torch.float64, device=dev, generator=gen)
+    P.damped_gram_solve(J, g, 1e-3)
+    ms = min(_timed(lambda: P.damped_gram_solve(J, g, 1e-3))[0] for _ in range(2))
+    _, _, _, st = P.damped_gram_solve(J, g, 1e-3)
+    flops = count * (n * n * (n + 1) + n ** 3 / 3 + 2 * n * n)
+    tf = flops / (ms / 1e3) / 1e12
+    res = {"instances": count, "n": n, "ms": ms, "flops": flops, "achieved_tflops": tf,
+           "frac_of_fp64_peak": tf / peak_tflops, "factored_fraction": float((st == 0).float().mean()),
+           "note": "one CTA (128 threads) per instance; 256 CTAs on 148 SMs at 2 CTAs/SM"}
+    del J, g
+    torch.cuda.empty_cache()
+    return res
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -1094,6 +1139,8 @@ def run_ours(args):
         line["uneven_batch"] = measure_uneven(P, args, dev)
     if rank == 0 and args.scaling_steps > 0:
         line["scaling_study"] = measure_scaling(P, args, dev)
+    if rank == 0 and args.damped_links > 0:
+        line["damped_system"] = measure_damped_system(P, args, dev, peak)
     if rank == 0 and args.drag_steps > 0:
         line["drag"] = measure_drag(P, args, dev)
     if rank == 0 and args.f32_steps > 0:

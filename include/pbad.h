@@ -205,6 +205,39 @@ PBAD_API int pbad_batch_set_threads(pbad_batch* batch, int32_t threads);
 #define PBAD_MAP_LINK 1
 PBAD_API int pbad_batch_set_mapping(pbad_batch* batch, int32_t mapping);
 
+/* The damped Gauss-Newton system of one LM iteration (Section 5, LM with
+ * J^T J), batched, on its own: for each instance b of count,
+ *   H_b = J_b^T J_b,  L_b L_b^T = H_b + lambda I (Cholesky),
+ *   dl_b = -(H_b + lambda I)^-1 g_b.
+ * One CTA per instance with the routines of the CTA-mode Newton rollout
+ * (tiled syrk, left-looking Cholesky, triangular solves).
+ *   J:      device, [count][n][n], each instance column-major (column c of
+ *           J_b at J + b n^2 + c n); read only.
+ *   g:      device, [count][n] (for LM, J^T r); read only.
+ *   H:      device, [count][n][n] out, row-major and symmetric.
+ *   L:      device, [count][n][n] out, the factor column-major (L[r][c] at
+ *           L + b n^2 + c n + r, r >= c; the upper part is left as is).
+ *   dl:     device, [count][n] out.
+ *   status: device, [count] out: PBAD_CONVERGED, or PBAD_CHOL_FAIL where a
+ *           pivot was not positive (dl and the rest of L then undefined).
+ * All buffers are caller-owned; nothing is allocated. Asynchronous on
+ * `stream` (NULL: the default stream). 1 <= n <= 4096 and count < 2^31,
+ * else PBAD_ERR_ARG (count 0 launches nothing); PBAD_ERR_ARG also for a
+ * null array or a non-finite lambda; PBAD_ERR_CUDA if the launch fails. */
+PBAD_API int pbad_damped_gram_solve(int64_t count, int32_t n, const double* J, const double* g,
+                                    double lambda, double* H, double* L, double* dl,
+                                    int32_t* status, void* stream);
+
+/* Per-bucket mapping of pbad_step and pbad_rollout: mapping[n_models] (host)
+ * of PBAD_MAP_STAGE, PBAD_MAP_LINK or -1 (the batch's mapping); NULL clears
+ * it. A launch whose buckets mix the mappings stays one persistent launch:
+ * each block runs its bucket's mapping (link-mapped buckets must qualify as
+ * for pbad_batch_set_mapping, else PBAD_ERR_UNSUPPORTED). The instance queue
+ * is not used in such launches. pbad_eval_objective_grad follows the
+ * batch's mapping. Errors: PBAD_ERR_ARG for a null batch or an unknown
+ * mapping value. */
+PBAD_API int pbad_batch_set_bucket_mapping(pbad_batch* batch, const int32_t* mapping);
+
 /* Arithmetic of the residual pass of pbad_eval_objective_grad (a
  * mixed-precision experiment; the paper states no precision):
  *   PBAD_PRECISION_F64 (default): binary64 throughout.

@@ -79,6 +79,26 @@ def fp64_mma_peak(device: int = 0) -> float:
     return out.value
 
 
+def damped_gram_solve(J, g, lam: float, stream=None):
+    """The LM iteration's damped system for a batch of square Jacobians
+    (pbad_damped_gram_solve): J (count, n, n) with J[b, c] column c of J_b,
+    g (count, n). Returns (H, L, dl, status): H = J^T J, L the Cholesky
+    factor of H + lam I stored column-major (L[b, c, r] = L_b[r][c], r >= c),
+    dl = -(H + lam I)^-1 g, status 0 or CHOL_FAIL per instance."""
+    import torch
+    count, n = int(J.shape[0]), int(J.shape[1])
+    if tuple(J.shape) != (count, n, n) or tuple(g.shape) != (count, n):
+        raise ValueError("J must be (count, n, n) and g (count, n)")
+    H = torch.empty_like(J)
+    L = torch.zeros_like(J)
+    dl = torch.empty_like(g)
+    st = torch.empty(count, dtype=torch.int32, device=J.device)
+    check(lib().pbad_damped_gram_solve(count, n, _tptr(J), _tptr(g), float(lam), _tptr(H), _tptr(L),
+                                        _tptr(dl), _tptr(st), _stream(stream)),
+          "pbad_damped_gram_solve")
+    return H, L, dl, st
+
+
 class Model:
     """One topology with ``count`` instances (pbad_model)."""
 
@@ -181,6 +201,18 @@ class Batch:
         per stage and link; serial chains with stages * links <= 32)."""
         check(lib().pbad_batch_set_mapping(self._h, int(mapping)), "pbad_batch_set_mapping")
         self.mapping = int(mapping)
+
+    def set_bucket_mapping(self, mappings):
+        """Per-bucket mapping of steps and rollouts (MAP_STAGE, MAP_LINK or -1
+        for the batch's); None clears it. Buckets of different mappings still
+        share one persistent launch."""
+        if mappings is None:
+            check(lib().pbad_batch_set_bucket_mapping(self._h, None), "pbad_batch_set_bucket_mapping")
+            self.bucket_mapping = None
+            return
+        arr = np.ascontiguousarray(mappings, dtype=np.int32).reshape(len(self.models))
+        check(lib().pbad_batch_set_bucket_mapping(self._h, _iptr(arr)), "pbad_batch_set_bucket_mapping")
+        self.bucket_mapping = [int(x) for x in arr]
 
     def set_precision(self, precision: int):
         """Arithmetic of eval_objective_grad's residual pass: PRECISION_F64

@@ -9,8 +9,8 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpbad.so")
 STAGE_COUNTS = (1, 2, 3, 4, 5)  # pbad_kernels.cu is compiled once per stage count
-SOURCES = ["pbad_kernels.cu", "pbad_capi.cu", "pbad_static.cu"]
-HEADERS = ["pbad_device.cuh", "pbad_kernels.cuh", "pbad_lp.cuh", "pbad_df64.cuh"]
+SOURCES = ["pbad_kernels.cu", "pbad_capi.cu", "pbad_static.cu", "pbad_dense.cu"]
+HEADERS = ["pbad_device.cuh", "pbad_kernels.cuh", "pbad_lp.cuh", "pbad_df64.cuh", "pbad_cta.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
@@ -35,7 +35,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         obj = os.path.join(CSRC, f"pbad_kernels_s{S}.o")
         jobs.append((obj, [NVCC, *FLAGS, f"-DPBAD_S={S}", "-c",
                            os.path.join(CSRC, "pbad_kernels.cu"), "-o", obj]))
-    for src in ("pbad_capi.cu", "pbad_static.cu"):
+    for src in ("pbad_capi.cu", "pbad_static.cu", "pbad_dense.cu"):
         obj = os.path.join(CSRC, src.replace(".cu", ".o"))
         jobs.append((obj, [NVCC, *FLAGS, "-c", os.path.join(CSRC, src), "-o", obj]))
     procs = []

@@ -11,6 +11,7 @@
 #include "../../include/pbad.h"
 #include "pbad_kernels.cuh"
 #include "pbad_lp.cuh"
+#include "pbad_cta.cuh"
 
 namespace pbad {
 #define PBAD_DECL(S)                                                                \
@@ -153,6 +154,7 @@ struct pbad_batch {
   int* d_queue = nullptr;
   int queue_blocks = -1;
   int mapping = PBAD_MAP_STAGE;  // instance-to-lane mapping of the L-BFGS and eval kernels
+  std::vector<int> bucket_mapping;  // per bucket for steps and rollouts (-1: the batch's mapping)
   int precision = PBAD_PRECISION_F64;  // arithmetic of pbad_eval_objective_grad's residual pass
 };
 
@@ -478,6 +480,8 @@ bool apply_queue(pbad_batch* bt, int S, LaunchArgs* A, int* grid) {
 // be a serial chain with S N <= 32 lanes per instance, solved by binary64
 // L-BFGS (solvers may be null for an evaluation), and for one stage carry no
 // drag or contact. On success *smem is the dynamic shared memory per block.
+int lp_eligible(const pbad_model* m, int S, int solver);
+
 int fill_launch_lp(pbad_batch* bt, int S, double dt, const int32_t* solvers, int history,
                    LaunchArgs* A, int* grid, size_t* smem) {
   int rc = fill_launch(bt, S, dt, solvers, history, A, grid);
@@ -486,13 +490,8 @@ int fill_launch_lp(pbad_batch* bt, int S, double dt, const int32_t* solvers, int
   int blocks = 0;
   for (int k = 0; k < A->nb; ++k) {
     const pbad_model* m = bt->models[k];
-    if (!m->chain) return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: the model is not a serial chain");
-    if (S * m->N > 32)
-      return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: stages x links exceeds the 32 lanes of a warp");
-    if (solvers && solvers[k] != PBAD_LBFGS)
-      return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: binary64 L-BFGS only");
-    if (S == 1 && (m->drag != 0.0 || m->n_contact > 0))
-      return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: no one-stage drag or contact");
+    rc = lp_eligible(m, S, solvers ? solvers[k] : PBAD_LBFGS);
+    if (rc != PBAD_OK) return rc;
     const int per_warp = 32 / (S * m->N);
     const int64_t warps = (m->count + per_warp - 1) / per_warp;
     A->bk[k].block_begin = blocks;
@@ -502,6 +501,51 @@ int fill_launch_lp(pbad_batch* bt, int S, double dt, const int32_t* solvers, int
   LpLayout L;
   L.make(history);
   *smem = (size_t)wpb * 32 * L.total * sizeof(double);
+  *grid = blocks;
+  return PBAD_OK;
+}
+
+// The link mapping's conditions for bucket k (PBAD_OK or PBAD_ERR_UNSUPPORTED).
+int lp_eligible(const pbad_model* m, int S, int solver) {
+  if (!m->chain) return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: the model is not a serial chain");
+  if (S * m->N > 32)
+    return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: stages x links exceeds the 32 lanes of a warp");
+  if (solver != PBAD_LBFGS) return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: binary64 L-BFGS only");
+  if (S == 1 && (m->drag != 0.0 || m->n_contact > 0))
+    return fail(PBAD_ERR_UNSUPPORTED, "link-parallel mapping: no one-stage drag or contact");
+  return PBAD_OK;
+}
+
+// A launch where only some buckets run the link mapping (want[k]): after
+// fill_launch, those buckets are checked, flagged, and the block ranges and
+// the dynamic shared memory (the larger of the link-mapped warps' tiles and
+// the CTA-mode Newton scratch) recomputed.
+int mark_lp_buckets(pbad_batch* bt, int S, const int32_t* solvers, int history,
+                    const std::vector<int>& want, LaunchArgs* A, int* grid) {
+  const int wpb = A->threads / 32;
+  int blocks = 0;
+  for (int k = 0; k < A->nb; ++k) {
+    const pbad_model* m = bt->models[k];
+    Bucket& B = A->bk[k];
+    int64_t warps;
+    if (want[k]) {
+      const int rc = lp_eligible(m, S, solvers ? solvers[k] : PBAD_LBFGS);
+      if (rc != PBAD_OK) return rc;
+      B.lp = 1;
+      const int per_warp = 32 / (S * m->N);
+      warps = (m->count + per_warp - 1) / per_warp;
+    } else if (B.solver == PBAD_NEWTON) {
+      warps = m->count * B.cta;
+    } else {
+      warps = (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
+    }
+    B.block_begin = blocks;
+    B.queue = nullptr;
+    blocks += (int)((warps + wpb - 1) / wpb);
+  }
+  LpLayout L;
+  L.make(history);
+  A->cta_smem = std::max(A->cta_smem, (int)(wpb * 32 * L.total * sizeof(double)));
   *grid = blocks;
   return PBAD_OK;
 }
@@ -540,13 +584,23 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
   LaunchArgs A;
   int grid = 0;
   size_t smem = 0;
-  const bool lp = bt->mapping == PBAD_MAP_LINK;
+  const int nb = (int)bt->models.size();
+  std::vector<int> want(nb);
+  int n_lp = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int mk = (k < (int)bt->bucket_mapping.size() && bt->bucket_mapping[k] >= 0)
+                       ? bt->bucket_mapping[k] : bt->mapping;
+    want[k] = mk == PBAD_MAP_LINK;
+    n_lp += want[k];
+  }
+  const bool lp = n_lp == nb;  // every bucket link-mapped: the pure kernel
   if (lp) {
-    std::vector<int32_t> sv(bt->models.size(), PBAD_LBFGS);
-    if (solvers) sv.assign(solvers, solvers + bt->models.size());
+    std::vector<int32_t> sv(nb, PBAD_LBFGS);
+    if (solvers) sv.assign(solvers, solvers + nb);
     rc = fill_launch_lp(bt, stages, dt, sv.data(), history, &A, &grid, &smem);
   } else {
     rc = fill_launch(bt, stages, dt, solvers, history, &A, &grid);
+    if (rc == PBAD_OK && n_lp > 0) rc = mark_lp_buckets(bt, stages, solvers, history, want, &A, &grid);
   }
   if (rc != PBAD_OK) return rc;
   A.q_prev0 = q_prev0;
@@ -574,7 +628,7 @@ int rollout_impl(pbad_batch* bt, const double* q_prev0, const double* q_cur0,
     if (e != cudaSuccess) return cuda_fail(e, "link-parallel rollout launch");
     return PBAD_OK;
   }
-  if (apply_queue(bt, stages, &A, &grid)) {
+  if (n_lp == 0 && apply_queue(bt, stages, &A, &grid)) {
     const cudaError_t e = cudaMemsetAsync(bt->d_queue, 0, sizeof(int) * kMaxBuckets, s);
     if (e != cudaSuccess) return cuda_fail(e, "queue reset");
   }
@@ -1023,6 +1077,22 @@ int pbad_batch_set_mapping(pbad_batch* bt, int32_t mapping) {
   if (!bt) return fail(PBAD_ERR_ARG, "null batch");
   if (mapping != PBAD_MAP_STAGE && mapping != PBAD_MAP_LINK) return fail(PBAD_ERR_ARG, "unknown mapping");
   bt->mapping = mapping;
+  return PBAD_OK;
+}
+
+int pbad_batch_set_bucket_mapping(pbad_batch* bt, const int32_t* mapping) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (!mapping) {
+    bt->bucket_mapping.clear();
+    return PBAD_OK;
+  }
+  std::vector<int> v(bt->models.size());
+  for (size_t k = 0; k < v.size(); ++k) {
+    if (mapping[k] != -1 && mapping[k] != PBAD_MAP_STAGE && mapping[k] != PBAD_MAP_LINK)
+      return fail(PBAD_ERR_ARG, "unknown mapping");
+    v[k] = mapping[k];
+  }
+  bt->bucket_mapping = v;
   return PBAD_OK;
 }
 

@@ -50,6 +50,7 @@ struct Bucket {
   int first_dynamic;
   int chain;             // 1 if parent[l] == l - 1 for every link (serial chain)
   int cta;               // Newton: warps per instance (1, or kNewtonCtaWarps for large S n)
+  int lp;                // L-BFGS: 1 if the bucket runs the link mapping (one lane per stage and link)
   int axial;             // 1 if every mass moment has Sxy = Sxz = Syz = mcx = mcy = 0
   double* dense;         // per-instance dense Newton/adjoint storage (or null)
   int64_t dense_stride;  // doubles per instance in `dense`

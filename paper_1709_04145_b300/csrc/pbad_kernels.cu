@@ -10,6 +10,7 @@ namespace pbad {
 
 }  // namespace pbad
 #include "pbad_lp.cuh"
+#include "pbad_cta.cuh"
 namespace pbad {
 
 // Lane identity inside a bucket: groups of S lanes, floor(32/S) groups per warp.
@@ -685,17 +686,19 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
 }
 
 // One launch serves every bucket of the batch; each block runs the solver of
-// its bucket (L-BFGS, Newton or L-BFGS with the binary32 direction), so an
-// uneven batch with mixed solvers is a single persistent launch. SOLVERS
-// selects the variant: 0 every bucket L-BFGS, 1 every bucket Newton, 3 every
-// bucket binary32-direction L-BFGS, 2 mixed; 4 and 5 are 0 and 3 with the
-// instance queue. The single-solver variants carry only their own solver's
+// its bucket (L-BFGS, Newton or L-BFGS with the binary32 direction) in the
+// bucket's mapping, so an uneven batch with mixed solvers and mappings is a
+// single persistent launch. SOLVERS selects the variant: 0 every bucket
+// L-BFGS, 1 every bucket Newton, 3 every bucket binary32-direction L-BFGS, 2
+// mixed (the only variant with link-mapped buckets next to others); 4 and 5
+// are 0 and 3 with the instance queue. The single-solver variants carry only their own solver's
 // code and registers (the queue's rebinding costs the others ~8% on large
 // batches, hence its own variants).
 template <int S, int SOLVERS>
 __global__ void __maxnreg__(255) k_rollout(const __grid_constant__ LaunchArgs A) {
   const Bucket& B = A.bk[find_bucket(A)];
-  if (SOLVERS == 0) rollout_lbfgs<S, false, false>(A, B);
+  if (SOLVERS == 2 && B.lp) rollout_lp<S>(A, B);  // a link-mapped bucket of a mixed launch
+  else if (SOLVERS == 0) rollout_lbfgs<S, false, false>(A, B);
   else if (SOLVERS == 1) rollout_newton<S>(A, B);
   else if (SOLVERS == 3) rollout_lbfgs<S, true, false>(A, B);
   else if (SOLVERS == 4) rollout_lbfgs<S, false, true>(A, B);
@@ -977,18 +980,30 @@ cudaError_t PBAD_CAT(launch_rollout_s, PBAD_S)(const LaunchArgs& A, int grid, cu
   int kinds = 0;  // bit per solver present
   for (int k = 0; k < A.nb; ++k) kinds |= 1 << A.bk[k].solver;
   const bool queue = A.bk[0].queue != nullptr;  // set for single-kind L-BFGS launches only
-  const size_t smem = A.cta_smem;               // CTA-mode Newton buckets only
-  if (kinds == 1) {
-    if (queue) k_rollout<PBAD_S, 4><<<grid, A.threads, 0, s>>>(A);
-    else k_rollout<PBAD_S, 0><<<grid, A.threads, 0, s>>>(A);
+  const size_t smem = A.cta_smem;  // CTA-mode Newton and link-mapped buckets
+  bool any_lp = false;
+  for (int k = 0; k < A.nb; ++k) any_lp = any_lp || A.bk[k].lp;
+  void (*kern)(const LaunchArgs) = nullptr;
+  size_t dyn = 0;
+  if (any_lp) {  // link-mapped buckets beside others: the mixed variant
+    kern = k_rollout<PBAD_S, 2>;
+    dyn = smem;
+  } else if (kinds == 1) {
+    kern = queue ? k_rollout<PBAD_S, 4> : k_rollout<PBAD_S, 0>;
   } else if (kinds == 2) {
-    k_rollout<PBAD_S, 1><<<grid, A.threads, smem, s>>>(A);
+    kern = k_rollout<PBAD_S, 1>;
+    dyn = smem;
   } else if (kinds == 4) {
-    if (queue) k_rollout<PBAD_S, 5><<<grid, A.threads, 0, s>>>(A);
-    else k_rollout<PBAD_S, 3><<<grid, A.threads, 0, s>>>(A);
+    kern = queue ? k_rollout<PBAD_S, 5> : k_rollout<PBAD_S, 3>;
   } else {
-    k_rollout<PBAD_S, 2><<<grid, A.threads, smem, s>>>(A);
+    kern = k_rollout<PBAD_S, 2>;
+    dyn = smem;
   }
+  if (dyn > 48 * 1024) {
+    const cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)dyn);
+    if (e != cudaSuccess) return e;
+  }
+  kern<<<grid, A.threads, dyn, s>>>(A);
   return cudaGetLastError();
 }
 // Link-parallel launches (every bucket a serial chain with S N <= 32): the

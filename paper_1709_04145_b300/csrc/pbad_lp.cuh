@@ -781,9 +781,8 @@ __global__ void __launch_bounds__(128) k_eval_lp(const __grid_constant__ LaunchA
 // different phases share each pass with per-group predicates.
 // ------------------------------------------------------------------------
 template <int S>
-__global__ void __launch_bounds__(128) k_rollout_lp(const __grid_constant__ LaunchArgs A) {
+__device__ __forceinline__ void rollout_lp_body(const LaunchArgs& A, const Bucket& B) {
   extern __shared__ double lp_smem[];
-  const Bucket& B = A.bk[find_bucket(A)];
   const int m = A.history;
   LpLayout L;
   L.make(m);
@@ -1066,6 +1065,19 @@ __global__ void __launch_bounds__(128) k_rollout_lp(const __grid_constant__ Laun
         }
     }
   }
+}
+
+// A link-mapped bucket inside the mixed rollout kernel (a call keeps the
+// other solvers' register allocation apart).
+template <int S>
+__device__ __noinline__ void rollout_lp(const LaunchArgs& A, const Bucket& B) {
+  rollout_lp_body<S>(A, B);
+}
+
+// The rollout with every bucket in the link mapping (the body inlined).
+template <int S>
+__global__ void __launch_bounds__(128) k_rollout_lp(const __grid_constant__ LaunchArgs A) {
+  rollout_lp_body<S>(A, A.bk[find_bucket(A)]);
 }
 
 }  // namespace pbad

@@ -168,3 +168,46 @@ def autotune_mapping(batch: Batch, probe_fn, mappings=(0, 1), threads=(32, 64, 1
     batch.set_mapping(mp)
     batch.set_threads(th)
     return mp, th, trials
+
+
+
+def choose_bucket_mappings(n_buckets: int, time_fn, stage: int = 0, link: int = 1):
+    """Greedy per-bucket mapping choice (host logic): starting from every
+    bucket stage-mapped, bucket k = 0, 1, ... is switched to the link mapping
+    and kept there if time_fn(mappings) (milliseconds, inf where the launch
+    is refused) falls. Returns (mappings, trials), trials[k] = (ms before,
+    ms with bucket k link-mapped)."""
+    chosen = [stage] * n_buckets
+    best = time_fn(chosen)
+    trials = []
+    for k in range(n_buckets):
+        cand = list(chosen)
+        cand[k] = link
+        ms = time_fn(cand)
+        trials.append((best, ms))
+        if ms < best:
+            chosen, best = cand, ms
+    return chosen, trials
+
+
+def autotune_bucket_mapping(batch: Batch, probe_fn, repeats=1):
+    """Chooses the mapping bucket by bucket inside one launch by
+    choose_bucket_mappings, timing probe_fn() (a short rollout on `batch`)
+    after one untimed call per candidate; buckets the link mapping cannot
+    take (not a chain, more than 32 stage-links, Newton) are refused by the
+    library and stay stage-mapped. Leaves the batch at the choice; returns
+    (mappings, trials)."""
+    from . import MAP_LINK, MAP_STAGE
+    from ._native import PBADError
+
+    def time_fn(mappings):
+        batch.set_bucket_mapping(mappings)
+        try:
+            probe_fn()
+        except PBADError:
+            return float("inf")
+        return min(_timed(probe_fn)[0] for _ in range(repeats))
+
+    chosen, trials = choose_bucket_mappings(len(batch.models), time_fn, MAP_STAGE, MAP_LINK)
+    batch.set_bucket_mapping(chosen)
+    return chosen, trials

@@ -111,8 +111,18 @@ def test_cta_newton_first_iterate_matches_oracle(S, N, dt):
     """One Newton iteration (Gram matrix, factorisation, solve, damping) on
     hinge chains in CTA mode - S n = 200, including the scaling study's
     200-link chains at one stage - from the same initial guess on both
-    sides: the iterate agrees per element (relative 1e-6, floor 1e-6 rad)
-    and so does its |r|."""
+    sides. The iterate agrees per element within the larger of 1e-6
+    max(1, |q|) and the rounding bound of the damped system kappa eps |dx|,
+    kappa the condition number of H + lambda_0 I at the initial guess (the
+    four-stage 50-link Gram matrix J^T J is singular in binary64, so its
+    damped condition number is ~1e12 / lambda_0 ~ 3e13 and the two sides'
+    summation orders differ by up to ~1e-4 in its weak directions). The
+    sharp check is the step's backward error: the GPU's step dx solves the
+    oracle's damped system, |(H + lambda_0 I) dx + g| <= S n eps
+    (|H + lambda_0 I| |dx| + |g|) in the max norm (a Cholesky solve's
+    bound; a step taken at 10 lambda_0 misses it by 5x). The |r| of the
+    iterate is not compared: its second-order part amplifies the weak
+    directions (4.6e-4 relative measured)."""
     import torch
 
     import paper_1709_04145_b300 as P
@@ -122,15 +132,33 @@ def test_cta_newton_first_iterate_matches_oracle(S, N, dt):
     nodes, _ = O.colloc(S)
     qp = q0 + nodes[0] * dt * qd0
     batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
-    out = P.rollout(batch, _t(qp, dev), _t(q0, dev), None, 1, dt, S, P.NEWTON, 8, 1e-12, 1)
+    out = P.rollout(batch, _t(qp, dev), _t(q0, dev), None, 1, dt, S, P.NEWTON, 8, 1e-12, 1,
+                    want_stages=True)
     traj = out["traj_cur"].cpu().numpy().reshape(spec.count, N)
+    stages = out["stages_traj"].cpu().numpy()[0].reshape(spec.count, S * N)
     st = out["step_status"].cpu().numpy()[0]
-    rn = out["step_rnorm"].cpu().numpy()[0]
     for b in (0, 3):
         om = O.OracleModel.from_spec(spec, b)
         ref = om.rollout(S, dt, qp[b], q0[b], np.zeros((1, N)), "lm", 8, 1e-12, 1)
         assert st[b] == ref["step_status"][0], (b, st[b], ref["step_status"][0])
         q = ref["traj_cur"][0]
+        x0 = om.step(S, dt, qp[b], q0[b], np.zeros(N), "lm", 8, 1e-12, 0)[0]
+        x1 = om.step(S, dt, qp[b], q0[b], np.zeros(N), "lm", 8, 1e-12, 1)[0]
+        _, r, _, J = om.eval(S, dt, x0, qp[b], q0[b], np.zeros(N), want_jac=True)
+        if S == 1:
+            H, g = om.hmass(x0.reshape(-1)) / dt**2, r
+        else:
+            H, g = J.T @ J, J.T @ r
+        A = H + 1e-12 * np.diag(H).max() * np.eye(len(H))
+        kappa = np.linalg.cond(A)
+        bound = kappa * np.finfo(float).eps * np.abs(x1 - x0).max()
         err = np.abs(traj[b] - q)
-        assert np.all(err <= 1e-6 * np.maximum(1.0, np.abs(q))), (b, err.max())
-        assert abs(rn[b] - ref["step_rnorm"][0]) <= 1e-4 * ref["step_rnorm"][0], (b, rn[b], ref["step_rnorm"][0])
+        assert np.all(err <= np.maximum(1e-6 * np.maximum(1.0, np.abs(q)), bound)), (b, err.max(),
+                                                                                    bound)
+
+        def backward_error(dx):
+            res = A @ dx + g
+            return np.abs(res).max() / (np.abs(A).sum(1).max() * np.abs(dx).max() + np.abs(g).max())
+        be_bound = S * N * np.finfo(float).eps
+        assert backward_error((x1 - x0).reshape(-1)) <= be_bound  # the oracle took the full step
+        assert backward_error(stages[b] - x0.reshape(-1)) <= be_bound, b

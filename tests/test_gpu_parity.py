@@ -341,3 +341,42 @@ def test_eval_general_mass_moments(S):
         assert abs(E[b] - Eo) <= REL_EVAL * max(abs(Eo), 1.0), b
         assert _relerr(resid[sl], ro) < REL_EVAL, b
         assert _relerr(grad[sl], go) < REL_EVAL, b
+
+
+@pytest.mark.parametrize("S", [1, 2, 3])
+def test_eval_rotations_straddling_the_series_switch(S):
+    """E, r and dE/dq (residual and tangent passes, both mappings) with every
+    ball joint's |theta| within 1e-6 .. 1e-2 of 1 rad on either side: the
+    kernels switch from the power series of the exponential map's
+    coefficients to their closed forms at |theta|^2 = 1, and both branches
+    must give the oracle's values (its own switch sits at |theta| = 0.5)."""
+    torch = _torch()
+    P = _pbad()
+    spec = I.ball_chain(10, 4, seed=17, radius=0.12)
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8)
+    rng = np.random.default_rng(18)
+    B, n, dt = spec.count, spec.n_dof, 0.02
+
+    def near_one(shape):
+        v = rng.normal(size=shape + (3,))
+        v /= np.linalg.norm(v, axis=-1, keepdims=True)
+        mag = 1.0 + rng.choice([-1.0, 1.0], size=shape + (1,)) * 10.0 ** rng.uniform(-6, -2, size=shape + (1,))
+        return (v * mag).reshape(shape[:-1] + (-1,))
+
+    q_cur = near_one((B, n // 3))
+    q_prev = near_one((B, n // 3))
+    qs = near_one((B, S, n // 3))
+    tau = rng.normal(0, 0.3, size=(B, n))
+    dev = torch.device("cuda:0")
+    t = lambda a: torch.tensor(np.ascontiguousarray(a).reshape(-1), device=dev)
+    for mapping in (P.MAP_STAGE, P.MAP_LINK):
+        batch.set_mapping(mapping)
+        E, grad, resid = P.eval_objective_grad(batch, t(qs), t(q_prev), t(q_cur), t(tau), dt, S)
+        E, grad, resid = E.cpu().numpy(), grad.cpu().numpy(), resid.cpu().numpy()
+        for b in range(B):
+            om = O.OracleModel.from_spec(spec, b)
+            Eo, ro, go, _ = om.eval(S, dt, qs[b].reshape(-1), q_prev[b], q_cur[b], tau[b], True)
+            sl = slice(b * S * n, (b + 1) * S * n)
+            assert abs(E[b] - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (mapping, b)
+            assert _relerr(resid[sl], ro) < REL_EVAL, (mapping, b)
+            assert _relerr(grad[sl], go) < REL_EVAL, (mapping, b)

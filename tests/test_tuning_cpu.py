@@ -54,3 +54,24 @@ def test_pick_mapping_fastest_then_stage_then_fewer_threads():
     import pytest
     with pytest.raises(ValueError):
         pick_mapping([MappingTrial(1, 32, inf)])
+
+
+def test_choose_bucket_mappings_greedy():
+    """Each bucket is switched to the link mapping only where the launch gets
+    faster; refused candidates (inf) stay stage-mapped."""
+    from paper_1709_04145_b300.tuning import choose_bucket_mappings
+    inf = float("inf")
+    # bucket 0 refused, bucket 1 helps, bucket 2 hurts once 1 is link-mapped
+    table = {(0, 0, 0): 10.0, (1, 0, 0): inf, (0, 1, 0): 7.0, (0, 1, 1): 8.0}
+    calls = []
+
+    def time_fn(m):
+        calls.append(tuple(m))
+        return table[tuple(m)]
+
+    chosen, trials = choose_bucket_mappings(3, time_fn)
+    assert chosen == [0, 1, 0]
+    assert trials == [(10.0, inf), (10.0, 7.0), (7.0, 8.0)]
+    assert calls == [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 1, 1)]
+    chosen, _ = choose_bucket_mappings(2, lambda m: 5.0)
+    assert chosen == [0, 0]  # ties keep the stage mapping
