@@ -47,14 +47,14 @@ COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 # traffic null until the kernel is captured again.
 ROLLOUT_TRAFFIC = {
     # link mapping, 3 stages, 10 links: 4096 ball chains x 100 steps, five launches of
-    # k_rollout_lp<3>: 50.45 MB read + 17.97 MB written over 5 x 56,195,059 evaluations
-    (1, 3, 10): ("79966d603667746e4bbee43847db3e3e02c098f6", 0.24351),
+    # k_rollout_lp<3>: 50.77 MB read + 15.93 MB written over 5 x 56,195,059 evaluations
+    (1, 3, 10): ("de3bdab5512f09857b31510697447b791bd7b1af", 0.23739),
 }
 
 
 # the headers k_rollout_lp's device code is compiled from (its body, the
 # per-lane passes, the launch arguments, the model layout, double-float)
-ROLLOUT_KERNEL_SOURCES = ("pbad_device.cuh", "pbad_df64.cuh", "pbad_kernels.cuh", "pbad_lp.cuh")
+ROLLOUT_KERNEL_SOURCES = ("pbad_device.cuh", "pbad_df64.cuh", "pbad_launch.cuh", "pbad_lp.cuh")
 
 
 def csrc_hash(files=ROLLOUT_KERNEL_SOURCES) -> str:
@@ -174,7 +174,7 @@ def parse():
                    help="add a step-size sweep of both solvers (ball and hinge chains, dt 0.001-0.128)")
     p.add_argument("--scaling-steps", type=int, default=50,
                    help="steps per rollout of the hinge-chain scaling study (0 = skip)")
-    p.add_argument("--scaling-budget", type=float, default=10.0,
+    p.add_argument("--scaling-budget", type=float, default=6.0,
                    help="seconds per (links, solver) row of the scaling study: fewer steps are "
                         "run when a one-step probe says the requested ones would take longer")
     p.add_argument("--scaling-links", type=int, nargs="+", default=[25, 50, 100, 200])
@@ -500,6 +500,10 @@ def measure_companions(P, args, dev):
                 continue  # the headline itself
             run = lambda T_: P.rollout(batch, qp, qc, None, T_, dt, S, sv, m, args.tol, mi,
                                        want_traj=False)
+            cta = None
+            if sv == P.NEWTON:  # one warp or one CTA per instance, by a two-step probe
+                from paper_1709_04145_b300.tuning import autotune_newton_cta
+                cta = autotune_newton_cta(batch, lambda: run(2), S)
             run(2)
             ms, out = _timed(lambda: run(T))
             it = out["iters"].float().mean().item() / T
@@ -509,6 +513,11 @@ def measure_companions(P, args, dev):
                 "max_iter_per_step": mi, "ms": ms,
                 "value": spec.count * spec.n_links * T / (ms / 1e3), "unit": UNIT,
                 "iters_per_step": it, "step_outcomes": step_outcomes(out)}
+            if cta is not None:
+                rows[f"{name}_radius{radius}"]["newton_cta_min"] = {
+                    "chosen": cta[0], "two_step_ms": {str(k): v for k, v in cta[1].items()},
+                    "rule": "S n >= threshold: one CTA of four warps per instance; 4097: "
+                            "one warp per instance"}
         del batch
         torch.cuda.empty_cache()
     return rows
@@ -536,6 +545,12 @@ def measure_adjoint(P, args, dev):
     target = t(np.random.default_rng(w["target_seed"]).normal(0, 0.3, (spec.count, 3)))
     kw = dict(dt=w["dt"], stages=S, solver=P.NEWTON, tol=w["tol"], max_iter=100,
               checkpoint_every=w["checkpoint_every"])
+    # one warp or one CTA per instance for the forward solves, by a one-step probe
+    from paper_1709_04145_b300.tuning import autotune_newton_cta
+    qp1, qc1 = _state_tensors(P, [(w["q0"], w["qd0"])], S, w["dt"], dev)
+    tau1 = tt[:1].detach().reshape(-1).contiguous()
+    cta = autotune_newton_cta(batch, lambda: P.rollout(batch, qp1, qc1, tau1, 1, w["dt"], S, P.NEWTON,
+                                                       8, w["tol"], 100, want_traj=False), S)
     ev = lambda: torch.cuda.Event(enable_timing=True)
     # warm-up: the first forward and adjoint launches in a process load their
     # kernels and the allocator's blocks (several seconds, once)
@@ -562,6 +577,7 @@ def measure_adjoint(P, args, dev):
     adjc = adj.cpu().numpy()
     return {"fwd_ms": fwd, "fwd_adjoint_ms": a.elapsed_time(b), "steps": steps,
             "workload_steps": 64, "instances": spec.count,
+            "newton_cta_min": {"chosen": cta[0], "one_step_ms": {str(k): v for k, v in cta[1].items()}},
             "all_steps_converged_fraction": float((stc == 0).mean()),
             "gradient_valid_fraction": float(np.isin(adjc, [0, 5]).mean()),
             "note": "gradients of instances with an unsolved step (or a singular adjoint "
@@ -593,7 +609,8 @@ def measure_uneven(P, args, dev):
     """Uneven batch in one persistent launch: 1024 humanoid trees (Newton),
     1024 chains of 50 hinge rods and 2048 chains of 5 (L-BFGS m = 8), dt =
     0.05, two stages, torques N(0, 0.1^2). Threads per block autotuned over
-    32/64/128 on one step; then one rollout of args.uneven_steps steps."""
+    32/64/128 on one step (near-ties to the smaller block: tuning.pick_threads)
+    and the mapping per bucket; then one rollout of args.uneven_steps steps."""
     import numpy as np
     import torch
     from paper_1709_04145_b300 import inputs as I
@@ -611,9 +628,9 @@ def measure_uneven(P, args, dev):
     for threads in (32, 64, 128):
         batch.set_threads(threads)
         tuned[threads] = _timed(lambda: run(1))[0]
-    best = min(tuned, key=tuned.get)
+    from paper_1709_04145_b300.tuning import autotune_bucket_mapping, pick_threads
+    best = pick_threads(tuned)
     batch.set_threads(best)
-    from paper_1709_04145_b300.tuning import autotune_bucket_mapping
     mapping_names = {P.MAP_STAGE: "stage", P.MAP_LINK: "link"}
     bmap, btrials = autotune_bucket_mapping(batch, lambda: run(1))
     ms, out = _timed(lambda: run(T))
@@ -652,6 +669,10 @@ def measure_uneven(P, args, dev):
     run_c = lambda steps: P.rollout(batch, qp, qc, tau[:steps].reshape(-1).contiguous(), steps, dt,
                                     S, chosen, m, u["tol"], args.max_iter_uneven, want_traj=False)
     bmap_c, _ = autotune_bucket_mapping(batch, lambda: run_c(1))
+    cta_c = None
+    if P.NEWTON in chosen:
+        from paper_1709_04145_b300.tuning import autotune_newton_cta
+        cta_c = autotune_newton_cta(batch, lambda: run_c(1), S)
     ms_c, out_c = _timed(lambda: run_c(T))
     st_c = out_c["status"].cpu().numpy()
     names = {P.LBFGS: "lbfgs", P.NEWTON: "newton"}
@@ -661,6 +682,8 @@ def measure_uneven(P, args, dev):
         "probe_wall_s": probe_s,
         "chosen": [names[c] for c in chosen],
         "bucket_mapping": [mapping_names[x] for x in bmap_c],
+        "newton_cta_min": None if cta_c is None else
+        {"chosen": cta_c[0], "one_step_ms": {str(k): v for k, v in cta_c[1].items()}},
         "value": link_steps / (ms_c / 1e3), "ms": ms_c,
         "buckets": [{"model": spec.name,
                      "probe": {names[r.solver]: {"ms": r.ms, "converged_fraction": r.converged / r.total}
@@ -874,7 +897,8 @@ def measure_scaling(P, args, dev):
     per iteration). Each (N, solver) runs args.scaling_steps steps forward
     in one launch, fewer when a one-step probe says they would take more
     than args.scaling_budget seconds (the row says how many), and a forward
-    + adjoint pass (end-state loss) over the first min(steps, 8) steps."""
+    + adjoint pass (end-state loss) over the first min(steps, 8) steps (fewer
+    when their forward alone would exceed half the budget)."""
     import numpy as np
     import torch
     from paper_1709_04145_b300 import inputs as I
@@ -895,7 +919,9 @@ def measure_scaling(P, args, dev):
             ms1, _ = _timed(lambda: run(1))
             T = int(max(1, min(args.scaling_steps, args.scaling_budget * 1e3 // max(ms1, 1e-3))))
             ms, out = _timed(lambda: run(T))
-            Ta = min(T, 8)
+            # the adjoint pass over up to 8 steps, fewer where their forward
+            # alone would take more than half the row's budget
+            Ta = max(1, min(T, 8, int(0.5 * args.scaling_budget * 1e3 // max(ms1, 1e-3))))
             tau = torch.zeros((Ta, batch.D), dtype=torch.float64, device=dev)
 
             def fwd_adj():

@@ -205,6 +205,16 @@ PBAD_API int pbad_batch_set_threads(pbad_batch* batch, int32_t threads);
 #define PBAD_MAP_LINK 1
 PBAD_API int pbad_batch_set_mapping(pbad_batch* batch, int32_t mapping);
 
+/* Newton (LM) buckets whose S n (stages x DOFs) is at least min_sn (and at
+ * most 4096) run one CTA of four warps per instance: the warps split the
+ * Jacobian columns and the CTA forms the Gram matrix and the Cholesky
+ * factor together; smaller systems run one warp per instance. Default 128;
+ * min_sn = 4097 keeps every bucket on one warp per instance. The batch's
+ * workspace grows (cudaFree of the old one waits for the device) where a
+ * bucket needs a CTA's lanes it was not created with. Errors: PBAD_ERR_ARG
+ * (null batch, min_sn outside 1..4097), PBAD_ERR_ALLOC, PBAD_ERR_CUDA. */
+PBAD_API int pbad_batch_set_newton_cta_min(pbad_batch* batch, int32_t min_sn);
+
 /* The damped Gauss-Newton system of one LM iteration (Section 5, LM with
  * J^T J), batched, on its own: for each instance b of count,
  *   H_b = J_b^T J_b,  L_b L_b^T = H_b + lambda I (Cholesky),

@@ -214,6 +214,12 @@ class Batch:
         check(lib().pbad_batch_set_bucket_mapping(self._h, _iptr(arr)), "pbad_batch_set_bucket_mapping")
         self.bucket_mapping = [int(x) for x in arr]
 
+    def set_newton_cta_min(self, min_sn: int):
+        """Newton buckets with stages x DOFs >= min_sn run one CTA of four
+        warps per instance (default 128; 4097: never)."""
+        check(lib().pbad_batch_set_newton_cta_min(self._h, int(min_sn)),
+              "pbad_batch_set_newton_cta_min")
+
     def set_precision(self, precision: int):
         """Arithmetic of eval_objective_grad's residual pass: PRECISION_F64
         (default) or PRECISION_DF64 (double-float after the joint rotations;

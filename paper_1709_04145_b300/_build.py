@@ -10,7 +10,7 @@ CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libpbad.so")
 STAGE_COUNTS = (1, 2, 3, 4, 5)  # pbad_kernels.cu is compiled once per stage count
 SOURCES = ["pbad_kernels.cu", "pbad_capi.cu", "pbad_static.cu", "pbad_dense.cu"]
-HEADERS = ["pbad_device.cuh", "pbad_kernels.cuh", "pbad_lp.cuh", "pbad_df64.cuh", "pbad_cta.cuh"]
+HEADERS = ["pbad_device.cuh", "pbad_kernels.cuh", "pbad_lp.cuh", "pbad_df64.cuh", "pbad_cta.cuh", "pbad_launch.cuh"]
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-O3", "-lineinfo", "-std=c++17",
          "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
@@ -47,10 +47,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if any(rcs):
         raise RuntimeError(f"nvcc failed: {rcs}")
     objs = [o for o, _ in jobs]
-    cmd = [NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", LIB, *objs]
+    tmp = LIB + ".tmp"  # linked aside, then renamed over the library in one step
+    cmd = [NVCC, "-gencode", "arch=compute_103a,code=sm_103a", "-shared", "-o", tmp, *objs]
     if verbose:
         print(" ".join(cmd))
     subprocess.check_call(cmd)
+    os.replace(tmp, LIB)
     for o in objs:
         os.remove(o)
     return LIB

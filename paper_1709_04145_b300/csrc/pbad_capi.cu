@@ -156,6 +156,7 @@ struct pbad_batch {
   int mapping = PBAD_MAP_STAGE;  // instance-to-lane mapping of the L-BFGS and eval kernels
   std::vector<int> bucket_mapping;  // per bucket for steps and rollouts (-1: the batch's mapping)
   int precision = PBAD_PRECISION_F64;  // arithmetic of pbad_eval_objective_grad's residual pass
+  int newton_cta_min = kNewtonCtaMin;  // Newton buckets with S n at least this run a CTA per instance
 };
 
 namespace {
@@ -363,7 +364,7 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
   if (!all_warp)
     for (int k = 0; k < (int)bt->models.size(); ++k) {
       const int sn = S * bt->models[k]->n;
-      if (solvers && solvers[k] == PBAD_NEWTON && sn >= kNewtonCtaMin && sn <= kNewtonCtaMaxSn)
+      if (solvers && solvers[k] == PBAD_NEWTON && sn >= bt->newton_cta_min && sn <= kNewtonCtaMaxSn)
         max_cta_sn = std::max(max_cta_sn, sn);
     }
   if (max_cta_sn > 0) A->threads = 32 * kNewtonCtaWarps;
@@ -411,7 +412,7 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.c_d2 = m->c_d2;
     const bool warp_map = all_warp || B.solver == PBAD_NEWTON;
     const int sn = S * m->n;
-    B.cta = (!all_warp && B.solver == PBAD_NEWTON && sn >= kNewtonCtaMin && sn <= kNewtonCtaMaxSn)
+    B.cta = (!all_warp && B.solver == PBAD_NEWTON && sn >= bt->newton_cta_min && sn <= kNewtonCtaMaxSn)
                 ? kNewtonCtaWarps : 1;
     const int64_t warps = warp_map ? m->count * B.cta
                                    : (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
@@ -548,6 +549,15 @@ int mark_lp_buckets(pbad_batch* bt, int S, const int32_t* solvers, int history,
   A->cta_smem = std::max(A->cta_smem, (int)(wpb * 32 * L.total * sizeof(double)));
   *grid = blocks;
   return PBAD_OK;
+}
+
+// Workspace lanes a Newton bucket needs: one warp per instance, or one CTA
+// of kNewtonCtaWarps warps when S n can reach cta_min (warps rounded up to a
+// multiple of 12 so that every block size of 1..4 warps launches whole
+// blocks inside the allocation).
+int64_t newton_lanes(const pbad_model* m, int max_stages, int cta_min) {
+  const int64_t per = max_stages * m->n >= cta_min ? kNewtonCtaWarps : 1;
+  return ((m->count * per + 11) / 12) * 12 * 32;
 }
 
 int check_common(pbad_batch* bt, int32_t stages, double dt) {
@@ -855,10 +865,7 @@ int pbad_batch_create(int32_t n_models, pbad_model* const* models, int32_t max_s
       if (l > lanes) lanes = l;
     }
     if (flags & PBAD_BATCH_NEWTON) {
-      // one warp per instance, or one CTA of kNewtonCtaWarps when S n is large
-      const int64_t per = max_stages * m->n >= kNewtonCtaMin ? kNewtonCtaWarps : 1;
-      const int64_t l = ((m->count * per + 11) / 12) * 12 * 32;
-      if (l > lanes) lanes = l;
+      lanes = std::max(lanes, newton_lanes(m, max_stages, kNewtonCtaMin));
       DenseLayout DL;
       DL.make(max_stages * m->n);
       bt->dense_off.push_back(bt->dense_doubles);
@@ -1093,6 +1100,51 @@ int pbad_batch_set_bucket_mapping(pbad_batch* bt, const int32_t* mapping) {
     v[k] = mapping[k];
   }
   bt->bucket_mapping = v;
+  return PBAD_OK;
+}
+
+int pbad_batch_set_newton_cta_min(pbad_batch* bt, int32_t min_sn) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (min_sn < 1 || min_sn > kNewtonCtaMaxSn + 1) return fail(PBAD_ERR_ARG, "min_sn out of range");
+  if (!(bt->flags & PBAD_BATCH_NEWTON)) {
+    bt->newton_cta_min = min_sn;
+    return PBAD_OK;
+  }
+  // grow the workspace where a bucket now needs a CTA's lanes per instance
+  const int nb = (int)bt->models.size();
+  std::vector<int64_t> lanes(bt->lanes);
+  bool grow = false;
+  for (int k = 0; k < nb; ++k) {
+    const int64_t need = newton_lanes(bt->models[k], bt->max_stages, min_sn);
+    if (need > lanes[k]) {
+      lanes[k] = need;
+      grow = true;
+    }
+  }
+  if (grow) {
+    std::vector<size_t> off(nb);
+    size_t ws = 0;
+    for (int k = 0; k < nb; ++k) {
+      off[k] = ws;
+      ws += (size_t)lanes[k] * bt->lane_doubles[k];
+    }
+    DeviceGuard dg(bt->device);
+    double* d = nullptr;
+    cudaError_t e = cudaMalloc(&d, sizeof(double) * ws);
+    if (e != cudaSuccess)
+      return fail(PBAD_ERR_ALLOC, std::string("workspace cudaMalloc: ") + cudaGetErrorString(e));
+    e = cudaMemset(d, 0, sizeof(double) * ws);
+    if (e != cudaSuccess) {
+      cudaFree(d);
+      return cuda_fail(e, "cudaMemset");
+    }
+    cudaFree(bt->d_ws);  // waits for the launches that still use it
+    bt->d_ws = d;
+    bt->ws_doubles = ws;
+    bt->ws_off = off;
+    bt->lanes = lanes;
+  }
+  bt->newton_cta_min = min_sn;
   return PBAD_OK;
 }
 

@@ -22,7 +22,7 @@
 // model constants of its link, the torques and the outputs.
 #pragma once
 #include "pbad_df64.cuh"
-#include "pbad_kernels.cuh"
+#include "pbad_launch.cuh"
 
 namespace pbad {
 

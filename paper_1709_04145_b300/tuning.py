@@ -147,6 +147,18 @@ def pick_mapping(trials):
     return best.mapping, best.threads
 
 
+def pick_threads(times, rel_tol: float = 0.01) -> int:
+    """Block size from {threads: ms} of a short probe: the smallest block
+    within rel_tol of the fastest. A short probe cannot see the tail of a
+    long rollout, where a block holds its SM slot until its slowest warp
+    is done, so near-ties go to the smaller block."""
+    finite = {t: ms for t, ms in times.items() if np.isfinite(ms)}
+    if not finite:
+        raise ValueError("no block size served the probe")
+    best = min(finite.values())
+    return min(t for t, ms in finite.items() if ms <= best * (1.0 + rel_tol))
+
+
 def autotune_mapping(batch: Batch, probe_fn, mappings=(0, 1), threads=(32, 64, 128), repeats=1):
     """Times probe_fn() (a short rollout of the workload on `batch`) under
     every mapping and block size, after one untimed call of each, and leaves
@@ -211,3 +223,27 @@ def autotune_bucket_mapping(batch: Batch, probe_fn, repeats=1):
     chosen, trials = choose_bucket_mappings(len(batch.models), time_fn, MAP_STAGE, MAP_LINK)
     batch.set_bucket_mapping(chosen)
     return chosen, trials
+
+
+def newton_cta_candidates(sizes):
+    """Thresholds of the Newton CTA mode worth timing for buckets of the
+    given S n (host logic): 4097 (every bucket one warp per instance) and
+    each distinct size up to 4096, which puts the buckets at least that
+    large in CTA mode."""
+    return [4097] + sorted({int(s) for s in sizes if 1 <= int(s) <= 4096}, reverse=True)
+
+
+def autotune_newton_cta(batch: Batch, probe_fn, stages: int, repeats=1):
+    """Times probe_fn() (a short Newton rollout on `batch`) at each threshold
+    of newton_cta_candidates over the batch's buckets (S n at `stages`),
+    after one untimed call each, and leaves the batch at the fastest.
+    Returns (threshold, {threshold: ms})."""
+    sizes = [stages * m.n_dof for m in batch.models]
+    trials = {}
+    for t in newton_cta_candidates(sizes):
+        batch.set_newton_cta_min(t)
+        probe_fn()
+        trials[t] = min(_timed(probe_fn)[0] for _ in range(repeats))
+    best = min(trials, key=trials.get)
+    batch.set_newton_cta_min(best)
+    return best, trials

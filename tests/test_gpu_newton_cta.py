@@ -162,3 +162,51 @@ def test_cta_newton_first_iterate_matches_oracle(S, N, dt):
         be_bound = S * N * np.finfo(float).eps
         assert backward_error((x1 - x0).reshape(-1)) <= be_bound  # the oracle took the full step
         assert backward_error(stages[b] - x0.reshape(-1)) <= be_bound, b
+
+
+def test_cta_threshold_moves_small_systems_to_cta_mode():
+    """pbad_batch_set_newton_cta_min: ten-link ball chains at three stages
+    (S n = 90, one warp per instance by default) in CTA mode after the
+    threshold drops to 64 (the batch's workspace grows for it): the same
+    statuses as one warp per instance and as the oracle, converged steps
+    equal to the oracle's per element to 1e-6 max(1, |q|); raising the
+    threshold to 4097 puts the batch back on one warp per instance, bit for
+    bit."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    dev = torch.device("cuda:0")
+    S, dt, T, tol = 3, 0.02, 4, 1e-8
+    spec = I.ball_chain(13, 10, seed=8, radius=0.15)
+    q0, qd0 = I.random_state(spec, 9, pose_scale=0.3, vel_sigma=0.3)
+    nodes, _ = O.colloc(S)
+    qp = q0 + nodes[0] * dt * qd0
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    run = lambda: {k: v.cpu().numpy() for k, v in
+                   P.rollout(batch, _t(qp, dev), _t(q0, dev), None, T, dt, S, P.NEWTON, 8, tol,
+                             100).items() if hasattr(v, "cpu")}
+    warp = run()
+    batch.set_newton_cta_min(64)
+    cta = run()
+    batch.set_newton_cta_min(4097)
+    warp2 = run()
+    for key in ("traj_cur", "step_status", "iters"):
+        assert np.array_equal(warp[key], warp2[key]), key
+    n = spec.n_dof
+    compared = 0
+    for b in (0, 6, 12):
+        om = O.OracleModel.from_spec(spec, b)
+        ref = om.rollout(S, dt, qp[b], q0[b], np.zeros((T, n)), "lm", 8, tol, 100)
+        for k in range(T):
+            assert cta["step_status"][k, b] == ref["step_status"][k] == warp["step_status"][k, b]
+            if ref["step_status"][k] != 0:
+                break
+            q = ref["traj_cur"][k]
+            for res in (cta, warp):
+                err = np.abs(res["traj_cur"][k, b * n:(b + 1) * n] - q)
+                assert np.all(err <= 1e-6 * np.maximum(1.0, np.abs(q))), (b, k, err.max())
+            compared += 1
+    assert compared >= 6
+    from paper_1709_04145_b300._native import PBADError
+    with pytest.raises(PBADError):
+        batch.set_newton_cta_min(0)

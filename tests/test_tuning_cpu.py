@@ -75,3 +75,17 @@ def test_choose_bucket_mappings_greedy():
     assert calls == [(0, 0, 0), (1, 0, 0), (0, 1, 0), (0, 1, 1)]
     chosen, _ = choose_bucket_mappings(2, lambda m: 5.0)
     assert chosen == [0, 0]  # ties keep the stage mapping
+
+
+def test_newton_cta_candidates():
+    from paper_1709_04145_b300.tuning import newton_cta_candidates
+    assert newton_cta_candidates([68, 90, 68]) == [4097, 90, 68]
+    assert newton_cta_candidates([5000, 800]) == [4097, 800]  # above 4096: never CTA
+    assert newton_cta_candidates([]) == [4097]
+
+
+def test_pick_threads_prefers_small_blocks_on_near_ties():
+    from paper_1709_04145_b300.tuning import pick_threads
+    assert pick_threads({32: 391.0, 64: 391.7, 128: 388.4}) == 32  # within 1%
+    assert pick_threads({32: 400.0, 64: 391.7, 128: 380.0}) == 128
+    assert pick_threads({32: float("inf"), 64: 10.0, 128: 10.05}) == 64
