@@ -87,33 +87,86 @@ __device__ inline void syrk(const double* Jc, double* H, int Sn, double* sa, dou
   __syncthreads();
 }
 
-// Cholesky of H + lambda I (left-looking, one column per pass: the rows
-// below the diagonal by threads, reading column k of L contiguously), then
+// Cholesky of H + lambda I, blocked left-looking by panels of kTile
+// columns: each panel is first updated by the columns to its left as
+// kTile x kTile tiles staged through shared memory (sa, sc; each thread a
+// 4 x 8 register block, the rows of one column of the column-major factor
+// read contiguously), then factored column by column within itself. Then
 // dl = -(H + lambda I)^-1 gg by forward and back substitution. Returns false
 // (on every thread) if a pivot is not positive. vec: Sn doubles of shared
-// memory, red: reduction scratch.
+// memory, red: reduction scratch. blockDim.x must be 128.
 __device__ inline bool factor_solve(const double* H, double* A, const double* gg, double* dl, int Sn,
-                             double lambda, double* vec, double* red) {
+                             double lambda, double* vec, double* red, double* sa, double* sc) {
   const int tid = threadIdx.x, nth = blockDim.x;
+  const int ty = tid >> 3, tx = tid & 7;
   __shared__ double s_piv;
-  for (int j = 0; j < Sn; ++j) {
-    // row j of L (columns 0..j-1) into shared memory
-    for (int k = tid; k < j; k += nth) vec[k] = A[(int64_t)k * Sn + j];
-    __syncthreads();
-    for (int r = j + tid; r < Sn; r += nth) {
-      double t = H[(int64_t)j * Sn + r];  // = H[r][j] (symmetric), coalesced
-      if (r == j) t += lambda;
-      for (int k = 0; k < j; ++k) t = fma(-A[(int64_t)k * Sn + r], vec[k], t);
-      if (r == j) s_piv = t;
-      A[(int64_t)j * Sn + r] = t;
+  for (int j0 = 0; j0 < Sn; j0 += kTile) {
+    const int jw = min(kTile, Sn - j0);
+    // the panel's columns of H + lambda I (rows from the diagonal down)
+    for (int c = 0; c < jw; ++c) {
+      const int j = j0 + c;
+      for (int r = j + tid; r < Sn; r += nth)
+        A[(int64_t)j * Sn + r] = H[(int64_t)j * Sn + r] + (r == j ? lambda : 0.0);
     }
-    __syncthreads();
-    const double d = s_piv;
-    if (!(d > 0.0)) return false;  // CTA-uniform
-    const double ljj = sqrt(d), inv = 1.0 / ljj;
-    for (int r = j + 1 + tid; r < Sn; r += nth) A[(int64_t)j * Sn + r] *= inv;
-    if (tid == 0) A[(int64_t)j * Sn + j] = ljj;
-    __syncthreads();
+    // minus L[r][0:j0] L[j0 + c][0:j0]^T for the rows r >= j0
+    if (j0 > 0) {
+      for (int r0 = j0; r0 < Sn; r0 += kTile) {
+        double acc[4][8];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) acc[i][q] = 0.0;
+        for (int k0 = 0; k0 < j0; k0 += kChunk) {
+          __syncthreads();
+          for (int e = tid; e < kTile * kChunk; e += nth) {
+            const int k = e / kTile, row = e - k * kTile;  // rows fastest: contiguous in A
+            const int kk = k0 + k, ra = r0 + row, rc = j0 + row;
+            sa[row * kPad + k] = (ra < Sn && kk < j0) ? A[(int64_t)kk * Sn + ra] : 0.0;
+            sc[row * kPad + k] = (row < jw && kk < j0) ? A[(int64_t)kk * Sn + rc] : 0.0;
+          }
+          __syncthreads();
+#pragma unroll 4
+          for (int k = 0; k < kChunk; ++k) {
+            double av[4], cv[8];
+#pragma unroll
+            for (int i = 0; i < 4; ++i) av[i] = sa[(ty * 4 + i) * kPad + k];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) cv[q] = sc[(tx * 8 + q) * kPad + k];
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+              for (int q = 0; q < 8; ++q) acc[i][q] = fma(av[i], cv[q], acc[i][q]);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int r = r0 + ty * 4 + i, c = tx * 8 + q;
+            if (r < Sn && c < jw && r >= j0 + c) A[(int64_t)(j0 + c) * Sn + r] -= acc[i][q];
+          }
+      }
+      __syncthreads();
+    }
+    // the panel itself, one column per pass (row j of the panel's L in vec)
+    for (int c = 0; c < jw; ++c) {
+      const int j = j0 + c;
+      for (int k = j0 + tid; k < j; k += nth) vec[k - j0] = A[(int64_t)k * Sn + j];
+      __syncthreads();
+      for (int r = j + tid; r < Sn; r += nth) {
+        double t = A[(int64_t)j * Sn + r];
+        for (int k = j0; k < j; ++k) t = fma(-A[(int64_t)k * Sn + r], vec[k - j0], t);
+        if (r == j) s_piv = t;
+        A[(int64_t)j * Sn + r] = t;
+      }
+      __syncthreads();
+      const double d = s_piv;
+      if (!(d > 0.0)) return false;  // CTA-uniform
+      const double ljj = sqrt(d), inv = 1.0 / ljj;
+      for (int r = j + 1 + tid; r < Sn; r += nth) A[(int64_t)j * Sn + r] *= inv;
+      if (tid == 0) A[(int64_t)j * Sn + j] = ljj;
+      __syncthreads();
+    }
   }
   // L y = -gg, column by column
   for (int k = tid; k < Sn; k += nth) vec[k] = -gg[k];

@@ -28,7 +28,8 @@ __global__ void __launch_bounds__(kDenseThreads) k_damped_gram_solve(
   double* vec = red + 32;
   const int64_t b = blockIdx.x, nn = (int64_t)n * n;
   cta::syrk(J + b * nn, H + b * nn, n, sa, sc);
-  const bool ok = cta::factor_solve(H + b * nn, L + b * nn, g + b * n, dl + b * n, n, lambda, vec, red);
+  const bool ok =
+      cta::factor_solve(H + b * nn, L + b * nn, g + b * n, dl + b * n, n, lambda, vec, red, sa, sc);
   if (threadIdx.x == 0) status[b] = ok ? PBAD_CONVERGED : PBAD_CHOL_FAIL;
 }
 }  // namespace

@@ -653,7 +653,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
       bool solved = false;
       while (!solved) {
         const bool f = ncta > 1 ? cta::factor_solve(Dn + DL.H, Dn + DL.A, Dn + DL.gg, Dn + DL.dl,
-                                                   S * n, lambda, s_vec, s_red)
+                                                   S * n, lambda, s_vec, s_red, s_sa, s_sc)
                                : c.factor_solve_warp(Dn, DL, lambda);
         if (f) {
           solved = true;

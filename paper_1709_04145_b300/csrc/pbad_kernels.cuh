@@ -785,19 +785,53 @@ struct Ctx {
         D[DL.gg + a] = D[DL.r + a];
       }
     } else {
-      const int npairs = Sn * (Sn + 1) / 2;
-      for (int pidx = lane; pidx < npairs; pidx += 32) {
-        // pair (a, c), a >= c, row-major over the lower triangle
-        int a = (int)((sqrt(8.0 * pidx + 1.0) - 1.0) * 0.5);
-        while ((a + 1) * (a + 2) / 2 <= pidx) ++a;
-        while (a * (a + 1) / 2 > pidx) --a;
-        const int c = pidx - a * (a + 1) / 2;
-        const double* ja = D + DL.J + (int64_t)a * Sn;
-        const double* jb = D + DL.J + (int64_t)c * Sn;
-        double h = 0.0;
-        for (int rr = 0; rr < Sn; ++rr) h = fma(ja[rr], jb[rr], h);
-        D[DL.H + (int64_t)a * Sn + c] = h;
-        D[DL.H + (int64_t)c * Sn + a] = h;
+      // 4 x 4 blocks of the lower triangle, one block per lane at a time:
+      // each entry is the same in-order dot product over the rows, with a
+      // quarter of the loads of one entry per lane
+      const int nb = (Sn + 3) / 4;
+      const int nblocks = nb * (nb + 1) / 2;
+      const double* J = D + DL.J;
+      for (int q = lane; q < nblocks; q += 32) {
+        // block (bi, bj), bi >= bj, row-major over the lower triangle
+        int bi = (int)((sqrt(8.0 * q + 1.0) - 1.0) * 0.5);
+        while ((bi + 1) * (bi + 2) / 2 <= q) ++bi;
+        while (bi * (bi + 1) / 2 > q) --bi;
+        const int bj = q - bi * (bi + 1) / 2;
+        const int a0 = 4 * bi, c0 = 4 * bj;
+        const double* ja[4];
+        const double* jc[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ja[u] = J + (int64_t)min(a0 + u, Sn - 1) * Sn;  // rows past Sn repeat the last column
+          jc[u] = J + (int64_t)min(c0 + u, Sn - 1) * Sn;
+        }
+        double h[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) h[u][v] = 0.0;
+        for (int rr = 0; rr < Sn; ++rr) {
+          double x[4], y[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            x[u] = ja[u][rr];
+            y[u] = jc[u][rr];
+          }
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) h[u][v] = fma(x[u], y[v], h[u][v]);
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+          for (int v = 0; v < 4; ++v) {
+            const int a = a0 + u, c = c0 + v;
+            if (a < Sn && c <= a) {
+              D[DL.H + (int64_t)a * Sn + c] = h[u][v];
+              D[DL.H + (int64_t)c * Sn + a] = h[u][v];
+            }
+          }
       }
       for (int a = lane; a < Sn; a += 32) {
         const double* ja = D + DL.J + (int64_t)a * Sn;
@@ -818,9 +852,10 @@ struct Ctx {
     return v;
   }
 
-  // Cholesky of H + lambda I into A (lower triangle, row-major) and
-  // dl = -(H + lambda I)^-1 gg. Returns false (on every lane) if a pivot is
-  // not positive.
+  // Cholesky of H + lambda I into A (lower triangle stored column-major:
+  // L[r][c] at A[c Sn + r], so that the lanes' rows of one column are
+  // contiguous) and dl = -(H + lambda I)^-1 gg. Returns false (on every
+  // lane) if a pivot is not positive.
   __device__ __noinline__ bool factor_solve_warp(double* D, const DenseLayout& DL, double lambda) const {
     const int Sn = S * n;
     const int lane = threadIdx.x & 31;
@@ -828,15 +863,15 @@ struct Ctx {
     const double* H = D + DL.H;
     for (int j = 0; j < Sn; ++j) {
       double s = 0.0;
-      for (int k = lane; k < j; k += 32) s = fma(A[(int64_t)j * Sn + k], A[(int64_t)j * Sn + k], s);
+      for (int k = lane; k < j; k += 32) s = fma(A[(int64_t)k * Sn + j], A[(int64_t)k * Sn + j], s);
       s = warp_sum(s);
       const double dj = H[(int64_t)j * Sn + j] + lambda - s;
       if (!(dj > 0.0)) return false;
       const double ljj = sqrt(dj), inv = 1.0 / ljj;
       for (int r = j + 1 + lane; r < Sn; r += 32) {
-        double t = H[(int64_t)r * Sn + j];
-        for (int k = 0; k < j; ++k) t = fma(-A[(int64_t)r * Sn + k], A[(int64_t)j * Sn + k], t);
-        A[(int64_t)r * Sn + j] = t * inv;
+        double t = H[(int64_t)j * Sn + r];  // = H[r][j] (symmetric), contiguous over the lanes
+        for (int k = 0; k < j; ++k) t = fma(-A[(int64_t)k * Sn + r], A[(int64_t)k * Sn + j], t);
+        A[(int64_t)j * Sn + r] = t * inv;
       }
       if (lane == 0) A[(int64_t)j * Sn + j] = ljj;
       __syncwarp();
@@ -844,7 +879,7 @@ struct Ctx {
     double* y = D + DL.dl;
     for (int r = 0; r < Sn; ++r) {
       double s = 0.0;
-      for (int k = lane; k < r; k += 32) s = fma(A[(int64_t)r * Sn + k], y[k], s);
+      for (int k = lane; k < r; k += 32) s = fma(A[(int64_t)k * Sn + r], y[k], s);
       s = warp_sum(s);
       const double v = (-D[DL.gg + r] - s) / A[(int64_t)r * Sn + r];
       __syncwarp();
@@ -853,7 +888,7 @@ struct Ctx {
     }
     for (int r = Sn - 1; r >= 0; --r) {
       double s = 0.0;
-      for (int k = r + 1 + lane; k < Sn; k += 32) s = fma(A[(int64_t)k * Sn + r], y[k], s);
+      for (int k = r + 1 + lane; k < Sn; k += 32) s = fma(A[(int64_t)r * Sn + k], y[k], s);
       s = warp_sum(s);
       const double v = (y[r] - s) / A[(int64_t)r * Sn + r];
       __syncwarp();
