@@ -19,10 +19,13 @@ Comparison rule, step by step for each sampled instance:
     iteration cap (MAX_ITER) it depends on the path the iterates took (a
     25-link chain ended at 3.5e-5 on the GPU and 4.2e-3 in the oracle after
     100 LM iterations) and is not compared;
-  - one exception is counted instead of failed: a step that converges on one
-    side on its last allowed iteration and ends MAX_ITER on the other (the
-    outcome at the iteration cap turns on the rounding of the last
-    iterate); each test bounds how many sampled instances may end so.
+  - two exceptions are counted instead of failed, and each test bounds how
+    many sampled instances may end so: a step that converges on one side on
+    its last allowed iteration and ends MAX_ITER on the other (the outcome
+    at the iteration cap turns on the rounding of the last iterate), and an
+    unsolved step that ends MAX_ITER on one side and in a failed damping
+    loop (LS_FAIL or STALLED) on the other (both unsolved: which stopping
+    rule fires first depends on the path the decorrelated iterates take).
 """
 import numpy as np
 import pytest
@@ -41,7 +44,8 @@ def _compare(name, b, st, rn, traj, ref, tol=TOL, cap=None):
     at the iteration cap on one side only)."""
     conv = 0
     for k in range(len(st)):
-        if st[k] != ref["step_status"][k] and {int(st[k]), int(ref["step_status"][k])} == {0, 1}:
+        pair = {int(st[k]), int(ref["step_status"][k])}
+        if st[k] != ref["step_status"][k] and (pair == {0, 1} or pair in ({1, 2}, {1, 5})):
             assert cap is not None, (name, b, k, st[k], ref["step_status"][k])
             cap.append((name, b, k))
             break
