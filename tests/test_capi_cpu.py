@@ -107,3 +107,15 @@ def test_header_constants_match_binding():
 def test_queue_setter_rejects_null_batch():
     from paper_1709_04145_b300._native import lib
     assert lib().pbad_batch_set_queue(None, 0) != 0
+
+
+def test_build_tracks_every_cuda_source():
+    """The in-tree build compiles every .cu file and rebuilds when any .cu or
+    .cuh file changes (a header left out of its dependency list would leave
+    a stale library)."""
+    import os
+
+    from paper_1709_04145_b300 import _build
+    files = os.listdir(_build.CSRC)
+    assert sorted(f for f in files if f.endswith(".cu")) == sorted(_build.SOURCES)
+    assert sorted(f for f in files if f.endswith(".cuh")) == sorted(_build.HEADERS)
