@@ -513,6 +513,9 @@ def measure_companions(P, args, dev):
                 "max_iter_per_step": mi, "ms": ms,
                 "value": spec.count * spec.n_links * T / (ms / 1e3), "unit": UNIT,
                 "iters_per_step": it, "step_outcomes": step_outcomes(out)}
+            row = rows[f"{name}_radius{radius}"]
+            # the same rate counting only the solved instance-steps
+            row["solved_value"] = row["value"] * row["step_outcomes"]["solved_fraction"]
             if cta is not None:
                 rows[f"{name}_radius{radius}"]["newton_cta_min"] = {
                     "chosen": cta[0], "two_step_ms": {str(k): v for k, v in cta[1].items()},
@@ -1130,6 +1133,7 @@ def run_ours(args):
                          "worst_status_counts": {P.STATUS[k]: int((status == k).sum())
                                                  for k in range(6)},
                          "step_outcomes": step_outcomes(out),
+                         "solved_link_steps_per_s": value * step_outcomes(out)["solved_fraction"],
                          "floor_note": "STALLED = line search failed at |r| <= 1e3 x the binary64 "
                                        "rounding floor of r (solved to rounding)",
                          "iters_per_step": float(iters.mean() / T),
