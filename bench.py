@@ -149,7 +149,7 @@ def parse():
     p.add_argument("--no-e2e", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
-    p.add_argument("--cpu-sample-seconds", type=float, default=15.0)
+    p.add_argument("--cpu-sample-seconds", type=float, default=10.0)
     p.add_argument("--threads", type=int, default=0,
                    help="threads per block (0 = autotune the mapping and 32/64/128 threads on a "
                         "short rollout)")
@@ -174,9 +174,11 @@ def parse():
                    help="add a step-size sweep of both solvers (ball and hinge chains, dt 0.001-0.128)")
     p.add_argument("--scaling-steps", type=int, default=50,
                    help="steps per rollout of the hinge-chain scaling study (0 = skip)")
-    p.add_argument("--scaling-budget", type=float, default=6.0,
+    p.add_argument("--scaling-budget", type=float, default=60.0,
                    help="seconds per (links, solver) row of the scaling study: fewer steps are "
                         "run when a one-step probe says the requested ones would take longer")
+    p.add_argument("--scaling-adjoint-budget", type=float, default=6.0,
+                   help="seconds of forward work per row for its forward + adjoint timing")
     p.add_argument("--scaling-links", type=int, nargs="+", default=[25, 50, 100, 200])
     p.add_argument("--damped-links", type=int, default=200,
                    help="links of the damped-system (Gram + Cholesky) timing, S = 4; 0 skips it")
@@ -901,7 +903,7 @@ def measure_scaling(P, args, dev):
     in one launch, fewer when a one-step probe says they would take more
     than args.scaling_budget seconds (the row says how many), and a forward
     + adjoint pass (end-state loss) over the first min(steps, 8) steps (fewer
-    when their forward alone would exceed half the budget)."""
+    when their forward alone would exceed half of args.scaling_adjoint_budget)."""
     import numpy as np
     import torch
     from paper_1709_04145_b300 import inputs as I
@@ -924,7 +926,7 @@ def measure_scaling(P, args, dev):
             ms, out = _timed(lambda: run(T))
             # the adjoint pass over up to 8 steps, fewer where their forward
             # alone would take more than half the row's budget
-            Ta = max(1, min(T, 8, int(0.5 * args.scaling_budget * 1e3 // max(ms1, 1e-3))))
+            Ta = max(1, min(T, 8, int(0.5 * args.scaling_adjoint_budget * 1e3 // max(ms1, 1e-3))))
             tau = torch.zeros((Ta, batch.D), dtype=torch.float64, device=dev)
 
             def fwd_adj():
@@ -947,7 +949,8 @@ def measure_scaling(P, args, dev):
         del batch
         torch.cuda.empty_cache()
     return {"rows": rows, "dt": 0.1, "stages": 4, "max_iter_per_step": args.max_iter_scaling,
-            "steps_requested": args.scaling_steps, "budget_s_per_row": args.scaling_budget}
+            "steps_requested": args.scaling_steps, "budget_s_per_row": args.scaling_budget,
+            "adjoint_budget_s_per_row": args.scaling_adjoint_budget}
 
 
 def measure_damped_system(P, args, dev, peak_tflops):
