@@ -1,4 +1,4 @@
-"""Solver choice per bucket and time-step sweeps.
+"""Solver choice per bucket, time-step sweeps and mapping autotuners.
 
 The paper compares L-BFGS and LM (Newton) per time step and finds the
 better one depends on the step size and the body (Section 6.1, Fig.
@@ -6,8 +6,13 @@ OPTProf). `choose_solvers` makes that choice for each bucket of a batch
 from a short probe: it runs the bucket alone with each solver over the
 first steps of its own inputs and keeps the solver with the smaller device
 time per converged instance-step. `dt_sweep` reports, for a range of step
-sizes, what each solver achieves on a model. Both only time launches of
-the library; the decision rule itself (`pick`) is plain host logic.
+sizes, what each solver achieves on a model. The mapping autotuners time
+the instance-to-lane mappings and block sizes (`autotune_mapping`), the
+mapping of each bucket inside one launch (`autotune_bucket_mapping`) and
+which Newton buckets run a CTA per instance (`autotune_newton_cta`). All
+of them only time launches of the library; their decision rules (`pick`,
+`pick_mapping`, `pick_threads`, `choose_bucket_mappings`,
+`newton_cta_candidates`) are plain host logic with CPU tests.
 """
 from __future__ import annotations
 
@@ -180,7 +185,6 @@ def autotune_mapping(batch: Batch, probe_fn, mappings=(0, 1), threads=(32, 64, 1
     batch.set_mapping(mp)
     batch.set_threads(th)
     return mp, th, trials
-
 
 
 def choose_bucket_mappings(n_buckets: int, time_fn, stage: int = 0, link: int = 1):
