@@ -147,6 +147,8 @@ def parse():
     p.add_argument("--max-iter", type=int, default=50, help="L-BFGS iteration cap per time step")
     p.add_argument("--tol", type=float, default=1e-8)
     p.add_argument("--no-e2e", action="store_true")
+    p.add_argument("--e2e-steps", type=int, default=5,
+                   help="steps of the end-to-end timing (at most --steps)")
     p.add_argument("--no-cpu-baseline", action="store_true")
     p.add_argument("--no-clocks", action="store_true")
     p.add_argument("--cpu-sample-seconds", type=float, default=10.0)
@@ -1093,7 +1095,8 @@ def run_ours(args):
         out2 = dict(out)
         torch.cuda.synchronize()
         t_e2e = []
-        for k in range(max(args.steps, 1)):
+        e2e_steps = max(1, min(args.steps, args.e2e_steps))
+        for k in range(e2e_steps):
             flush.fill_(float(k))
             e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
             e0.record(cur)
@@ -1112,7 +1115,7 @@ def run_ours(args):
         e2e = {"value": job_throughput(link_steps, world, ms_e), "unit": UNIT,
                "h2d_bytes_per_step": 2 * batch.D * 8,
                "d2h_bytes_per_step": batch.D * 8 + batch.n_instances * 4,
-               "ms_per_step": ms_e}
+               "ms_per_step": ms_e, "steps": e2e_steps}
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
