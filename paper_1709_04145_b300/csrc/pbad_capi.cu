@@ -120,7 +120,7 @@ struct pbad_model {
   double drag = 0.0;  // drag coefficient c of Q_drag (Section 6.2)
   std::vector<int> parent, jtype, dof;
   double g[3] = {0, 0, 0};
-  int* d_topo = nullptr;     // parent[N] | jtype[N] | dof[N] | rest_eye[N]
+  int* d_topo = nullptr;     // parent[N] | jtype[N] | dof[N] | rest_eye[N] | sub_end[N]
   double* d_axis = nullptr;  // [N][3]
   double* d_mm = nullptr;    // [N][10][count]
   double* d_rest = nullptr;  // [N][12][count]
@@ -381,6 +381,7 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     B.jtype = m->d_topo + m->N;
     B.dof = m->d_topo + 2 * m->N;
     B.rest_eye = m->d_topo + 3 * m->N;
+    B.sub_end = m->d_topo + 4 * m->N;
     B.axis = m->d_axis;
     B.mm = m->d_mm;
     B.rest = m->d_rest;
@@ -700,7 +701,23 @@ int pbad_model_create(int32_t n_links, const int32_t* parent, const int32_t* joi
     delete m;
     return fail(PBAD_ERR_CUDA, "cudaSetDevice failed");
   }
-  std::vector<int> topo(4 * n_links);
+  std::vector<int> topo(5 * n_links);
+  // subtree end: link l's descendants are l + 1 .. sub_end[l] - 1 when the
+  // order numbers each subtree contiguously (depth-first), else N
+  std::vector<int> size(n_links, 1);
+  for (int l = n_links - 1; l > 0; --l)
+    if (m->parent[l] >= 0) size[m->parent[l]] += size[l];
+  bool contiguous = true;
+  for (int l = 0; l < n_links && contiguous; ++l)
+    for (int c = l + 1; c < l + size[l]; ++c) {  // every link inside must descend from l
+      int a = c;
+      while (a > l) a = m->parent[a];
+      if (a != l) {
+        contiguous = false;
+        break;
+      }
+    }
+  for (int l = 0; l < n_links; ++l) topo[4 * n_links + l] = contiguous ? l + size[l] : n_links;
   for (int l = 0; l < n_links; ++l) {
     topo[l] = m->parent[l];
     topo[n_links + l] = m->jtype[l];
@@ -1265,6 +1282,7 @@ int fill_launch_single(const pbad_model* m, int S, double dt, double* ws, Launch
   B.jtype = m->d_topo + m->N;
   B.dof = m->d_topo + 2 * m->N;
   B.rest_eye = m->d_topo + 3 * m->N;
+  B.sub_end = m->d_topo + 4 * m->N;
   B.axis = m->d_axis;
   B.mm = m->d_mm;
   B.rest = m->d_rest;

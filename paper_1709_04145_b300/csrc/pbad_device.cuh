@@ -33,6 +33,7 @@ struct Bucket {
   const int* jtype;      // [N] 0 hinge, 1 ball
   const int* dof;        // [N] first DOF of each joint
   const int* rest_eye;   // [N] 1 if every instance's rest rotation is the identity
+  const int* sub_end;    // [N] link l's subtree is l .. sub_end[l] - 1 (N where not contiguous)
   const double* axis;    // [N][3] hinge axes (joint frame)
   const double* mm;      // [N][10][count] mass moments (SoA over instances)
   const double* rest;    // [N][12][count] rest transforms (SoA over instances)

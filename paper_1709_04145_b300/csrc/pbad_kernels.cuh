@@ -545,17 +545,22 @@ struct Ctx {
   // The result, times `scale`, goes to offset `out`. Needs the primal pass's
   // T, G, axes and acc at the same point. Convergent across the warp.
   enum TangentMode { kGrad = 0, kJvp = 1, kGn = 2 };
-  // l_first (warp-uniform): the direction has no component on the DOFs of
-  // links before it, so their twists, seed tangents and wrench tangents are
-  // zero (no link before l_first descends from one at or after it) and the
-  // forward sweep only stores those zeros.
+  // [l_first, l_end) (warp-uniform): the links the direction can move. It
+  // has no component on the DOFs outside that range, and every link it moves
+  // lies in the subtree of one of its joints, numbered inside the range. So
+  // the twists, seed tangents and wrench tangents are zero before l_first
+  // (the forward sweep only stores those zeros) and past l_end, where the
+  // residual tangents are zero too (no link there is an ancestor of a moved
+  // one: ancestors come first); the backward sweep starts at l_end - 1.
   template <int MODE>
-  __device__ __noinline__ void tangent_pass(int dir, int out, double scale, int l_first = 0) const {
+  __device__ __noinline__ void tangent_pass(int dir, int out, double scale, int l_first = 0,
+                                            int l_end = -1) const {
     const Ctx self(*this);
-    self.template tangent_body<MODE>(dir, out, scale, l_first);
+    self.template tangent_body<MODE>(dir, out, scale, l_first, l_end < 0 ? N : l_end);
   }
   template <int MODE>
-  __device__ __forceinline__ void tangent_body(int dir, int out, double scale, int l_first) const {
+  __device__ __forceinline__ void tangent_body(int dir, int out, double scale, int l_first,
+                                               int l_end) const {
     const bool chain = B.chain;
     double V[6] = {0, 0, 0, 0, 0, 0};  // parent twist (kept in registers along a chain)
     for (int l = 0; l < l_first; ++l)
@@ -563,7 +568,9 @@ struct Ctx {
         ws[L.V + 6 * l + k] = 0.0;
         ws[L.accd + 6 * l + k] = 0.0;
       }
-    for (int l = l_first; l < N; ++l) {
+    if (l_end < N)
+      for (int d = B.dof[l_end]; d < n; ++d) ws[out + d] = 0.0;
+    for (int l = l_first; l < l_end; ++l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
       if (!chain) {
         if (p >= 0) {
@@ -639,7 +646,7 @@ struct Ctx {
       for (int k = 0; k < 6; ++k) ws[L.accd + 6 * l + k] = w6[k];
     }
     double carry[6] = {0, 0, 0, 0, 0, 0};
-    for (int l = N - 1; l >= 0; --l) {
+    for (int l = l_end - 1; l >= 0; --l) {
       const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
       double ad[6], T[12];
       for (int k = 0; k < 6; ++k) ad[k] = ws[L.accd + 6 * l + k] + carry[k];
@@ -713,7 +720,7 @@ struct Ctx {
   }
 
   // gradient of Eq. EQHOC: 2 Jr^T r, into gt
-  __device__ __forceinline__ void tangent() const { tangent_pass<kGrad>(L.rt, L.gt, 2.0, 0); }
+  __device__ __forceinline__ void tangent() const { tangent_pass<kGrad>(L.rt, L.gt, 2.0, 0, N); }
 
   // Full evaluation at xt: returns E (group total, identical on the group's
   // lanes); rt = residual of the own stage; gt = dE/dq of the own stage.
@@ -756,19 +763,23 @@ struct Ctx {
     const int Sn = S * n;
     const int rounds = (Sn + R - 1) / R;
     for (int t = 0; t < rounds; ++t) {
+      // the round's columns run DOF-major (the stages of one DOF side by
+      // side), so that one round covers few joints and their subtrees
       const int c = rep + t * R;
       const bool real = c < Sn && rep < R;
       const int cc = real ? c : Sn - 1;  // surplus replicas repeat the last column and discard it
-      const int k = cc / n, e = cc - k * n;
+      const int e = cc / S, k = cc - e * S;
       for (int d = 0; d < n; ++d) ws[L.u + d] = (i == k && d == e) ? 1.0 : 0.0;
-      // the link that owns DOF e; the warp's passes start at the smallest
+      // the link that owns DOF e; the warp's passes cover the smallest such
+      // link up to the end of the largest of their subtrees
       int le = N - 1;
       while (le > 0 && B.dof[le] > e) --le;
+      const int lend = __reduce_max_sync(0xffffffffu, B.sub_end[le]);
       le = __reduce_min_sync(0xffffffffu, le);
-      if (S == 1 && !exact) tangent_pass<kGn>(L.u, L.jc, 1.0, le);
-      else tangent_pass<kJvp>(L.u, L.jc, 1.0, le);
+      if (S == 1 && !exact) tangent_pass<kGn>(L.u, L.jc, 1.0, le, lend);
+      else tangent_pass<kJvp>(L.u, L.jc, 1.0, le, lend);
       if (real)
-        for (int d = 0; d < n; ++d) D[DL.J + (int64_t)c * Sn + i * n + d] = ws[L.jc + d];
+        for (int d = 0; d < n; ++d) D[DL.J + (int64_t)(k * n + e) * Sn + i * n + d] = ws[L.jc + d];
     }
     __syncwarp();
   }
