@@ -47,8 +47,8 @@ COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 # traffic null until the kernel is captured again.
 ROLLOUT_TRAFFIC = {
     # link mapping, 3 stages, 10 links: 4096 ball chains x 100 steps, five launches of
-    # k_rollout_lp<3>: 50.77 MB read + 15.93 MB written over 5 x 56,195,059 evaluations
-    (1, 3, 10): ("de3bdab5512f09857b31510697447b791bd7b1af", 0.23739),
+    # k_rollout_lp<3>: 50.59 MB read + 17.20 MB written over 5 x 56,195,050 evaluations
+    (1, 3, 10): ("0d733459a38bd9d7dddc6f865d386d5fe9b2d9a1", 0.24127),
 }
 
 
