@@ -5,6 +5,7 @@ properties that hold for every instance are checked on all of them."""
 import numpy as np
 import pytest
 
+import parity_bounds as PB
 from oracle import oracle as O
 from paper_1709_04145_b300 import inputs as I
 
@@ -49,10 +50,13 @@ def _check_eval(P, batch, specs, cases, S, dt, per_bucket, seed):
         qp, qc, ta, q_s = cases[k]
         for b in _samples(spec.count, per_bucket, seed + k):
             om = O.OracleModel.from_spec(spec, b)
-            Eo, ro, go, _ = om.eval(S, dt, q_s[b], qp[b], qc[b], ta[b], True)
+            Eo, ro, go, rb, gb = PB.oracle_eval_bounds(om, S, dt, q_s[b], qp[b], qc[b], ta[b])
             assert abs(E[batch.inst_off[k] + b] - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (spec.name, b)
             assert _relerr(resids[k][b].reshape(-1), ro) < REL_EVAL, (spec.name, b)
             assert _relerr(grads[k][b].reshape(-1), go) < REL_EVAL, (spec.name, b)
+            # per element, with the floor from the rounding bound of r
+            assert PB.ratio(resids[k][b], ro, rb) <= 1.0, (spec.name, b)
+            assert PB.ratio(grads[k][b], go, gb) <= 1.0, (spec.name, b)
 
 
 def test_ball_chains_4096_eval_and_first_step():

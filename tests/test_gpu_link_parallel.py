@@ -5,6 +5,7 @@ several groups per warp, and the requests it does not serve."""
 import numpy as np
 import pytest
 
+import parity_bounds as PB
 from oracle import oracle as O
 from paper_1709_04145_b300 import inputs as I
 
@@ -60,14 +61,14 @@ def test_link_parallel_eval_matches_oracle(S):
         qp, qc, ta, q_s = cases[k]
         for b in range(spec.count):
             om = O.OracleModel.from_spec(spec, b)
-            Eo, ro, go, _ = om.eval(S, dt, q_s[b], qp[b], qc[b], ta[b], True)
+            Eo, ro, go, rb, gb = PB.oracle_eval_bounds(om, S, dt, q_s[b], qp[b], qc[b], ta[b])
             Eg = E[batch.inst_off[k] + b]
             assert abs(Eg - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (spec.name, b, Eg, Eo)
             assert _relerr(resids[k][b].reshape(-1), ro) < REL_EVAL, (spec.name, b)
             assert _relerr(grads[k][b].reshape(-1), go) < REL_EVAL, (spec.name, b)
-            # per element, with twice the binary64 rounding bound of r as floor
-            dr = np.abs(resids[k][b].reshape(-1) - ro)
-            assert np.all(dr <= REL_EVAL * np.abs(ro) + 2 * om.floor(S, dt)), (spec.name, b)
+            # per element, with the floor from the rounding bound of r
+            assert PB.ratio(resids[k][b], ro, rb) <= 1.0, (spec.name, b)
+            assert PB.ratio(grads[k][b], go, gb) <= 1.0, (spec.name, b)
             # and the two mappings agree to rounding
             assert _relerr(grads[k][b], grads_s[k][b]) < REL_EVAL, (spec.name, b)
 
@@ -83,10 +84,12 @@ def test_link_parallel_eval_full_warp_groups(S, N):
     qp, qc, ta, q_s = cases[0]
     for b in range(specs[0].count):
         om = O.OracleModel.from_spec(specs[0], b)
-        Eo, ro, go, _ = om.eval(S, dt, q_s[b], qp[b], qc[b], ta[b], True)
+        Eo, ro, go, rb, gb = PB.oracle_eval_bounds(om, S, dt, q_s[b], qp[b], qc[b], ta[b])
         assert abs(E[b] - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (b, E[b], Eo)
         assert _relerr(resids[0][b].reshape(-1), ro) < REL_EVAL, b
         assert _relerr(grads[0][b].reshape(-1), go) < REL_EVAL, b
+        assert PB.ratio(resids[0][b], ro, rb) <= 1.0, b
+        assert PB.ratio(grads[0][b], go, gb) <= 1.0, b
 
 
 def test_link_parallel_eval_free_root_chain():
@@ -248,9 +251,11 @@ def test_link_parallel_full_size_ball_chains():
     E, g = E.cpu().numpy(), g.cpu().numpy().reshape(spec.count, S * spec.n_dof)
     for b in np.linspace(0, spec.count - 1, 12).astype(int):
         om = O.OracleModel.from_spec(spec, int(b))
-        Eo, _, go, _ = om.eval(S, dt, qs_h[b], qp_h[b], w["q0"][b], np.zeros(spec.n_dof), True)
+        Eo, _, go, _, gb = PB.oracle_eval_bounds(om, S, dt, qs_h[b], qp_h[b], w["q0"][b],
+                                                 np.zeros(spec.n_dof))
         assert abs(E[b] - Eo) <= REL_EVAL * abs(Eo), b
         assert _relerr(g[b], go) < REL_EVAL, b
+        assert PB.ratio(g[b], go, gb) <= 1.0, b
     outs = {}
     for mp in (P.MAP_STAGE, P.MAP_LINK):
         batch.set_mapping(mp)

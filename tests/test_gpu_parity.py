@@ -2,6 +2,7 @@
 import numpy as np
 import pytest
 
+import parity_bounds as PB
 from oracle import oracle as O
 from paper_1709_04145_b300 import inputs as I
 
@@ -68,17 +69,16 @@ def test_eval_matches_oracle(S):
         qp, qc, ta, q_s = cases[k]
         for b in range(spec.count):
             om = O.OracleModel.from_spec(spec, b)
-            Eo, ro, go, _ = om.eval(S, dt, q_s[b], qp[b], qc[b], ta[b], True)
+            Eo, ro, go, rb, gb = PB.oracle_eval_bounds(om, S, dt, q_s[b], qp[b], qc[b], ta[b])
             Eg = E[batch.inst_off[k] + b]
             assert abs(Eg - Eo) <= REL_EVAL * max(abs(Eo), 1.0), (spec.name, b, Eg, Eo)
             assert _relerr(resids[k][b].reshape(-1), ro) < REL_EVAL, (spec.name, b)
             assert _relerr(grads[k][b].reshape(-1), go) < REL_EVAL, (spec.name, b)
-            # per element: each residual component to 1e-10 of itself, with an
-            # absolute floor of twice the binary64 rounding bound of r (the
-            # largest component alone would let small ones pass loosely)
-            fl = om.floor(S, dt)
-            dr = np.abs(resids[k][b].reshape(-1) - ro)
-            assert np.all(dr <= REL_EVAL * np.abs(ro) + 2 * fl), (spec.name, b, dr.max(), fl)
+            # per element: each component to 1e-10 of itself, with an absolute
+            # floor from the binary64 rounding bound of r (the largest component
+            # alone would let small ones pass loosely)
+            assert PB.ratio(resids[k][b], ro, rb) <= 1.0, (spec.name, b)
+            assert PB.ratio(grads[k][b], go, gb) <= 1.0, (spec.name, b)
 
 
 def test_eval_without_tau_and_single_instance():
