@@ -3,7 +3,11 @@ whose backward pass applies the implicit-function-theorem adjoint of every
 converged step. States are checkpointed every ``checkpoint_every`` steps;
 going back over each segment takes two launches: a rollout that recomputes
 the segment's steps and keeps their stages, and pbad_rollout_backward,
-which walks them in reverse.
+which walks them in reverse. With ``keep_stages=True`` the forward pass
+keeps every step's stages instead (S n doubles per instance-step: 36 MB for
+1024 twenty-link trees over 64 two-stage steps), and the backward pass runs
+only the pbad_rollout_backward launches; the gradients are bitwise those of
+the recomputing form, which re-runs the same launches on the same inputs.
 
 The adjoint of a step is the implicit-function theorem at its root, r = 0,
 so it holds only for steps solved to the tolerance (CONVERGED) or to the
@@ -53,17 +57,20 @@ class _Rollout(torch.autograd.Function):
         q_prev = (q0 + nodes[0] * dt * qd0).contiguous()
         q_cur = q0.contiguous()
         ckpts = []
+        kept = []  # per segment (stages_traj, status) when keep_stages
         status = torch.zeros(batch.n_instances, dtype=torch.int32, device=q0.device)
         for s0 in range(0, n_steps, k):
             s1 = min(s0 + k, n_steps)
             ckpts.append((s0, s1, q_prev.clone(), q_cur.clone()))
             out = rollout(batch, q_prev, q_cur, tau_seq[s0:s1].contiguous(), s1 - s0, dt, S,
                           cfg["solver"], cfg["history"], cfg["tol"], cfg["max_iter"],
-                          want_traj=False, want_step_log=False)
+                          want_traj=False, want_step_log=False, want_stages=cfg["keep_stages"])
+            if cfg["keep_stages"]:
+                kept.append((out["stages_traj"], out["status"]))
             status = worse_status(status, out["status"])
             q_prev, q_cur = out["q_prev"], out["q_cur"]
         ckpts.append((n_steps, n_steps, q_prev.clone(), q_cur.clone()))  # the end state
-        ctx.batch, ctx.cfg, ctx.ckpts = batch, cfg, ckpts
+        ctx.batch, ctx.cfg, ctx.ckpts, ctx.kept = batch, cfg, ckpts, kept
         ctx.save_for_backward(tau_seq)
         ctx.node_prev = float(nodes[0])
         ctx.mark_non_differentiable(status)
@@ -84,21 +91,25 @@ class _Rollout(torch.autograd.Function):
         for si in range(len(segs) - 2, -1, -1):
             s0, s1, qp0, qc0 = segs[si]
             tau_seg = tau_seq[s0:s1].contiguous()
-            # recompute the segment in one launch, keeping every step's stages
-            out = rollout(batch, qp0, qc0, tau_seg, s1 - s0, dt, S, cfg["solver"], cfg["history"],
-                          cfg["tol"], cfg["max_iter"], want_traj=False, want_step_log=False,
-                          want_stages=True)
-            adj = worse_status(adj, out["status"])
-            # the same launch on the same inputs: the recomputed segment must
-            # end bitwise where the forward pass's did
-            ep, ec = segs[si + 1][2], segs[si + 1][3]
-            if not (torch.equal(out["q_prev"], ep) and torch.equal(out["q_cur"], ec)):
-                raise RuntimeError("rollout recompute diverged from the forward pass "
-                                   f"(steps {s0}..{s1 - 1})")
+            if ctx.kept:
+                stages_traj, seg_status = ctx.kept[si]
+            else:
+                # recompute the segment in one launch, keeping every step's stages
+                out = rollout(batch, qp0, qc0, tau_seg, s1 - s0, dt, S, cfg["solver"],
+                              cfg["history"], cfg["tol"], cfg["max_iter"], want_traj=False,
+                              want_step_log=False, want_stages=True)
+                # the same launch on the same inputs: the recomputed segment must
+                # end bitwise where the forward pass's did
+                ep, ec = segs[si + 1][2], segs[si + 1][3]
+                if not (torch.equal(out["q_prev"], ep) and torch.equal(out["q_cur"], ec)):
+                    raise RuntimeError("rollout recompute diverged from the forward pass "
+                                       f"(steps {s0}..{s1 - 1})")
+                stages_traj, seg_status = out["stages_traj"], out["status"]
+            adj = worse_status(adj, seg_status)
             # the adjoint of the segment's steps, in reverse, in one launch
-            a_prev, a_cur, g_seg, st = rollout_backward(batch, qp0, qc0, tau_seg,
-                                                        out["stages_traj"], s1 - s0, dt, S,
-                                                        a_prev.contiguous(), a_cur.contiguous())
+            a_prev, a_cur, g_seg, st = rollout_backward(batch, qp0, qc0, tau_seg, stages_traj,
+                                                        s1 - s0, dt, S, a_prev.contiguous(),
+                                                        a_cur.contiguous())
             adj = worse_status(adj, st)
             g_tau[s0:s1] = g_seg
         g_q0 = a_prev + a_cur
@@ -120,7 +131,8 @@ class _Rollout(torch.autograd.Function):
 def rollout_differentiable(batch: Batch, q0, qd0, tau_seq, dt: float, stages: int,
                            solver=NEWTON, history: int = 8, tol: float = 1e-10,
                            max_iter: int = 100, checkpoint_every: int = 8,
-                           on_unsolved: str = "nan", adjoint_status=None):
+                           on_unsolved: str = "nan", adjoint_status=None,
+                           keep_stages: bool = False):
     """Differentiable rollout of tau_seq.shape[0] steps from (q0, qd0).
     Returns (q_cur, q_prev, status) after the last step (status: the worst
     step status per instance); q_cur and q_prev carry gradients to q0, qd0
@@ -129,12 +141,16 @@ def rollout_differentiable(batch: Batch, q0, qd0, tau_seq, dt: float, stages: in
     or with a singular adjoint system, are set to NaN (on_unsolved="nan"),
     to zero ("zero"), or left as computed ("keep"). adjoint_status, an int32
     CUDA tensor (instances,), receives in the backward pass the worst over
-    the steps of each recomputed step's status and its adjoint's status."""
+    the steps of each recomputed step's status and its adjoint's status.
+    keep_stages=True keeps every step's stages from the forward pass (S n
+    doubles per instance-step) so that the backward pass recomputes nothing;
+    the gradients are the same bits."""
     if on_unsolved not in ("nan", "zero", "keep"):
         raise ValueError("on_unsolved must be 'nan', 'zero' or 'keep'")
     cfg = dict(stages=stages, dt=dt, n_steps=int(tau_seq.shape[0]), solver=solver,
                history=history, tol=tol, max_iter=max_iter, checkpoint_every=checkpoint_every,
-               on_unsolved=on_unsolved, adjoint_status=adjoint_status)
+               on_unsolved=on_unsolved, adjoint_status=adjoint_status,
+               keep_stages=bool(keep_stages))
     return _Rollout.apply(q0, qd0, tau_seq, batch, cfg)
 
 

@@ -254,6 +254,40 @@ def test_unsolved_steps_flag_their_instances_gradients():
                 assert np.array_equal(blk(gz[k]), blk(gk[k])), (b, k)
 
 
+def test_kept_stages_give_the_recomputed_gradients_bitwise():
+    """keep_stages=True (the forward pass keeps every step's stages, the
+    backward pass recomputes nothing) gives the same gradient bits and the
+    same adjoint status as recomputing each checkpoint segment, with two
+    fast-moving instances unsolved under an eight-iteration cap."""
+    import torch
+
+    import paper_1709_04145_b300 as P
+    from paper_1709_04145_b300.autograd import rollout_differentiable
+    dev = torch.device("cuda:0")
+    S, dt, n_steps = 2, 0.033, 7
+    spec = I.humanoid(6, seed=95)
+    q0, qd0 = I.random_state(spec, 96, pose_scale=0.3, vel_sigma=0.3)
+    qd0[:2] *= 6.0
+    tau = I.torques(spec, n_steps, 97, sigma=0.1)
+    batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
+    w = torch.tensor(np.random.default_rng(98).normal(size=batch.D), device=dev)
+    res = {}
+    for keep in (False, True):
+        x0 = torch.tensor(q0.reshape(-1), device=dev, requires_grad=True)
+        v0 = torch.tensor(qd0.reshape(-1), device=dev, requires_grad=True)
+        tt = torch.tensor(tau.reshape(n_steps, -1), device=dev, requires_grad=True)
+        adj = torch.full((spec.count,), -1, dtype=torch.int32, device=dev)
+        qc, qp, st = rollout_differentiable(batch, x0, v0, tt, dt, S, P.NEWTON, tol=1e-10,
+                                            max_iter=8, checkpoint_every=3, on_unsolved="keep",
+                                            adjoint_status=adj, keep_stages=keep)
+        ((qc * w).sum() + (qp * w).sum()).backward()
+        res[keep] = [a.cpu().numpy() for a in (x0.grad, v0.grad, tt.grad, st, adj, qc.detach())]
+    for a, b in zip(res[False], res[True]):
+        assert np.array_equal(a, b, equal_nan=True)
+    st = res[True][3]
+    assert (st == 0).any() and (st != 0).any(), st  # both kinds of instance
+
+
 @pytest.mark.parametrize("S", [1, 2])
 def test_segment_backward_equals_chained_step_backward(S):
     """pbad_rollout_backward over a segment (one launch) gives what chaining
