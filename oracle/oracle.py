@@ -94,6 +94,8 @@ def lib():
         L.om_deriv.argtypes = [vp, dp, dp, dp]
         L.om_lbfgs_direction.argtypes = [C.c_int, C.c_int, C.c_int, C.c_int, dp, dp, dp,
                                          C.c_double, dp, dp, C.c_int, dp]
+        L.om_precond_apply.argtypes = [vp, C.c_int, C.c_double, dp, dp, dp]
+        L.om_contact_gn.argtypes = [vp, C.c_double, dp, dp, dp]
         _lib = L
     return _lib
 
@@ -335,6 +337,24 @@ class OracleModel:
                            C.byref(it), C.byref(ev), C.byref(rn))
         self.last_rnorm = rn.value
         return qs.reshape(S, n), st, it.value, ev.value
+
+    def precond_apply(self, S: int, dt: float, q_cur, v):
+        """P v with the L-BFGS preconditioner built at q_cur (v: S n)."""
+        n = self.n_dof
+        q_cur, cp = _d(q_cur)
+        v, vp_ = _d(np.asarray(v).reshape(S * n))
+        out = np.zeros(S * n)
+        lib().om_precond_apply(self._h, S, dt, cp, vp_, out.ctypes.data_as(C.POINTER(C.c_double)))
+        return out
+
+    def contact_gn(self, dt: float, q, q_cur):
+        """The contact term (n x n) of the one-stage Gauss-Newton matrix at q."""
+        n = self.n_dof
+        q, qp_ = _d(q)
+        q_cur, cp = _d(q_cur)
+        H = np.zeros((n, n))
+        lib().om_contact_gn(self._h, dt, qp_, cp, H.ctypes.data_as(C.POINTER(C.c_double)))
+        return H
 
     def floor(self, S: int, dt: float) -> float:
         """Rounding floor of |r|_2 for one step (see om_floor); a step whose

@@ -1251,6 +1251,14 @@ static void contact_gn(om_model *m, double dt, const double *q, const double *q_
   free(Tn); free(Tc); free(dTl); free(dP);
 }
 
+/* Test access: H (n x n, overwritten) = the contact term of the one-stage
+ * Gauss-Newton matrix at q, as the Newton solve adds it. */
+void om_contact_gn(void *p, double dt, const double *q, const double *q_cur, double *H) {
+  om_model *m = (om_model *)p;
+  memset(H, 0, sizeof(double) * m->n_dof * m->n_dof);
+  contact_gn(m, dt, q, q_cur, H);
+}
+
 /* ------------------------------------------------------------------ */
 /* dense linear algebra for the optimisers and the adjoint              */
 /* ------------------------------------------------------------------ */
@@ -1514,6 +1522,19 @@ static void precond_apply(const om_model *m, const om_precond *pc, double *v) {
       }
     }
   free(t);
+}
+
+/* Test access to the preconditioner: out = P v with P built at q_cur as the
+ * L-BFGS solve builds it (v, out: S*n, stage-major). */
+void om_precond_apply(void *p, int S, double dt, const double *q_cur, const double *v,
+                      double *out) {
+  om_model *m = (om_model *)p;
+  om_precond pc;
+  pc.Pb = (double *)malloc(sizeof(double) * 9 * m->n_links);
+  lbfgs_precond(m, S, dt, q_cur, &pc);
+  memcpy(out, v, sizeof(double) * S * m->n_dof);
+  precond_apply(m, &pc, out);
+  free(pc.Pb);
 }
 
 /* Line-search constants: Armijo c1, approximate-Wolfe delta and relative
