@@ -1,8 +1,9 @@
 """Differentiable rollouts: a torch.autograd.Function over the CUDA rollout
 whose backward pass applies the implicit-function-theorem adjoint of every
-converged step. The forward pass is one persistent launch over all steps;
-states are checkpointed every ``checkpoint_every`` steps (rows of its
-trajectory), and going back over each segment takes two launches: a rollout that recomputes
+converged step. The forward pass is one persistent launch over all steps
+(one per segment when the whole trajectory would exceed
+ONE_LAUNCH_TRAJ_BYTES); states are checkpointed every ``checkpoint_every``
+steps, and going back over each segment takes two launches: a rollout that recomputes
 the segment's steps and keeps their stages, and pbad_rollout_backward,
 which walks them in reverse. With ``keep_stages=True`` the forward pass
 keeps every step's stages instead (S n doubles per instance-step: 36 MB for
@@ -33,6 +34,9 @@ from . import Batch, LBFGS, NEWTON, colloc, rollout, rollout_backward
 from ._native import check, lib
 
 CONVERGED, STALLED = 0, 5
+# the forward pass runs in one launch when its whole trajectory (q_prev and
+# q_cur of every step) fits in this many bytes, else one launch per segment
+ONE_LAUNCH_TRAJ_BYTES = 1 << 30
 _RANK = torch.tensor([0, 2, 3, 4, 5, 1], dtype=torch.int32)  # severity of status 0..5
 
 
@@ -57,28 +61,43 @@ class _Rollout(torch.autograd.Function):
         nodes, _ = colloc(S)
         q_prev = (q0 + nodes[0] * dt * qd0).contiguous()
         q_cur = q0.contiguous()
-        # every step in one persistent launch (each instance's warp carries its
-        # state from step to step exactly as separate launches would, so the
-        # backward pass's segment recomputes end bitwise at the checkpoints);
-        # the checkpoints are the trajectory's rows at the segment starts
-        out = rollout(batch, q_prev, q_cur, tau_seq.contiguous(), n_steps, dt, S, cfg["solver"],
-                      cfg["history"], cfg["tol"], cfg["max_iter"], want_traj=True,
-                      want_step_log=False, want_stages=cfg["keep_stages"])
-        status = out["status"]
         ckpts = []
         kept = []  # per segment (stages_traj, status) when keep_stages
-        for s0 in range(0, n_steps, k):
-            s1 = min(s0 + k, n_steps)
-            if s0 > 0:
-                q_prev, q_cur = out["traj_prev"][s0 - 1], out["traj_cur"][s0 - 1]
-            ckpts.append((s0, s1, q_prev.clone(), q_cur.clone()))
-            if cfg["keep_stages"]:
-                # (the worst status over all steps: the adjoint status is the
-                # worst over the segments either way)
-                kept.append((out["stages_traj"][s0:s1], status))
-        q_prev, q_cur = out["q_prev"], out["q_cur"]  # the end state
+        traj_bytes = 2 * n_steps * batch.D * 8
+        if cfg["keep_stages"] or traj_bytes <= ONE_LAUNCH_TRAJ_BYTES:
+            # every step in one persistent launch (each instance's warp carries
+            # its state from step to step exactly as separate launches would,
+            # so the backward pass's segment recomputes end bitwise at the
+            # checkpoints); the checkpoints are the trajectory's rows at the
+            # segment starts
+            out = rollout(batch, q_prev, q_cur, tau_seq.contiguous(), n_steps, dt, S,
+                          cfg["solver"], cfg["history"], cfg["tol"], cfg["max_iter"],
+                          want_traj=True, want_step_log=False, want_stages=cfg["keep_stages"])
+            status = out["status"]
+            for s0 in range(0, n_steps, k):
+                s1 = min(s0 + k, n_steps)
+                if s0 > 0:
+                    q_prev, q_cur = out["traj_prev"][s0 - 1], out["traj_cur"][s0 - 1]
+                ckpts.append((s0, s1, q_prev.clone(), q_cur.clone()))
+                if cfg["keep_stages"]:
+                    # (the worst status over all steps: the adjoint status is
+                    # the worst over the segments either way)
+                    kept.append((out["stages_traj"][s0:s1], status))
+            q_prev, q_cur = out["q_prev"], out["q_cur"]  # the end state
+            del out
+        else:
+            # a trajectory too large to hold: one launch per segment, keeping
+            # only the checkpoints
+            status = torch.zeros(batch.n_instances, dtype=torch.int32, device=q0.device)
+            for s0 in range(0, n_steps, k):
+                s1 = min(s0 + k, n_steps)
+                ckpts.append((s0, s1, q_prev.clone(), q_cur.clone()))
+                out = rollout(batch, q_prev, q_cur, tau_seq[s0:s1].contiguous(), s1 - s0, dt, S,
+                              cfg["solver"], cfg["history"], cfg["tol"], cfg["max_iter"],
+                              want_traj=False, want_step_log=False)
+                status = worse_status(status, out["status"])
+                q_prev, q_cur = out["q_prev"], out["q_cur"]
         ckpts.append((n_steps, n_steps, q_prev.clone(), q_cur.clone()))
-        del out
         ctx.batch, ctx.cfg, ctx.ckpts, ctx.kept = batch, cfg, ckpts, kept
         ctx.save_for_backward(tau_seq)
         ctx.node_prev = float(nodes[0])

@@ -254,14 +254,16 @@ def test_unsolved_steps_flag_their_instances_gradients():
                 assert np.array_equal(blk(gz[k]), blk(gk[k])), (b, k)
 
 
-def test_kept_stages_give_the_recomputed_gradients_bitwise():
+def test_kept_stages_give_the_recomputed_gradients_bitwise(monkeypatch):
     """keep_stages=True (the forward pass keeps every step's stages, the
     backward pass recomputes nothing) gives the same gradient bits and the
-    same adjoint status as recomputing each checkpoint segment, with two
+    same adjoint status as recomputing each checkpoint segment, whether the
+    forward pass ran as one launch or as one launch per segment, with two
     fast-moving instances unsolved under an eight-iteration cap."""
     import torch
 
     import paper_1709_04145_b300 as P
+    from paper_1709_04145_b300 import autograd as AG
     from paper_1709_04145_b300.autograd import rollout_differentiable
     dev = torch.device("cuda:0")
     S, dt, n_steps = 2, 0.033, 7
@@ -272,7 +274,9 @@ def test_kept_stages_give_the_recomputed_gradients_bitwise():
     batch = P.Batch([P.Model.from_spec(spec)], max_stages=S, max_history=8, newton=True)
     w = torch.tensor(np.random.default_rng(98).normal(size=batch.D), device=dev)
     res = {}
-    for keep in (False, True):
+    for keep, one_launch_bytes in ((False, AG.ONE_LAUNCH_TRAJ_BYTES), (False, 0),
+                                   (True, AG.ONE_LAUNCH_TRAJ_BYTES)):
+        monkeypatch.setattr(AG, "ONE_LAUNCH_TRAJ_BYTES", one_launch_bytes)
         x0 = torch.tensor(q0.reshape(-1), device=dev, requires_grad=True)
         v0 = torch.tensor(qd0.reshape(-1), device=dev, requires_grad=True)
         tt = torch.tensor(tau.reshape(n_steps, -1), device=dev, requires_grad=True)
@@ -281,10 +285,13 @@ def test_kept_stages_give_the_recomputed_gradients_bitwise():
                                             max_iter=8, checkpoint_every=3, on_unsolved="keep",
                                             adjoint_status=adj, keep_stages=keep)
         ((qc * w).sum() + (qp * w).sum()).backward()
-        res[keep] = [a.cpu().numpy() for a in (x0.grad, v0.grad, tt.grad, st, adj, qc.detach())]
-    for a, b in zip(res[False], res[True]):
-        assert np.array_equal(a, b, equal_nan=True)
-    st = res[True][3]
+        res[(keep, one_launch_bytes)] = [a.cpu().numpy() for a in
+                                         (x0.grad, v0.grad, tt.grad, st, adj, qc.detach())]
+    runs = list(res.values())
+    for other in runs[1:]:
+        for a, b in zip(runs[0], other):
+            assert np.array_equal(a, b, equal_nan=True)
+    st = runs[0][3]
     assert (st == 0).any() and (st != 0).any(), st  # both kinds of instance
 
 
