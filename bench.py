@@ -320,13 +320,14 @@ def _cpu_model() -> str:
     return "unknown"
 
 
-def cpu_oracle_rate(w, n_inst, n_steps, budget_s, fast=False):
+def cpu_oracle_rate(w, n_inst, n_steps, budget_s, fast=False, counts=None):
     """Oracle link-steps/s on the host cores over a bounded sample: the first
     n_inst instances of the workload, one process per core (spawn; started,
     imported and warmed before the timed map). n_steps = 0 picks the number
     of time steps so that the timed map takes about budget_s seconds, from
     the warm-up's seconds per instance-step. Returns (rate, cores, sample
-    description)."""
+    description); `counts`, a dict, receives the sample's size and each
+    instance's iterations and evaluations."""
     import multiprocessing as mp
     from oracle import oracle as O
     spec = w["spec"]
@@ -350,6 +351,9 @@ def cpu_oracle_rate(w, n_inst, n_steps, budget_s, fast=False):
         t0 = time.perf_counter()
         res = pool.map(_oracle_instance, [job(b, n_steps) for b in range(n_inst)], chunksize=1)
         wall = time.perf_counter() - t0
+    if counts is not None:
+        counts.update(n_inst=n_inst, n_steps=n_steps, iters=[int(r[1]) for r in res],
+                      evals=[int(r[2]) for r in res])
     link_steps = n_inst * spec.n_links * n_steps
     sample = (f"{n_inst} of {spec.count} instances x the first {n_steps} of {w['n_steps']} time "
               f"steps, same solver settings, {'O(N)' if fast else 'brute-force O(N^2)'} "
@@ -1225,12 +1229,22 @@ def run_ours(args):
         line["cpu_baseline"]["single_core"] = {"value": rate1, "unit": UNIT, "sample": sample1}
         # the fair CPU baseline: the same L-BFGS with O(N) evaluations
         # (Algorithm DERIV for the residuals, its tangent for the gradient)
+        cnt = {}
         rate_f, cores_f, sample_f = cpu_oracle_rate(w, n_inst=min(os.cpu_count() or 1, 16),
                                                     n_steps=0, budget_s=args.cpu_sample_seconds,
-                                                    fast=True)
+                                                    fast=True, counts=cnt)
         line["cpu_baseline"]["o_n_evaluation"] = {"value": rate_f, "unit": UNIT, "cores": cores_f,
                                                   "kind": "oracle L-BFGS, O(N) evaluation",
                                                   "sample": sample_f}
+        # the oracle's iteration and evaluation counts beside the GPU's on the
+        # same instances (the GPU's over all T steps of the timed rollout)
+        ni, ns = cnt["n_inst"], cnt["n_steps"]
+        line["cpu_baseline"]["o_n_evaluation"]["counts_side_by_side"] = {
+            "instances": ni, "oracle_steps": ns, "gpu_steps": T,
+            "oracle_iters_per_step": sum(cnt["iters"]) / (ni * ns),
+            "gpu_iters_per_step": float(iters[:ni].mean() / T),
+            "oracle_evals_per_step": sum(cnt["evals"]) / (ni * ns),
+            "gpu_evals_per_step": float(evals[:ni].mean() / T)}
     if world > 1:
         dist.destroy_process_group()
     if rank == 0:
