@@ -215,6 +215,18 @@ PBAD_API int pbad_batch_set_mapping(pbad_batch* batch, int32_t mapping);
  * (null batch, min_sn outside 1..4097), PBAD_ERR_ALLOC, PBAD_ERR_CUDA. */
 PBAD_API int pbad_batch_set_newton_cta_min(pbad_batch* batch, int32_t min_sn);
 
+/* One-warp Newton (LM) buckets with S >= 2 (Eq. EQHOC): on = 1 (the default)
+ * spreads the residual pass at each trial point of the damping loop over the
+ * warp's 32 / S replicas of the stage group (each replica takes every
+ * (32 / S)-th link's joint rotation, axes, stage coupling, mass product,
+ * seed and wrench; the forward kinematics and the subtree sums stay
+ * sequential, in the order of the full pass); on = 0 has every replica
+ * evaluate the whole pass. Both give the same bits: the setting changes
+ * only the time of a trial, which matters for instances whose damping loop
+ * rejects many trials (Section 5: lambda is raised until E decreases).
+ * Errors: PBAD_ERR_ARG (null batch, on not 0 or 1). */
+PBAD_API int pbad_batch_set_newton_split(pbad_batch* batch, int32_t on);
+
 /* The damped Gauss-Newton system of one LM iteration (Section 5, LM with
  * J^T J), batched, on its own: for each instance b of count,
  *   H_b = J_b^T J_b,  L_b L_b^T = H_b + lambda I (Cholesky),

@@ -220,6 +220,14 @@ class Batch:
         check(lib().pbad_batch_set_newton_cta_min(self._h, int(min_sn)),
               "pbad_batch_set_newton_cta_min")
 
+    def set_newton_split(self, on: bool):
+        """One-warp Newton buckets with two or more stages: spread the
+        residual pass at each trial point of the damping loop over the
+        warp's replicas (True, the default) or have every replica evaluate
+        it (False). Both give the same bits."""
+        check(lib().pbad_batch_set_newton_split(self._h, 1 if on else 0),
+              "pbad_batch_set_newton_split")
+
     def set_precision(self, precision: int):
         """Arithmetic of eval_objective_grad's residual pass: PRECISION_F64
         (default) or PRECISION_DF64 (double-float after the joint rotations;

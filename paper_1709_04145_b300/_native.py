@@ -21,7 +21,7 @@ SYMBOLS = ("pbad_version", "pbad_last_error", "pbad_colloc", "pbad_model_create"
            "pbad_model_set_contact", "pbad_batch_set_queue", "pbad_batch_set_mapping",
            "pbad_fp64_mma_peak", "pbad_batch_set_precision", "pbad_rollout_backward",
            "pbad_batch_set_bucket_mapping", "pbad_damped_gram_solve",
-           "pbad_batch_set_newton_cta_min")
+           "pbad_batch_set_newton_cta_min", "pbad_batch_set_newton_split")
 
 
 class PBADError(RuntimeError):
@@ -67,6 +67,7 @@ def lib():
         L.pbad_batch_set_bucket_mapping.argtypes = [vp, C.POINTER(C.c_int32)]
         L.pbad_damped_gram_solve.argtypes = [C.c_int64, i32, vp, vp, C.c_double, vp, vp, vp, vp, vp]
         L.pbad_batch_set_newton_cta_min.argtypes = [vp, i32]
+        L.pbad_batch_set_newton_split.argtypes = [vp, i32]
         L.pbad_model_set_drag.argtypes = [vp, f64]
         L.pbad_model_set_contact.argtypes = [vp, i32, C.POINTER(C.c_int32), C.POINTER(C.c_double),
                                              f64, f64, f64]

@@ -157,6 +157,7 @@ struct pbad_batch {
   std::vector<int> bucket_mapping;  // per bucket for steps and rollouts (-1: the batch's mapping)
   int precision = PBAD_PRECISION_F64;  // arithmetic of pbad_eval_objective_grad's residual pass
   int newton_cta_min = kNewtonCtaMin;  // Newton buckets with S n at least this run a CTA per instance
+  int newton_split = 1;  // one-warp Newton: trial residual passes spread over the replicas
 };
 
 namespace {
@@ -415,6 +416,7 @@ int fill_launch(pbad_batch* bt, int S, double dt, const int32_t* solvers, int hi
     const int sn = S * m->n;
     B.cta = (!all_warp && B.solver == PBAD_NEWTON && sn >= bt->newton_cta_min && sn <= kNewtonCtaMaxSn)
                 ? kNewtonCtaWarps : 1;
+    B.split = bt->newton_split;
     const int64_t warps = warp_map ? m->count * B.cta
                                    : (m->count + groups_per_warp(S) - 1) / groups_per_warp(S);
     blocks += (int)((warps + wpb - 1) / wpb);
@@ -1117,6 +1119,13 @@ int pbad_batch_set_bucket_mapping(pbad_batch* bt, const int32_t* mapping) {
     v[k] = mapping[k];
   }
   bt->bucket_mapping = v;
+  return PBAD_OK;
+}
+
+int pbad_batch_set_newton_split(pbad_batch* bt, int32_t on) {
+  if (!bt) return fail(PBAD_ERR_ARG, "null batch");
+  if (on != 0 && on != 1) return fail(PBAD_ERR_ARG, "on must be 0 or 1");
+  bt->newton_split = on;
   return PBAD_OK;
 }
 

@@ -51,6 +51,8 @@ struct Bucket {
   int first_dynamic;
   int chain;             // 1 if parent[l] == l - 1 for every link (serial chain)
   int cta;               // Newton: warps per instance (1, or kNewtonCtaWarps for large S n)
+  int split;             // Newton, one warp per instance, S >= 2: residual passes at trial
+                         // points spread over the warp's replicas (Ctx::primal_split)
   int lp;                // L-BFGS: 1 if the bucket runs the link mapping (one lane per stage and link)
   int axial;             // 1 if every mass moment has Sxy = Sxz = Syz = mcx = mcy = 0
   double* dense;         // per-instance dense Newton/adjoint storage (or null)

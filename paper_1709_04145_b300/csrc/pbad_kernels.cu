@@ -573,9 +573,15 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
     }
   };
 
+  // trial points of the one-warp mode: residual pass spread over the replicas
+  // (the same bits as every replica evaluating it; the Jacobian that follows
+  // an accepted trial first completes the lanes' per-link arrays)
+  const bool split_ok = ncta == 1 && S >= 2 && B.split;
   while (phase != kDone) {
     const double* tau = A.tau ? A.tau + (int64_t)min(step, A.n_steps - 1) * D : nullptr;
-    const double Et = bcast0(c.evaluate_primal(tau));
+    const bool split = split_ok && phase == kTrial;
+    const double Et = bcast0(split ? c.evaluate_primal_split(tau, id.rep, id.R)
+                                   : c.evaluate_primal(tau));
     ++evals_total;
     double rrt = 0.0, fint = 1.0;
     for (int d = 0; d < n; ++d) {
@@ -641,6 +647,7 @@ __device__ __noinline__ void rollout_newton(const LaunchArgs& A, const Bucket& B
         hmax = gram_cta(c, Dn, DL, s_sa, s_sc, s_red);
       } else {
         __syncwarp();
+        if (split) c.complete_split(id.R);
         c.build_jacobian_warp(Dn, DL, id.rep, id.R, false);
         hmax = c.gram_warp(Dn, DL);
       }

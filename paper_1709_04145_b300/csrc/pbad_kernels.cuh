@@ -514,6 +514,200 @@ struct Ctx {
     return (S == 1) ? (Eown - tq) : rr;
   }
 
+  // ------------------------------------------------ replica-split residual
+  // One warp per instance (Newton) holds R = 32 / S replicas of the stage
+  // group, and a binary64 FMA costs the sub-partition the same cycles
+  // whatever the warp's active mask: the replicas evaluating the same point
+  // redundantly cost R times the per-link work. primal_split gives each
+  // replica the links rep, rep + R, ...: it computes their joint rotations,
+  // joint axes, stage coupling, mass products, seeds and wrenches into its
+  // own lanes' slots. The forward kinematics (a product along the tree) and
+  // the subtree sums and joint contractions stay sequential on every lane,
+  // in primal's order and with its arithmetic, so E, r, T and the subtree
+  // sums come out bitwise equal to primal's. A lane then holds the axes,
+  // seeds G and exponential-map coefficients of its own links only;
+  // complete_split copies the others before a tangent pass reads them.
+  // S >= 2 (the one-stage pass adds energy, drag and contact terms per link).
+  // Called convergently by the whole warp; surplus lanes (rep == R) own no
+  // link.
+  __device__ __forceinline__ Lane owner_lane(int l, int R) const {
+    Lane o;
+    o.p = ws.p + ((l % R) * S + i - grp.lane);
+    return o;
+  }
+  __device__ __noinline__ double primal_split(const double* tau, int rep, int R) const {
+    const Ctx self(*this);
+    return self.primal_split_body(tau, rep, R);
+  }
+  __device__ __forceinline__ double primal_split_body(const double* tau, int rep, int R) const {
+    const bool chain = B.chain;
+    const int slots = (N + R - 1) / R;
+    // (1) joint rotations of the own links: R into the axes slots, Jr into
+    //     the seed slots (both overwritten in (3)), the exponential-map
+    //     coefficients into their own slots
+    for (int s = 0; s < slots; ++s) {
+      const int l = s * R + rep;
+      if (rep >= R || l >= N) continue;
+      const int nd = ndof(l), d0 = B.dof[l], jt = B.jtype[l];
+      double q3[3], R9[9], Jr[9];
+      ExpCoef ec;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) q3[k] = k < nd ? ws[L.xt + d0 + k] : 0.0;
+      const double u[3] = {B.axis[3 * l], B.axis[3 * l + 1], B.axis[3 * l + 2]};
+      joint_rotation(jt, u, q3, R9, Jr, jt == kBall ? &ec : nullptr);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) {
+        ws[L.axes + 9 * l + k] = R9[k];
+        ws[L.G + 12 * l + k] = Jr[k];
+      }
+      if (jt == kBall) {
+        ws[L.ec + 4 * l] = ec.c;
+        ws[L.ec + 4 * l + 1] = ec.a;
+        ws[L.ec + 4 * l + 2] = ec.b;
+        ws[L.ec + 4 * l + 3] = ec.h;
+      }
+    }
+    __syncwarp();
+    // (2) forward kinematics, every lane, in link order
+    double Tp[12];
+    for (int l = 0; l < N; ++l) {
+      const int p = B.parent[l], nd = ndof(l), d0 = B.dof[l];
+      const Lane wo = owner_lane(l, R);
+      double R9[9], q3[3], T[12];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) R9[k] = wo[L.axes + 9 * l + k];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) q3[k] = k < nd ? ws[L.xt + d0 + k] : 0.0;
+      if (p >= 0 && !chain) load12(L.T + 12 * p, Tp);
+      link_fk_rot(l, p >= 0 ? Tp : nullptr, q3, R9, T);
+      store12(L.T + 12 * l, T);
+#pragma unroll
+      for (int k = 0; k < 12; ++k) Tp[k] = T[k];
+    }
+    __syncwarp();
+    // (3) axes, stage coupling (Eq. HOC), mass product, seed and wrench of
+    //     the own links; a replica without a link in a slot recomputes link
+    //     N - 1 and stores nothing, so that every lane takes part in the
+    //     stage shuffles
+    for (int s = 0; s < slots; ++s) {
+      const int lr = s * R + rep;
+      const bool own = rep < R && lr < N;
+      const int l = own ? lr : N - 1;
+      double T[12], Jr[9], w[9];
+      load12(L.T + 12 * l, T);
+#pragma unroll
+      for (int k = 0; k < 9; ++k) Jr[k] = ws[L.G + 12 * l + k];
+      link_axes(l, T, Jr, w);
+      double A[12];
+      load12(L.C + 12 * l, A);
+#pragma unroll
+      for (int j = 0; j < S; ++j) {
+        const double wij = wu_row[j];
+#pragma unroll
+        for (int k = 0; k < 12; ++k) A[k] = fma(wij, grp.from_full(T[k], j), A[k]);
+      }
+      const MassMoment M = mass(l);
+      double G[12];
+      if (B.axial) mul_mass_axial(A, M, G);
+      else mul_mass(A, M, G);
+      double w6[6];
+      wrench(G, T, w6);
+      if (own) {
+        const int nd = ndof(l);
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+          if (k < 3 * nd) ws[L.axes + 9 * l + k] = w[k];
+        store12(L.G + 12 * l, G);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) ws[L.acc + 6 * l + k] = w6[k];
+      }
+    }
+    __syncwarp();
+    // (4) every lane: its own copy of each link's wrench, then primal's
+    //     backward sweep (subtree sums and joint contraction)
+    for (int l = 0; l < N; ++l) {
+      const Lane wo = owner_lane(l, R);
+      double w6[6];
+#pragma unroll
+      for (int k = 0; k < 6; ++k) w6[k] = wo[L.acc + 6 * l + k];
+      __syncwarp();
+#pragma unroll
+      for (int k = 0; k < 6; ++k) ws[L.acc + 6 * l + k] = w6[k];
+    }
+    __syncwarp();
+    double rr = 0.0;
+    double carry[6] = {0, 0, 0, 0, 0, 0};
+    for (int l = N - 1; l >= 0; --l) {
+      const int p = B.parent[l], d0 = B.dof[l], nd = ndof(l);
+      const Lane wo = owner_lane(l, R);
+      double a[6];
+      for (int k = 0; k < 6; ++k) a[k] = ws[L.acc + 6 * l + k] + carry[k];
+      const double o[3] = {ws[L.T + 12 * l + 3], ws[L.T + 12 * l + 7], ws[L.T + 12 * l + 11]};
+      double of[3];
+      cross(o, a + 3, of);
+      const double mo[3] = {a[0] - of[0], a[1] - of[1], a[2] - of[2]};
+      const bool tr = B.jtype[l] == kTranslation;
+      const double load[3] = {tr ? a[3] : mo[0], tr ? a[4] : mo[1], tr ? a[5] : mo[2]};
+      for (int k = 0; k < nd; ++k) {
+        const double w[3] = {wo[L.axes + 9 * l + 3 * k], wo[L.axes + 9 * l + 3 * k + 1],
+                             wo[L.axes + 9 * l + 3 * k + 2]};
+        const double tk = tau ? tau[gdof(d0 + k)] : 0.0;
+        const double rk = dot3(w, load) - tk;
+        ws[L.rt + d0 + k] = rk;
+        rr = fma(rk, rk, rr);
+      }
+      if (chain) {
+        for (int k = 0; k < 6; ++k) {
+          carry[k] = a[k];
+          ws[L.acc + 6 * l + k] = a[k];
+        }
+      } else if (p >= 0) {
+        for (int k = 0; k < 6; ++k) ws[L.acc + 6 * p + k] += a[k];
+      }
+    }
+    return rr;
+  }
+  // Residual pass only at xt by primal_split: returns E (group total).
+  __device__ double evaluate_primal_split(const double* tau, int rep, int R) const {
+    const double e = primal_split(tau, rep, R);
+    double E = 0.0;
+#pragma unroll
+    for (int j = 0; j < S; ++j) E += grp.from_full(e, j);
+    return E;
+  }
+  // After primal_split: every lane copies the axes, seeds and exponential-map
+  // coefficients of the links it does not own from their owners, so that its
+  // slots hold what primal leaves.
+  __device__ __noinline__ void complete_split(int R) const {
+    __syncwarp();
+    for (int l = 0; l < N; ++l) {
+      const int o = (l % R) * S + i;
+      const bool copy = o != grp.lane;
+      const Lane wo = owner_lane(l, R);
+      const int nd = ndof(l);
+      double v[25];
+#pragma unroll
+      for (int k = 0; k < 12; ++k) v[k] = wo[L.G + 12 * l + k];
+#pragma unroll
+      for (int k = 0; k < 9; ++k) v[12 + k] = k < 3 * nd ? wo[L.axes + 9 * l + k] : 0.0;
+      const bool ball = B.jtype[l] == kBall;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) v[21 + k] = ball ? wo[L.ec + 4 * l + k] : 0.0;
+      __syncwarp();
+      if (copy) {
+#pragma unroll
+        for (int k = 0; k < 12; ++k) ws[L.G + 12 * l + k] = v[k];
+#pragma unroll
+        for (int k = 0; k < 9; ++k)
+          if (k < 3 * nd) ws[L.axes + 9 * l + k] = v[12 + k];
+        if (ball)
+#pragma unroll
+          for (int k = 0; k < 4; ++k) ws[L.ec + 4 * l + k] = v[21 + k];
+      }
+    }
+    __syncwarp();
+  }
+
   // V += the twist of joint l's DOFs along the direction at offset dir (own
   // stage slice); o is the joint origin. Three DOFs are summed into one axis
   // rate first (one cross product instead of three).
