@@ -47,8 +47,8 @@ COUPLING_FLOPS = 24                 # per stage of the sum over stages, per pass
 # traffic null until the kernel is captured again.
 ROLLOUT_TRAFFIC = {
     # link mapping, 3 stages, 10 links: 4096 ball chains x 100 steps, five launches of
-    # k_rollout_lp<3>: 50.59 MB read + 17.20 MB written over 5 x 56,195,050 evaluations
-    (1, 3, 10): ("0d733459a38bd9d7dddc6f865d386d5fe9b2d9a1", 0.24127),
+    # k_rollout_lp<3>: 50.58 MB read + 17.63 MB written over 5 x 56,195,050 evaluations
+    (1, 3, 10): ("4ae377fb961b07f8b13c84a51632ba974a7080cb", 0.24274),
 }
 
 
